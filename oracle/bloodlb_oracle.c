@@ -662,7 +662,7 @@ static void step_once(orc_state *s) {
       for (int r = 0; r < NQ; ++r) s->n[i * NQ + r] = s->nnew[i * NQ + r];
 
   /* 5. potentials: all pairs closer than r_cut, then every cell against every
-     surface wall node (a wall node with a fluid neighbour) */
+     surface wall node (a wall node linked to a non-wall node, Sec. III) */
   double *o = (double *)xcalloc(3 * (long)(s->np > 0 ? s->np : 1), sizeof(double));
   for (int k = 0; k < s->np; ++k) orc_axis(&s->q[4 * k], &o[3 * k]);
   for (int i = 0; i < s->np; ++i)
@@ -680,8 +680,9 @@ static void step_once(orc_state *s) {
   if (s->np > 0) {
     for (long x = 0; x < N; ++x) {
       if (!IS_WALL(s->owner[x])) continue;
+      /* a surface wall node is linked to a non-wall node by some c_r (static) */
       int surface = 0;
-      for (int r = 1; r < NQ && !surface; ++r) surface = s->owner[neighbour(p, x, r, +1)] == FLUID;
+      for (int r = 1; r < NQ && !surface; ++r) surface = !IS_WALL(s->owner[neighbour(p, x, r, +1)]);
       if (!surface) continue;
       double xc[3];
       node_coords(p, x, xc);

@@ -32,7 +32,8 @@
  * Where the paper is silent the readings are (numbered as in the design notes):
  *   Q1 body force: Guo forcing, u = (j + rho g / 2) / rho
  *   Q2 v_b at the link midpoint, rho(y,t) local in C
- *   Q3 C uses V, Omega of t-1/2; fill uses V, Omega of t+1/2 and X(t+1)
+ *   Q3 C uses V, Omega of t+1/2, solved jointly with the link forces
+ *      (implicit coupling); fill uses V, Omega of t+1/2 and X(t+1)
  *   Q4 lab-frame angular-momentum leap-frog, exact quaternion exponential
  *   Q5 simultaneous arrival: lowest particle index; s == 1 counts as inside
  *   Q6 owner change p->q: uncover by p, then cover by q
@@ -349,20 +350,16 @@ double orc_wall(const orc_params *p, const double rvec[3], const double oi[3], d
      q(t+1) = normalize(exp(Omega / 2) (x) q(t)), the exact rotation by
      |Omega| about Omega / |Omega| applied in the lab frame.              */
 
-void orc_integrate_one(const orc_params *p, double X[3], double q[4], double V[3], double L[3], double Om[3],
-                       const double F[3], const double T[3]) {
-  double m = cell_mass(p);
+/* X += V (wrapped on periodic axes); q <- exp(Om / 2) (x) q, normalised */
+static void rigid_advance(const orc_params *p, double X[3], double q[4], const double V[3], const double Om[3]) {
   int n[3] = {p->nx, p->ny, p->nz};
   for (int k = 0; k < 3; ++k) {
-    V[k] += F[k] / m;
     X[k] += V[k];
     if (p->periodic[k]) {
       if (X[k] < 0.0) X[k] += (double)n[k];
       else if (X[k] >= (double)n[k]) X[k] -= (double)n[k];
     }
-    L[k] += T[k];
   }
-  omega_from_L(p, q, L, Om);
   double th = sqrt(dot3(Om, Om));
   double dq[4] = {1.0, 0.0, 0.0, 0.0};
   if (th > 0.0) {
@@ -376,6 +373,57 @@ void orc_integrate_one(const orc_params *p, double X[3], double q[4], double V[3
   nq[3] = dq[0] * q[3] + dq[1] * q[2] - dq[2] * q[1] + dq[3] * q[0];
   double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
   for (int k = 0; k < 4; ++k) q[k] = nq[k] / nn;
+}
+
+/* free rigid-body step with a given force and torque */
+void orc_integrate_one(const orc_params *p, double X[3], double q[4], double V[3], double L[3], double Om[3],
+                       const double F[3], const double T[3]) {
+  double m = cell_mass(p);
+  for (int k = 0; k < 3; ++k) {
+    V[k] += F[k] / m;
+    L[k] += T[k];
+  }
+  omega_from_L(p, q, L, Om);
+  rigid_advance(p, X, q, V, Om);
+}
+
+/* lab-frame inertia tensor R diag(I_perp, I_perp, I_par) R^T */
+static void inertia_lab(const orc_params *p, const double q[4], double I[3][3]) {
+  double m = cell_mass(p);
+  double Iperp = m * (p->R_par * p->R_par + p->R_perp * p->R_perp) / 5.0;
+  double Ipar = 2.0 * m * p->R_perp * p->R_perp / 5.0;
+  double R[3][3];
+  rotmat(q, R);
+  double d[3] = {Iperp, Iperp, Ipar};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < 3; ++k) v += R[i][k] * d[k] * R[j][k];
+      I[i][j] = v;
+    }
+}
+
+/* Gaussian elimination with partial pivoting: A x = b for n <= 6 */
+static void solve_dense(int n, double A[6][6], double b[6], double x[6]) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) { double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+      double t = b[c]; b[c] = b[piv]; b[piv] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      double f = A[r][c] / A[c][c];
+      for (int k = c; k < n; ++k) A[r][k] -= f * A[c][k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double v = b[r];
+    for (int k = r + 1; k < n; ++k) v -= A[r][k] * x[k];
+    x[r] = v / A[r][r];
+  }
 }
 
 /* ------------------------------------------------------------------ */
@@ -593,48 +641,7 @@ static void step_once(orc_state *s) {
     s->rho[i] = rho;
   }
 
-  /* 3. advection with mid-link bounce-back and moving-boundary term (Eq. adv,
-     lbe-bb, c, lbe-bb-corr); momentum exchange Eq. (deltap) with reading Q7 */
-  for (long y = 0; y < N; ++y) {
-    if (s->owner[y] != FLUID) continue;
-    double yc[3];
-    node_coords(p, y, yc);
-    s->nnew[y * NQ + 0] = s->nstar[y * NQ + 0];
-    for (int r = 1; r < NQ; ++r) {
-      long x = neighbour(p, y, r, -1); /* source node x = y - c_r */
-      int32_t ox = s->owner[x];
-      if (ox == FLUID) {
-        s->nnew[y * NQ + r] = s->nstar[x * NQ + r];
-        continue;
-      }
-      int rb = opposite(r);
-      double cr[3] = {CX[r], CY[r], CZ[r]};
-      double vb[3] = {0, 0, 0}, arm[3] = {0, 0, 0};
-      if (IS_WALL(ox)) {
-        for (int k = 0; k < 3; ++k) vb[k] = p->wall_vel[WALL_ID(ox)][k];
-      } else {
-        /* Q2: velocity of the link midpoint y - c_r / 2 */
-        for (int k = 0; k < 3; ++k) arm[k] = min_image(p, k, yc[k] - 0.5 * cr[k] - s->X[3 * ox + k]);
-        double w[3];
-        cross(&s->Om[3 * ox], arm, w);
-        for (int k = 0; k < 3; ++k) vb[k] = s->V[3 * ox + k] + w[k];
-      }
-      double C = 2.0 * weight(r) / cs2 * s->rho[y] * dot3(cr, vb);
-      double nsb = s->nstar[y * NQ + rb];
-      s->nnew[y * NQ + r] = nsb + C;
-      s->sumC += C;
-      double dp[3] = {(2.0 * nsb + C) * -cr[0], (2.0 * nsb + C) * -cr[1], (2.0 * nsb + C) * -cr[2]};
-      if (IS_WALL(ox)) {
-        for (int k = 0; k < 3; ++k) s->wallmom[WALL_ID(ox)][k] += dp[k];
-      } else {
-        double tq[3];
-        cross(arm, dp, tq);
-        for (int k = 0; k < 3; ++k) { s->Fh[3 * ox + k] += dp[k]; s->Th[3 * ox + k] += tq[k]; }
-      }
-    }
-  }
-
-  /* 4. contact links, Eq. (deltapppp),(deltapppm): each solid node of p with a
+  /* 3. contact links, Eq. (deltapppp),(deltapppm): each solid node of p with a
      neighbour owned by another cell or a wall gets -2 alpha_r rho_bar c_r */
   for (long x = 0; x < N; ++x) {
     int32_t ox = s->owner[x];
@@ -649,19 +656,11 @@ static void step_once(orc_state *s) {
       for (int k = 0; k < 3; ++k) f[k] = -2.0 * weight(r) * p->rho0 * cr[k];
       for (int k = 0; k < 3; ++k) arm[k] = min_image(p, k, xc[k] + 0.5 * cr[k] - s->X[3 * ox + k]);
       cross(arm, f, tq);
-      for (int k = 0; k < 3; ++k) {
-        s->Fh[3 * ox + k] += f[k]; s->Th[3 * ox + k] += tq[k];
-        s->Fc[3 * ox + k] += f[k]; s->Tc[3 * ox + k] += tq[k];
-      }
+      for (int k = 0; k < 3; ++k) { s->Fc[3 * ox + k] += f[k]; s->Tc[3 * ox + k] += tq[k]; }
     }
   }
 
-  /* the fluid now holds t+1 on the nodes that were fluid at t */
-  for (long i = 0; i < N; ++i)
-    if (s->owner[i] == FLUID)
-      for (int r = 0; r < NQ; ++r) s->n[i * NQ + r] = s->nnew[i * NQ + r];
-
-  /* 5. potentials: all pairs closer than r_cut, then every cell against every
+  /* 4. potentials: all pairs closer than r_cut, then every cell against every
      surface wall node (a wall node linked to a non-wall node, Sec. III) */
   double *o = (double *)xcalloc(3 * (long)(s->np > 0 ? s->np : 1), sizeof(double));
   for (int k = 0; k < s->np; ++k) orc_axis(&s->q[4 * k], &o[3 * k]);
@@ -697,8 +696,114 @@ static void step_once(orc_state *s) {
   }
   free(o);
 
-  /* 6. leap-frog (reading Q4) with the total force and torque */
+  /* 5. cell velocities of the half step (reading Q3).  The bounce-back
+     momentum of a link (Eq. deltap) is 2 n*_rbar c_rbar minus
+     w c_r (c_r . v_b) with w = 6 alpha_r rho(y) (Eq. c) and
+     v_b = V + Omega x a, so the link force is linear in (V, Omega):
+       F = F0 - Zff V - Zft Omega,   T = T0 - Ztf V - Ztt Omega,
+     Zff = sum w c c^T, Zft = sum w c b^T, Ztf = Zft^T, Ztt = sum w b b^T,
+     b = a x c_r.  The wall moves with the velocity of the step it streams
+     across: V(t+1/2) and Omega(t+1/2) = I_lab(q(t))^-1 L(t+1/2) solve
+       (m + Zff) V + Zft Omega = m V(t-1/2) + F0 + F_other
+       Ztf V + (I_lab + Ztt) Omega = L(t-1/2) + T0 + T_other,
+     with F_other, T_other the contact, potential, fill/drain and body forces. */
   double m = cell_mass(p);
+  if (s->np > 0 && p->move_particles) {
+    double *F0 = (double *)xcalloc(3 * (long)s->np, sizeof(double));
+    double *T0 = (double *)xcalloc(3 * (long)s->np, sizeof(double));
+    double *Z = (double *)xcalloc(36 * (long)s->np, sizeof(double)); /* 6 x 6 per cell */
+    for (long y = 0; y < N; ++y) {
+      if (s->owner[y] != FLUID) continue;
+      double yc[3];
+      node_coords(p, y, yc);
+      for (int r = 1; r < NQ; ++r) {
+        int32_t ox = s->owner[neighbour(p, y, r, -1)];
+        if (ox < 0) continue;
+        int rb = opposite(r);
+        double cr[3] = {CX[r], CY[r], CZ[r]}, arm[3], b[3];
+        for (int k = 0; k < 3; ++k) arm[k] = min_image(p, k, yc[k] - 0.5 * cr[k] - s->X[3 * ox + k]);
+        cross(arm, cr, b);
+        double nsb = s->nstar[y * NQ + rb];
+        double f0[3] = {-2.0 * nsb * cr[0], -2.0 * nsb * cr[1], -2.0 * nsb * cr[2]}, t0[3];
+        cross(arm, f0, t0);
+        double w = 2.0 * weight(r) / cs2 * s->rho[y];
+        double cb[6] = {cr[0], cr[1], cr[2], b[0], b[1], b[2]};
+        for (int k = 0; k < 3; ++k) { F0[3 * ox + k] += f0[k]; T0[3 * ox + k] += t0[k]; }
+        for (int i = 0; i < 6; ++i)
+          for (int j = 0; j < 6; ++j) Z[36 * ox + 6 * i + j] += w * cb[i] * cb[j];
+      }
+    }
+    for (int i = 0; i < s->np; ++i) {
+      double I[3][3], A[6][6], rhs[6], sol[6];
+      inertia_lab(p, &s->q[4 * i], I);
+      for (int a = 0; a < 6; ++a)
+        for (int c = 0; c < 6; ++c) A[a][c] = Z[36 * i + 6 * a + c];
+      for (int k = 0; k < 3; ++k) {
+        A[k][k] += m;
+        for (int c = 0; c < 3; ++c) A[3 + k][3 + c] += I[k][c];
+        rhs[k] = m * s->V[3 * i + k] + F0[3 * i + k] + s->Fc[3 * i + k] + s->Fp[3 * i + k] + s->PF[3 * i + k] +
+                 (p->body_force_on_cells ? m * p->g[k] : 0.0);
+        rhs[3 + k] = s->L[3 * i + k] + T0[3 * i + k] + s->Tc[3 * i + k] + s->Tp[3 * i + k] + s->PT[3 * i + k];
+      }
+      solve_dense(6, A, rhs, sol);
+      for (int k = 0; k < 3; ++k) {
+        s->V[3 * i + k] = sol[k];
+        s->Om[3 * i + k] = sol[3 + k];
+      }
+      for (int k = 0; k < 3; ++k) s->L[3 * i + k] = I[k][0] * sol[3] + I[k][1] * sol[4] + I[k][2] * sol[5];
+    }
+    free(F0); free(T0); free(Z);
+  }
+
+  /* 6. advection with mid-link bounce-back and moving-boundary term (Eq. adv,
+     lbe-bb, c, lbe-bb-corr) at the cell velocities of the half step;
+     momentum exchange Eq. (deltap) with reading Q7 */
+  for (long y = 0; y < N; ++y) {
+    if (s->owner[y] != FLUID) continue;
+    double yc[3];
+    node_coords(p, y, yc);
+    s->nnew[y * NQ + 0] = s->nstar[y * NQ + 0];
+    for (int r = 1; r < NQ; ++r) {
+      long x = neighbour(p, y, r, -1); /* source node x = y - c_r */
+      int32_t ox = s->owner[x];
+      if (ox == FLUID) {
+        s->nnew[y * NQ + r] = s->nstar[x * NQ + r];
+        continue;
+      }
+      int rb = opposite(r);
+      double cr[3] = {CX[r], CY[r], CZ[r]};
+      double vb[3] = {0, 0, 0}, arm[3] = {0, 0, 0};
+      if (IS_WALL(ox)) {
+        for (int k = 0; k < 3; ++k) vb[k] = p->wall_vel[WALL_ID(ox)][k];
+      } else {
+        /* Q2: velocity of the link midpoint y - c_r / 2, cell at X(t) */
+        for (int k = 0; k < 3; ++k) arm[k] = min_image(p, k, yc[k] - 0.5 * cr[k] - s->X[3 * ox + k]);
+        double w[3];
+        cross(&s->Om[3 * ox], arm, w);
+        for (int k = 0; k < 3; ++k) vb[k] = s->V[3 * ox + k] + w[k];
+      }
+      double C = 2.0 * weight(r) / cs2 * s->rho[y] * dot3(cr, vb);
+      double nsb = s->nstar[y * NQ + rb];
+      s->nnew[y * NQ + r] = nsb + C;
+      s->sumC += C;
+      double dp[3] = {(2.0 * nsb + C) * -cr[0], (2.0 * nsb + C) * -cr[1], (2.0 * nsb + C) * -cr[2]};
+      if (IS_WALL(ox)) {
+        for (int k = 0; k < 3; ++k) s->wallmom[WALL_ID(ox)][k] += dp[k];
+      } else {
+        double tq[3];
+        cross(arm, dp, tq);
+        for (int k = 0; k < 3; ++k) { s->Fh[3 * ox + k] += dp[k]; s->Th[3 * ox + k] += tq[k]; }
+      }
+    }
+  }
+  for (int i = 0; i < 3 * s->np; ++i) { s->Fh[i] += s->Fc[i]; s->Th[i] += s->Tc[i]; }
+
+  /* the fluid now holds t+1 on the nodes that were fluid at t */
+  for (long i = 0; i < N; ++i)
+    if (s->owner[i] == FLUID)
+      for (int r = 0; r < NQ; ++r) s->n[i * NQ + r] = s->nnew[i * NQ + r];
+
+  /* totals of the step; the leap-frog moves the cells with V(t+1/2), Omega(t+1/2) */
   for (int i = 0; i < s->np; ++i) {
     for (int k = 0; k < 3; ++k) {
       s->Ftot[3 * i + k] = s->Fh[3 * i + k] + s->Fp[3 * i + k] + s->PF[3 * i + k] +
@@ -706,9 +811,7 @@ static void step_once(orc_state *s) {
       s->Ttot[3 * i + k] = s->Th[3 * i + k] + s->Tp[3 * i + k] + s->PT[3 * i + k];
       s->PF[3 * i + k] = s->PT[3 * i + k] = 0.0;
     }
-    if (!p->move_particles) continue;
-    orc_integrate_one(p, &s->X[3 * i], &s->q[4 * i], &s->V[3 * i], &s->L[3 * i], &s->Om[3 * i],
-                      &s->Ftot[3 * i], &s->Ttot[3 * i]);
+    if (p->move_particles) rigid_advance(p, &s->X[3 * i], &s->q[4 * i], &s->V[3 * i], &s->Om[3 * i]);
   }
 
   /* 7. re-discretise with the first-arrival rule, fill/drain */

@@ -1,0 +1,337 @@
+"""Benchmark of the coupled LB / rigid-ellipsoid time step on GB300.
+
+Workload (default): the 128^3 shear cell of the paper's microvessel setting,
+walls at z moving at -/+0.02, 1022 oblate (7,7,3) cells at 30 % volume
+fraction, tau = 1, FP32 shifted population storage.  One "step" is one
+coupled time step (lattice sweep with bounce-back, momentum exchange and
+contact links; cell list; pair and wall potentials; leap-frog; first-arrival
+re-discretisation with fill/drain).
+
+Metric: coupled MLUPS = lattice sites x steps / time / 1e6 over all sites
+(the paper's cost measure), plus the achieved fraction of the HBM roofline of
+the lattice sweep (algorithmic bytes per launch / its CUDA-event duration).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (launched by torchrun) every rank steps its own replica of the
+workload (the single-domain path does not shard); value sums all ranks'
+site updates over the slowest rank's time.  --impl reference times the FP64
+CPU oracle on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled MLUPS & % HBM roofline, plain FP32 vs BF16/FP16 store at stated error"
+UNIT = "MLUPS"
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if _cuda() else "gloo")
+    return ws, rank, local
+
+
+def _cuda():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name):
+    from paper_1005_2594_gb300 import workloads
+
+    if name == "shear128":
+        p, X, q = workloads.shear_cell(n=128, phi=0.30, U=0.02, seed=1002)
+        return p, X, q, None, "shear cell 128^3, walls z +-0.02, 1022 (7,7,3) cells at 30 %"
+    if name == "small32":
+        p, X, q = workloads.small_shear()
+        return p, X, q, None, "shear cell 32^3, walls z +-0.01, 20 (3.5,3.5,1.5) cells"
+    raise ValueError(name)
+
+
+def sweep_bytes(sim, dtype_size):
+    """algorithmic bytes of one lattice sweep: every fluid node reads and
+    writes its 19 populations, every node's owner id is read once"""
+    owner = sim.owner()
+    n_fluid = int((owner == -1).sum())
+    return n_fluid * 2 * 19 * dtype_size + owner.size * 4, n_fluid
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+
+    import __graft_entry__
+    from paper_1005_2594_gb300 import bloodlb as bl
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    p, X, q, mask, desc = make_workload(args.config)
+    N = p["nx"] * p["ny"] * p["nz"]
+    dsize = {0: 4, 1: 2, 2: 2}[args.store]
+    sim = bl.Simulation(p, store_dtype=args.store, stream=stream.cuda_stream, wall_mask=mask)
+    sim.set_particles(X, q)
+    sim.step(args.warmup)
+    sim.sync()
+    bl.bl_timing_enable(sim.ctx, True)
+    bl.bl_timing_read(sim.ctx)  # clear
+    launches0 = bl.bl_launch_count(sim.ctx)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    sim.sync()
+    launches = bl.bl_launch_count(sim.ctx) - launches0
+    groups = bl.bl_timing_read(sim.ctx)
+    bl.bl_timing_enable(sim.ctx, False)
+    ms_max = allreduce_max(ms, ws)
+    value = ws * N * args.steps / (ms_max * 1e-3) / 1e6
+    k1_ms, k1_n = groups["lattice_sweep"]
+    bytes_per, n_fluid = sweep_bytes(sim, dsize)
+    hbm, src = peaks()
+    achieved = bytes_per / (k1_ms / k1_n * 1e-3) / 1e9 if k1_n else None
+    group_share = {g: round(v[0] / max(sum(x[0] for x in groups.values()), 1e-30), 4) for g, v in groups.items()}
+    # end-to-end through the C ABI with host buffers: each step uploads the
+    # cell state (bl_particles_set), steps once and reads back forces and state
+    e2e = run_e2e(sim, X.shape[0], N, args.e2e_steps, stream)
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "f16"}[args.store],
+        "data": "synthetic (seeded random packing, resting start)",
+        "config": {"workload": desc, "lattice": [p["nx"], p["ny"], p["nz"]], "cells": int(X.shape[0]),
+                   "fluid_nodes": n_fluid, "store": {0: "f32", 1: "bf16", 2: "f16"}[args.store],
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "populations %.0f MB > 129 MB L2, no flush" % (N * 19 * dsize / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": hbm,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
+                     "traffic": None, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
+                     else "fallback 6.8 TB/s", "kernel": "k_lb_step (fused collide/stream/bounce-back)",
+                     "bytes_per_launch": bytes_per, "launch_ms": round(k1_ms / max(k1_n, 1), 5)},
+        "kernel_time_share": group_share,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    return out, (p, X, q, desc)
+
+
+def run_e2e(sim, n, N, steps, stream):
+    import torch
+
+    from paper_1005_2594_gb300 import bloodlb as bl
+
+    if steps <= 0:
+        return None
+    st = sim.particles()
+    Xh, qh, Vh, Lh = (np.ascontiguousarray(st[k]) for k in ("X", "q", "V", "L"))
+    sim.sync()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.set_particles(Xh, qh, Vh, Lh)
+        sim.step(1)
+        st = sim.particles()
+        Xh, qh, Vh, Lh = st["X"], st["q"], st["V"], st["L"]
+    sim.sync()
+    dt = time.perf_counter() - t0
+    return {"value": round(N * steps / dt / 1e6, 2), "unit": UNIT, "steps": steps,
+            "h2d_bytes_per_step": n * 13 * 8, "d2h_bytes_per_step": n * 19 * 8,
+            "path": "bl_particles_set(host X,q,V,L) + bl_step(1) + bl_forces_get(host F,T,X,q,V,L)"}
+
+
+def cpu_oracle_step_time(p, X, q, nsteps=1):
+    import oracle
+
+    o = oracle.Oracle(p)
+    o.set_particles(X, q)
+    t0 = time.perf_counter()
+    o.step(nsteps)
+    return (time.perf_counter() - t0) / nsteps
+
+
+def reference_sample(p, X, q, budget_s, nsteps):
+    """largest lateral sub-box of the workload (same height, walls, wall speed,
+    cell shape and volume fraction) whose oracle steps fit the time budget"""
+    from paper_1005_2594_gb300 import workloads
+
+    full = p["nx"] * p["ny"] * p["nz"]
+    # the oracle's re-discretisation visits every node for every cell, so
+    # its step costs ~ N * n_cells (12 s for 128^3 with 1022 cells)
+    t_full = 12.0 * (full / 128 ** 3) * (len(X) / 1022.0)
+    for fx, fy in ((1, 1), (2, 1), (2, 2), (4, 2), (4, 4), (8, 4), (8, 8)):
+        nx, ny = max(p["nx"] // fx, 16), max(p["ny"] // fy, 16)
+        frac = nx * ny / (p["nx"] * p["ny"])
+        if t_full * frac * frac * nsteps <= budget_s or (fx, fy) == (8, 8):
+            break
+    if (nx, ny) == (p["nx"], p["ny"]):
+        return p, X, q, "the full workload"
+    sp = dict(p)
+    sp["nx"], sp["ny"] = nx, ny
+    n = max(1, int(round(len(X) * frac)))
+    sX, sq, _ = workloads.pack_cells(sp, n, 1002)
+    return sp, sX, sq, "%dx%dx%d sub-box of the workload (same walls, wall speed, cells, volume fraction), %d cells" % (
+        nx, ny, p["nz"], n)
+
+
+def run_reference(args, ws, rank):
+    """FP64 CPU oracle on the host cores, bounded sample of the same workload."""
+    if rank != 0:
+        return None
+    import oracle
+
+    p, X, q, _, desc = make_workload(args.config)
+    sp, sX, sq, sample = reference_sample(p, X, q, 150.0, args.steps + args.warmup)
+    o = oracle.Oracle(sp)
+    o.set_particles(sX, sq)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    Ns = sp["nx"] * sp["ny"] * sp["nz"]
+    v = Ns * args.steps / dt / 1e6
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random packing, resting start)",
+            "config": {"workload": desc, "sample": sample},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--config", default="shear128", choices=["shear128", "small32"])
+    ap.add_argument("--store", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+    out, (p, X, q, desc) = run_gpu(args, ws, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline and ws == 1:
+            t = cpu_oracle_step_time(p, X, q, 1)
+            N = p["nx"] * p["ny"] * p["nz"]
+            out["cpu_baseline"] = {"value": round(N / t / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": "1 coupled step of the same workload (FP64 C oracle, 1 thread)"}
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * bloodlb.h -- C ABI of the GB300 (sm_103a) library for the coupled time step
+ * of Janoschek, Toschi & Harting, "A simplified particulate model for
+ * coarse-grained hemodynamics simulations" (arXiv:1005.2594):
+ * a D3Q19 lattice-BGK plasma (Sec. II) with rigid ellipsoidal cells coupled
+ * by moving-boundary bounce-back, fill/drain and contact links (Sec. II), and
+ * Berne-Pechukas-scaled Hookean cell-cell and cell-wall potentials (Sec. III).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Status: every int-returning call returns BL_OK (0) or a negative BL_E*
+ *   code.  Errors are sticky per context: after a failure every later call
+ *   returns the same code until bl_destroy; bl_last_error() names the cause.
+ *   Device-side failures (unstable fluid, list overflow) are raised by the
+ *   kernels into a status word and reported by bl_sync() and by the next
+ *   call that waits on the stream.
+ * Ownership: the library owns all of its device memory (allocated in
+ *   bl_lb_init / bl_particles_set, released by bl_destroy).  Caller pointers
+ *   are borrowed for the duration of the call only.
+ * Streams: every kernel of a context runs on the CUDA stream given to
+ *   bl_lb_init (NULL = the legacy default stream).  A context is not
+ *   thread-safe; use one context per stream.
+ * Lattice: nodes are numbered n = x + nx (y + ny z), x fastest.  A
+ *   non-periodic axis carries solid wall layers at index 0 and N-1; faces
+ *   are numbered x-,x+,y-,y+,z-,z+ = wall ids 0..5.  Owner codes: -1 fluid,
+ *   -2-w wall with id w (0..7), k >= 0 cell k.
+ * Directions: r = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (1,1,0),
+ *   (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1),
+ *   (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1).  Weights 1/3, 1/18, 1/36
+ *   (Sec. II, after Eq. neq).
+ * Cells: X centre, q unit quaternion (w,x,y,z) whose rotation takes e_z to
+ *   the symmetry axis, V linear velocity, L lab-frame angular momentum.
+ *   A time step takes X(t), q(t), V(t-1/2), L(t-1/2) to the next level.
+ * Units: lattice units (dx = dt = 1).
+ */
+#ifndef BLOODLB_H
+#define BLOODLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BL_OK 0
+#define BL_EINVAL (-1)     /* bad argument, size or parameter */
+#define BL_ENOMEM (-2)     /* device allocation failed */
+#define BL_EUNSTABLE (-3)  /* rho <= 0, NaN, or |u| above the Mach guard in a fluid node */
+#define BL_EOVERFLOW (-4)  /* an internal list exceeded its capacity */
+#define BL_EBARRIER (-5)   /* a bounded device-side wait timed out */
+#define BL_ECUDA (-6)      /* a CUDA runtime call failed */
+#define BL_ESTATE (-7)     /* call out of order (e.g. step before particles_set with cells) */
+
+#define BL_STORE_F32 0  /* populations stored as FP32 (shifted by alpha_r rho_bar) */
+#define BL_STORE_BF16 1 /* shifted populations stored as BF16, collided in FP32 */
+#define BL_STORE_F16 2  /* shifted populations stored as FP16 (scaled by 2^10), collided in FP32 */
+
+typedef struct bl_ctx bl_ctx;
+
+/* Lattice and fluid (Sec. II; tau = 1 and rho_bar = 1 in every run of the
+   paper, Sec. IV).  The body force g is an acceleration: force density rho g,
+   applied with the Guo scheme, u = (j + rho g / 2) / rho. */
+typedef struct {
+  int nx, ny, nz;          /* lattice size, each >= 1 */
+  int periodic[3];         /* 1 periodic, 0 wall layers at 0 and N-1 */
+  double wall_vel[8][3];   /* velocity of wall id 0..7 (moving bounce-back, Eq. c) */
+  double tau;              /* BGK relaxation time (Eq. col), > 1/2 */
+  double rho0;             /* rho_bar: initial density, fill density (Sec. II) */
+  double g[3];             /* body-force acceleration on the fluid */
+  int store_dtype;         /* BL_STORE_* */
+  int body_force_on_cells; /* 1: cells also feel m g (tube flow of Sec. IV) */
+} bl_lb_params;
+
+/* Cells (Sec. II fluid coupling, Sec. III potentials).  The strength of the
+   pair potential is eps (1 - chi^2 (o_i.o_j)^2)^(-nu/2) eps2^mu, eps2 being
+   the bracket of Eq. (sigma) with chi_prime; the paper's Berne-Pechukas form
+   is nu = 1, mu = 0. */
+typedef struct {
+  double R_par, R_perp;     /* half-axes of the fluid-coupling ellipsoid */
+  double sig_par, sig_perp; /* half-axes of the potential (Eq. sigma) */
+  double eps, eps_w, sig_w; /* epsbar, epsbar_w, wall sphere radius (1/2) */
+  double mu, nu, chi_prime; /* Gay-Berne exponents of the strength */
+  double r_cut;             /* neighbour-list radius (the potential is compact) */
+  double rho_p;             /* cell density; mass rho_p 4/3 pi R_perp^2 R_par */
+  int move_particles;       /* 0: cells held fixed (forces still computed) */
+  int reserved;
+} bl_particle_params;
+
+/* Creates a context: allocates the population field (19 x N in the storage
+   type, single AA buffer), the owner map, and sets resting fluid
+   n = n^eq(rho_bar, 0) on all non-wall nodes (the paper starts from rest,
+   Sec. IV).  cuda_stream is a cudaStream_t or NULL.  *out receives the
+   context, or NULL on failure (status returned). */
+int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream);
+
+/* Adds static walls: mask is a host array of N bytes; mask[n] = k in 1..8
+   makes node n a wall with id k-1 (0 leaves the node unchanged).  Call
+   before bl_particles_set.  The surface wall nodes (walls linked to a
+   non-wall node, Sec. III) are rebuilt. */
+int bl_walls_set(bl_ctx *c, const uint8_t *mask);
+
+/* Sets the cells: host arrays X (n x 3), q (n x 4), V (n x 3), L (n x 3).
+   The first call (or a call with a different n) discretises from scratch
+   (lowest index wins on overlap), deletes the fluid of covered nodes and
+   gives no impulses.  A later call with the same n re-discretises against
+   the current owner map with the first-arrival rule and fill/drain
+   impulses, exactly as a time step does (Sec. II).  n may be 0. */
+int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, const double *X, const double *q,
+                     const double *V, const double *L);
+
+/* Enqueues nsteps coupled time steps on the context stream (no host sync):
+   collide + stream + bounce-back + momentum exchange + contact links, cell
+   list, pair and wall potentials, leap-frog, re-discretisation with
+   fill/drain.  Returns the sticky status known so far (device errors of
+   this call surface at the next bl_sync). */
+int bl_step(bl_ctx *c, int nsteps);
+
+/* Moments of the current populations: rho (N doubles) and
+   u = (j + rho g / 2) / rho (N x 3 doubles) on fluid nodes, 0 elsewhere;
+   owner (N int32).  Any pointer may be NULL.  on_device = 1: the pointers
+   are device memory (e.g. CUDA tensors) written on the context stream;
+   on_device = 0: host memory, the call waits. */
+int bl_fields_get(bl_ctx *c, double *rho, double *u, int32_t *owner, int on_device);
+
+/* Cell read-out after the last step (host arrays, n x 3 / n x 4, any may be
+   NULL): F, T = total force and torque used by the last integration (links,
+   potentials, fill/drain impulses, body force); X, q, V, L = current state.
+   Waits on the stream. */
+int bl_forces_get(bl_ctx *c, double *F, double *T, double *X, double *q, double *V, double *L);
+
+/* Parts of the last step's force (host, n x 3 each, any may be NULL):
+   Fh/Th link force (bounce-back momentum exchange Eq. deltap plus contact
+   links Eq. deltapppp), Fp/Tp potentials (Eqs. phi-sigmaw), Om angular
+   velocity I_lab^-1 L used for the rotation; PF/PT fill/drain impulses
+   waiting for the next integration. */
+int bl_force_parts_get(bl_ctx *c, double *Fh, double *Th, double *Fp, double *Tp, double *Om, double *PF,
+                       double *PT);
+
+/* Momentum given to each wall id by its bounce-back links, summed over the
+   steps since the previous call (or since bl_lb_init), then reset (8 x 3
+   doubles, host); the momentum-transfer observable of Eq. (mu). */
+int bl_wall_momentum_get(bl_ctx *c, double *wallmom);
+
+/* Checkpoint of the fluid: node-major host array N x 19 doubles, the
+   unshifted populations n_r(x, t) in the direction order above; non-fluid
+   nodes read as 0 and are ignored on set. */
+int bl_populations_get(bl_ctx *c, double *pop);
+int bl_populations_set(bl_ctx *c, const double *pop);
+
+/* Boundary links (fluid node y, direction r with y + c_r solid, owner of
+   y + c_r) and contact links (node x of cell p, r, owner of x + c_r, a wall
+   or another cell) of the current owner map, as int32 triples in (node, r)
+   order, built by warp-level stream compaction.  Writes min(count, cap)
+   triples to the host array out and the full count to *count. */
+int bl_boundary_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count);
+int bl_contact_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count);
+
+/* Cell list of the current positions in canonical (bin, id) order:
+   nb_k = max(1, floor(N_k / r_cut)), bin_k = floor((X_k / N_k) nb_k)
+   clamped; start has nb0 nb1 nb2 + 1 entries, ids n entries (host).
+   Pass start = ids = NULL to query nb only. */
+int bl_cell_list_get(bl_ctx *c, int32_t nb[3], int32_t *start, int32_t *ids);
+
+/* Kernel timing with CUDA events on the context stream.  While enabled,
+   each kernel group of a step is bracketed by an event pair.  Groups:
+   0 fused collide/stream/bounce-back (the lattice sweep), 1 cell list,
+   2 pair + wall potentials, 3 leap-frog + claims, 4 resolve + fill/drain.
+   bl_timing_read waits, then writes per group the summed milliseconds and
+   the number of timed launches (arrays of ngroups), and clears the sums. */
+int bl_timing_enable(bl_ctx *c, int enable);
+int bl_timing_read(bl_ctx *c, double *ms, int64_t *count, int ngroups);
+
+/* Number of kernels this context has launched since bl_lb_init. */
+int64_t bl_launch_count(const bl_ctx *c);
+
+/* Waits for the stream; returns the sticky status including device errors. */
+int bl_sync(bl_ctx *c);
+
+/* Human-readable cause of the sticky error ("" if none). */
+const char *bl_last_error(const bl_ctx *c);
+
+/* Releases all device memory of the context; c may be NULL. */
+void bl_destroy(bl_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLOODLB_H */

@@ -1,0 +1,351 @@
+"""Python binding of the CUDA library ``libbloodlb.so`` (C ABI in
+``include/bloodlb.h``): argument marshalling only.  Every step of the coupled
+time step runs in the library's kernels; there is no CPU fallback, and
+loading fails loudly if the library has not been built.
+
+The functions carry the C names.  Arrays are numpy arrays (host) or CUDA
+tensors (``on_device`` read-outs).  Parameters come as the plain dict of
+``paper_1005_2594_gb300.workloads``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libbloodlb.so")
+
+BL_OK = 0
+BL_EINVAL = -1
+BL_ENOMEM = -2
+BL_EUNSTABLE = -3
+BL_EOVERFLOW = -4
+BL_EBARRIER = -5
+BL_ECUDA = -6
+BL_ESTATE = -7
+
+BL_STORE_F32 = 0
+BL_STORE_BF16 = 1
+BL_STORE_F16 = 2
+
+TIMING_GROUPS = ("lattice_sweep", "cell_list", "potentials", "leapfrog_claims", "resolve_fill")
+
+ABI_FUNCTIONS = (
+    "bl_lb_init", "bl_walls_set", "bl_particles_set", "bl_step", "bl_fields_get", "bl_forces_get",
+    "bl_force_parts_get", "bl_wall_momentum_get", "bl_populations_get", "bl_populations_set",
+    "bl_boundary_links_get", "bl_contact_links_get", "bl_cell_list_get", "bl_timing_enable",
+    "bl_timing_read", "bl_launch_count", "bl_sync", "bl_last_error", "bl_destroy",
+)
+
+
+class BloodLBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("bloodlb error %d: %s" % (code, msg))
+        self.code = code
+
+
+class bl_lb_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("periodic", ctypes.c_int * 3),
+        ("wall_vel", (ctypes.c_double * 3) * 8),
+        ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("g", ctypes.c_double * 3),
+        ("store_dtype", ctypes.c_int),
+        ("body_force_on_cells", ctypes.c_int),
+    ]
+
+
+class bl_particle_params(ctypes.Structure):
+    _fields_ = [
+        ("R_par", ctypes.c_double), ("R_perp", ctypes.c_double),
+        ("sig_par", ctypes.c_double), ("sig_perp", ctypes.c_double),
+        ("eps", ctypes.c_double), ("eps_w", ctypes.c_double), ("sig_w", ctypes.c_double),
+        ("mu", ctypes.c_double), ("nu", ctypes.c_double), ("chi_prime", ctypes.c_double),
+        ("r_cut", ctypes.c_double), ("rho_p", ctypes.c_double),
+        ("move_particles", ctypes.c_int), ("reserved", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("CUDA library %s is not built; run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, D, I = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    i64 = ctypes.c_int64
+    sig = {
+        "bl_lb_init": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(bl_lb_params), vp]),
+        "bl_walls_set": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint8)]),
+        "bl_particles_set": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(bl_particle_params), D, D, D, D]),
+        "bl_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "bl_fields_get": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
+        "bl_forces_get": (ctypes.c_int, [vp, D, D, D, D, D, D]),
+        "bl_force_parts_get": (ctypes.c_int, [vp, D, D, D, D, D, D, D]),
+        "bl_wall_momentum_get": (ctypes.c_int, [vp, D]),
+        "bl_populations_get": (ctypes.c_int, [vp, D]),
+        "bl_populations_set": (ctypes.c_int, [vp, D]),
+        "bl_boundary_links_get": (ctypes.c_int, [vp, I, i64, ctypes.POINTER(i64)]),
+        "bl_contact_links_get": (ctypes.c_int, [vp, I, i64, ctypes.POINTER(i64)]),
+        "bl_cell_list_get": (ctypes.c_int, [vp, I, I, I]),
+        "bl_timing_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+        "bl_timing_read": (ctypes.c_int, [vp, D, ctypes.POINTER(i64), ctypes.c_int]),
+        "bl_launch_count": (i64, [vp]),
+        "bl_sync": (ctypes.c_int, [vp]),
+        "bl_last_error": (ctypes.c_char_p, [vp]),
+        "bl_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def lb_params(d: dict, store_dtype=BL_STORE_F32) -> bl_lb_params:
+    p = bl_lb_params()
+    p.nx, p.ny, p.nz = int(d["nx"]), int(d["ny"]), int(d["nz"])
+    wv = np.zeros((8, 3))
+    given = np.asarray(d.get("wall_vel", np.zeros((8, 3))), dtype=np.float64)
+    wv[: given.shape[0]] = given
+    for k in range(3):
+        p.periodic[k] = int(d["periodic"][k])
+        p.g[k] = float(d.get("g", (0.0, 0.0, 0.0))[k])
+    for w in range(8):
+        for k in range(3):
+            p.wall_vel[w][k] = float(wv[w, k])
+    p.tau = float(d.get("tau", 1.0))
+    p.rho0 = float(d.get("rho0", 1.0))
+    p.store_dtype = int(store_dtype)
+    p.body_force_on_cells = int(d.get("body_force_on_cells", 0))
+    return p
+
+
+def particle_params(d: dict) -> bl_particle_params:
+    p = bl_particle_params()
+    for key in ("R_par", "R_perp", "sig_par", "sig_perp", "eps", "eps_w", "sig_w", "mu", "nu", "chi_prime",
+                "r_cut", "rho_p"):
+        setattr(p, key, float(d.get(key, 0.0)))
+    p.move_particles = int(d.get("move_particles", 1))
+    return p
+
+
+def _check(ctx, rc):
+    if rc != BL_OK:
+        msg = lib().bl_last_error(ctx)
+        raise BloodLBError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# --- the C functions, one to one -------------------------------------------
+
+
+def bl_lb_init(params: dict, stream=None, store_dtype=BL_STORE_F32):
+    ctx = ctypes.c_void_p()
+    p = lb_params(params, store_dtype)
+    rc = lib().bl_lb_init(ctypes.byref(ctx), ctypes.byref(p), ctypes.c_void_p(stream or 0))
+    if rc != BL_OK:
+        raise BloodLBError(rc, "bl_lb_init")
+    return ctx
+
+
+def bl_walls_set(ctx, mask):
+    m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    return _check(ctx, lib().bl_walls_set(ctx, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+
+def bl_particles_set(ctx, params: dict, X, q, V=None, L=None):
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+    n = X.shape[0]
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(n, 4)
+    V = np.zeros((n, 3)) if V is None else np.ascontiguousarray(V, dtype=np.float64).reshape(n, 3)
+    L = np.zeros((n, 3)) if L is None else np.ascontiguousarray(L, dtype=np.float64).reshape(n, 3)
+    pp = particle_params(params)
+    return _check(ctx, lib().bl_particles_set(ctx, n, ctypes.byref(pp), _dp(X), _dp(q), _dp(V), _dp(L)))
+
+
+def bl_step(ctx, nsteps=1):
+    return _check(ctx, lib().bl_step(ctx, int(nsteps)))
+
+
+def bl_sync(ctx):
+    return _check(ctx, lib().bl_sync(ctx))
+
+
+def bl_fields_get(ctx, N, rho=None, u=None, owner=None, on_device=False):
+    """Host: returns (rho, u, owner) numpy arrays.  Device: pass CUDA tensors
+    (float64 N, float64 N x 3, int32 N) and they are written on the stream."""
+    if on_device:
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+        _check(ctx, lib().bl_fields_get(ctx, ptr(rho), ptr(u), ptr(owner), 1))
+        return rho, u, owner
+    rho = np.zeros(N)
+    u = np.zeros((N, 3))
+    owner = np.zeros(N, dtype=np.int32)
+    _check(ctx, lib().bl_fields_get(ctx, ctypes.c_void_p(rho.ctypes.data), ctypes.c_void_p(u.ctypes.data),
+                                    ctypes.c_void_p(owner.ctypes.data), 0))
+    return rho, u, owner
+
+
+def bl_forces_get(ctx, n):
+    out = {k: np.zeros((n, 3)) for k in ("F", "T", "X", "V", "L")}
+    out["q"] = np.zeros((n, 4))
+    _check(ctx, lib().bl_forces_get(ctx, _dp(out["F"]), _dp(out["T"]), _dp(out["X"]), _dp(out["q"]),
+                                    _dp(out["V"]), _dp(out["L"])))
+    return out
+
+
+def bl_force_parts_get(ctx, n):
+    keys = ("Fh", "Th", "Fp", "Tp", "Om", "PF", "PT")
+    out = {k: np.zeros((n, 3)) for k in keys}
+    _check(ctx, lib().bl_force_parts_get(ctx, *(_dp(out[k]) for k in keys)))
+    return out
+
+
+def bl_wall_momentum_get(ctx):
+    out = np.zeros((8, 3))
+    _check(ctx, lib().bl_wall_momentum_get(ctx, _dp(out)))
+    return out
+
+
+def bl_populations_get(ctx, N):
+    pop = np.zeros((N, 19))
+    _check(ctx, lib().bl_populations_get(ctx, _dp(pop)))
+    return pop
+
+
+def bl_populations_set(ctx, pop):
+    pop = np.ascontiguousarray(pop, dtype=np.float64)
+    return _check(ctx, lib().bl_populations_set(ctx, _dp(pop)))
+
+
+def _links(fn, ctx):
+    cnt = ctypes.c_int64(0)
+    _check(ctx, fn(ctx, None, 0, ctypes.byref(cnt)))
+    out = np.zeros((max(cnt.value, 1), 3), dtype=np.int32)
+    _check(ctx, fn(ctx, _ip(out), cnt.value, ctypes.byref(cnt)))
+    return out[: cnt.value]
+
+
+def bl_boundary_links_get(ctx):
+    return _links(lib().bl_boundary_links_get, ctx)
+
+
+def bl_contact_links_get(ctx):
+    return _links(lib().bl_contact_links_get, ctx)
+
+
+def bl_cell_list_get(ctx, n):
+    nb = np.zeros(3, dtype=np.int32)
+    _check(ctx, lib().bl_cell_list_get(ctx, _ip(nb), None, None))
+    start = np.zeros(int(np.prod(nb)) + 1, dtype=np.int32)
+    ids = np.zeros(max(n, 1), dtype=np.int32)
+    _check(ctx, lib().bl_cell_list_get(ctx, _ip(nb), _ip(start), _ip(ids)))
+    return nb, start, ids[:n]
+
+
+def bl_timing_enable(ctx, enable=True):
+    return _check(ctx, lib().bl_timing_enable(ctx, 1 if enable else 0))
+
+
+def bl_timing_read(ctx):
+    n = len(TIMING_GROUPS)
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    _check(ctx, lib().bl_timing_read(ctx, _dp(ms), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n))
+    return {g: (ms[i], int(cnt[i])) for i, g in enumerate(TIMING_GROUPS)}
+
+
+def bl_launch_count(ctx):
+    return int(lib().bl_launch_count(ctx))
+
+
+def bl_last_error(ctx):
+    m = lib().bl_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def bl_destroy(ctx):
+    if ctx:
+        lib().bl_destroy(ctx)
+
+
+# --- convenience wrapper ------------------------------------------------------
+
+
+class Simulation:
+    """One lattice with its cells on the GPU (owns one library context)."""
+
+    def __init__(self, params: dict, store_dtype=BL_STORE_F32, stream=None, wall_mask=None):
+        self.params = dict(params)
+        self.N = int(params["nx"]) * int(params["ny"]) * int(params["nz"])
+        self.ctx = bl_lb_init(params, stream=stream, store_dtype=store_dtype)
+        self.n = 0
+        if wall_mask is not None:
+            bl_walls_set(self.ctx, wall_mask)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            bl_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_particles(self, X, q, V=None, L=None):
+        bl_particles_set(self.ctx, self.params, X, q, V, L)
+        self.n = np.asarray(X).reshape(-1, 3).shape[0]
+
+    def step(self, n=1):
+        bl_step(self.ctx, n)
+
+    def sync(self):
+        bl_sync(self.ctx)
+
+    def fields(self):
+        return bl_fields_get(self.ctx, self.N)
+
+    def owner(self):
+        return self.fields()[2]
+
+    def particles(self):
+        return bl_forces_get(self.ctx, self.n)
+
+    def force_parts(self):
+        return bl_force_parts_get(self.ctx, self.n)
+
+    def populations(self):
+        return bl_populations_get(self.ctx, self.N)
+
+    def set_populations(self, pop):
+        bl_populations_set(self.ctx, pop)
+
+    def boundary_links(self):
+        return bl_boundary_links_get(self.ctx)
+
+    def contact_links(self):
+        return bl_contact_links_get(self.ctx)
+
+    def cell_list(self):
+        return bl_cell_list_get(self.ctx, self.n)
+
+    def wall_momentum(self):
+        return bl_wall_momentum_get(self.ctx)

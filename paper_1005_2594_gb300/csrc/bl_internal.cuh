@@ -1,0 +1,234 @@
+// bl_internal.cuh -- device-side definitions shared by the library's kernels.
+//
+// The method is the coupled step of arXiv:1005.2594 (Sec. II, III); this file
+// holds only lattice constants, the views passed to kernels and small device
+// helpers.  Nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace bl {
+
+constexpr int Q = 19;
+constexpr int FLUID = -1;
+constexpr int NWALL = 8;
+
+// D3Q19 in the interface order (Sec. II): rest, 6 axis vectors, 12 diagonals,
+// each followed by its opposite.  m = 36 alpha (alpha = 1/3, 1/18, 1/36).
+struct D3Q19 {
+  static __host__ __device__ constexpr int cx(int r) {
+    return (r == 1 || r == 7 || r == 9 || r == 11 || r == 13) ? 1 : ((r == 2 || r == 8 || r == 10 || r == 12 || r == 14) ? -1 : 0);
+  }
+  static __host__ __device__ constexpr int cy(int r) {
+    return (r == 3 || r == 7 || r == 10 || r == 15 || r == 17) ? 1 : ((r == 4 || r == 8 || r == 9 || r == 16 || r == 18) ? -1 : 0);
+  }
+  static __host__ __device__ constexpr int cz(int r) {
+    return (r == 5 || r == 11 || r == 14 || r == 15 || r == 18) ? 1 : ((r == 6 || r == 12 || r == 13 || r == 16 || r == 17) ? -1 : 0);
+  }
+  static __host__ __device__ constexpr int opp(int r) { return r == 0 ? 0 : ((r & 1) ? r + 1 : r - 1); }
+  static __host__ __device__ constexpr int m(int r) { return r == 0 ? 12 : (r <= 6 ? 2 : 1); }
+};
+
+// compile-time loop: f(std::integral_constant<int, I>) for I in [B, E)
+template <int B, int E, class F>
+__device__ __forceinline__ void sfor(F &&f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    sfor<B + 1, E>(f);
+  }
+}
+
+// storage of the shifted populations f~ = f - alpha rho_bar
+template <class S>
+struct Store;
+template <>
+struct Store<float> {
+  static __device__ __forceinline__ float ld(const float *p) { return *p; }
+  static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+// FP16 stores f~ scaled by 2^10 so that small deviations stay in the normal range
+template <>
+struct Store<__half> {
+  static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p) * (1.0f / 1024.0f); }
+  static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v * 1024.0f); }
+};
+
+struct LatticeView {
+  int nx, ny, nz;
+  int per[3];
+  unsigned N;  // nodes; 19 N < 2^32 is checked on the host
+  float wall_vel[NWALL][3];
+  float omega;  // 1 / tau
+  float rho0;
+  float g[3];
+  int has_force;
+  void *pop;       // 19 x N storage elements, slot r of node n at r * N + n
+  int32_t *owner;  // N
+};
+
+// per-cell kinematics for the lattice sweep, three float4 per cell:
+//   [0] = (f.x, f.y, f.z, Xi.x)   X = Xi + f, Xi = rint(X) (exact integer)
+//   [1] = (V.x, V.y, V.z, Xi.y)
+//   [2] = (W.x, W.y, W.z, Xi.z)   W = angular velocity
+// link-force accumulators: the variable part of the momentum exchange in
+// FP64 (accF, accT) and the constant part 2 alpha rho_bar c_r as exact
+// integers: K = sum m_r c_r, IT = sum m_r (dI x c_r), dI = x - Xi.
+struct PartAcc {
+  double *F;  // n x 3
+  double *T;  // n x 3
+  int *K;     // n x 3
+  int *IT;    // n x 3
+};
+
+struct WallAcc {
+  double *F;     // 8 x 3
+  long long *K;  // 8 x 3
+};
+
+// cell bounce links of one sweep, compacted per warp: fluid node, (cell << 5)
+// | direction (towards the cell), local density of the node
+struct LinkList {
+  int *count;
+  uint32_t *node;
+  uint32_t *pr;
+  float *rho;
+  int cap;
+};
+
+struct PartView {
+  int n;
+  double *X, *q, *V, *L, *Om;
+  double *o;        // exact FP64 symmetry axis of the current q, n x 3
+  float4 *kin;      // lattice-sweep kinematics of the current step, 3 float4 per cell
+  float4 *kin_next; // kinematics written for the next step
+  double *zeta;     // n x 21 drag matrices of the bounce links (FF 6, FT 9, TT 6)
+  float *dvel;      // n x 6 velocity increment (dV, dOmega) of the implicit solve
+  PartAcc acc;
+  double *Fpot, *Tpot;                // potentials of the current step
+  double *PF, *PT;                    // pending fill/drain impulses
+  double *Flink, *Tlink, *Ftot, *Ttot; // read-out of the last step
+  int *box;                           // n x 6 inclusive node box lo[3], hi[3]
+  double *stage;                      // n x 13 staged state for particles_set
+  int *status;                        // device status word (ST_* bits)
+  double m, Iperp, Ipar, rho0;
+  double g[3];
+  int bfc, move;
+  double inv_rpar2, inv_rperp2, R_par, R_perp;
+  float sig_par, sig_perp, eps, eps_w, mu, nu, chi_prime, r_cut;
+  float chi, sigbar, sigbar_w, chi_w, sigw_max;
+};
+
+struct CellListView {
+  int nb[3];
+  int nbins;
+  int *bin_of, *count, *start, *cursor, *ids;
+};
+
+struct WallRows {
+  int *row_start;  // ny nz + 1
+  int *row_x;      // sorted x of the surface wall nodes of each row
+};
+
+struct ChangeList {
+  int *count;
+  int32_t *items;  // triples (node, old, new)
+  int cap;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (each adds the number of kernels it launched to *nl where given)
+
+void launch_lb_step(int dtype, const LatticeView &lv, int par, const float4 *kin, const PartAcc &pa,
+                    const WallAcc &wa, const LinkList &ll, int *status, cudaStream_t st);
+void launch_link_zeta(const LatticeView &lv, const PartView &pv, const LinkList &ll, cudaStream_t st, int64_t *nl);
+void launch_link_correct(int dtype, const LatticeView &lv, int par, const PartView &pv, const LinkList &ll,
+                         cudaStream_t st, int64_t *nl);
+void launch_fields(int dtype, const LatticeView &lv, int par, double *rho, double *u, int32_t *owner,
+                   cudaStream_t st);
+void launch_pop_io(int dtype, const LatticeView &lv, int par, double *buf, int to_storage, cudaStream_t st);
+void launch_init(int dtype, const LatticeView &lv, cudaStream_t st);
+void launch_fill_int(int *a, unsigned n, int v, cudaStream_t st);
+void launch_apply_wall_mask(const LatticeView &lv, const uint8_t *mask, cudaStream_t st);
+void launch_surface_rows(const LatticeView &lv, int *row_count, int *row_x, const int *row_start, cudaStream_t st);
+unsigned links_blocks(const LatticeView &lv);
+void launch_links(const LatticeView &lv, int contact, int pass, int *block_count, const int *block_off, int32_t *out,
+                  long long cap, cudaStream_t st);
+void launch_cell_list(const LatticeView &lv, const PartView &pv, const CellListView &cl, cudaStream_t st, int64_t *nl);
+void launch_forces(const LatticeView &lv, const PartView &pv, const CellListView &cl, const WallRows &wr,
+                   cudaStream_t st, int64_t *nl);
+void launch_integrate_claim(const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg, int mode,
+                            cudaStream_t st, int64_t *nl);
+void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg,
+                         const LinkList &ll, int par_next, int impulses, cudaStream_t st, int64_t *nl);
+void launch_clear_cells(int dtype, const LatticeView &lv, int par, cudaStream_t st, int64_t *nl);
+
+// bit flags of the device status word
+constexpr int ST_UNSTABLE = 1;
+constexpr int ST_OVERFLOW = 2;
+
+// ---------------------------------------------------------------------------
+// exact FP64 geometry (no contraction), matching the operation order of the
+// plain reference so that inside decisions agree bit for bit
+
+__device__ __forceinline__ void axis_exact(const double *q, double *o) {
+  o[0] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(q[1], q[3]), __dmul_rn(q[0], q[2])));
+  o[1] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(q[2], q[3]), __dmul_rn(q[0], q[1])));
+  o[2] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(q[1], q[1]), __dmul_rn(q[2], q[2]))));
+}
+
+__device__ __forceinline__ double min_image_exact(double d, int n, int per) {
+  if (!per) return d;
+  double half = __dmul_rn(0.5, (double)n);
+  if (d > half) return __dsub_rn(d, (double)n);
+  if (d < -half) return __dadd_rn(d, (double)n);
+  return d;
+}
+
+__device__ __forceinline__ bool inside_exact(int x, int y, int z, const double *X, const double *o,
+                                             double inv_rpar2, double inv_rperp2, const LatticeView &lv) {
+  double d0 = min_image_exact(__dsub_rn((double)x, X[0]), lv.nx, lv.per[0]);
+  double d1 = min_image_exact(__dsub_rn((double)y, X[1]), lv.ny, lv.per[1]);
+  double d2 = min_image_exact(__dsub_rn((double)z, X[2]), lv.nz, lv.per[2]);
+  double dpar = __dadd_rn(__dadd_rn(__dmul_rn(d0, o[0]), __dmul_rn(d1, o[1])), __dmul_rn(d2, o[2]));
+  double dd = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+  double pp = __dmul_rn(dpar, dpar);
+  double s = __dadd_rn(__dmul_rn(pp, inv_rpar2), __dmul_rn(__dsub_rn(dd, pp), inv_rperp2));
+  return s <= 1.0;
+}
+
+// integer minimum image of a lattice displacement
+__device__ __forceinline__ int imin_image(int d, int n, int per) {
+  if (!per) return d;
+  if (2 * d > n) return d - n;
+  if (2 * d < -n) return d + n;
+  return d;
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace bl

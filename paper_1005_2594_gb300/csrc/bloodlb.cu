@@ -1,0 +1,663 @@
+// bloodlb.cu -- host side of the C ABI declared in include/bloodlb.h.
+//
+// One context owns one lattice and its cells on one CUDA stream.  A time step
+// (arXiv:1005.2594, Sec. II and III) is enqueued as five kernel groups:
+//   0  fused collide / stream / bounce-back / momentum exchange / contact links
+//   1  cell list (count, scan, scatter, per-bin sort)
+//   2  pair and wall potentials
+//   3  leap-frog + ownership claims
+//   4  resolve + fill/drain
+// The host never waits inside bl_step; device failures are raised into a
+// status word that bl_sync reads.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <climits>
+#include <utility>
+#include <vector>
+
+#include "../../include/bloodlb.h"
+#include "bl_internal.cuh"
+
+using namespace bl;
+
+namespace {
+constexpr int NGROUPS = 5;
+constexpr int MAX_TIMED = 1 << 16;
+}  // namespace
+
+struct bl_ctx {
+  bl_lb_params lp;
+  bl_particle_params pp;
+  cudaStream_t stream;
+  int dtype;
+  int parity;  // layout of the current populations (next step's parity)
+  LatticeView lv;
+  int *claim;
+  int *status;
+  int sticky;
+  char err[256];
+  int64_t launches;
+  // walls
+  WallAcc wacc;
+  WallRows wrows;
+  int *row_count_dev;
+  // cells
+  int np;
+  PartView pv;
+  CellListView cl;
+  ChangeList chg;
+  LinkList links;
+  // scratch for read-outs
+  double *scratch;
+  size_t scratch_bytes;
+  // timing
+  int timing;
+  std::vector<cudaEvent_t> ev;  // pairs
+  std::vector<int> ev_group;
+  int ev_used;
+  double t_ms[NGROUPS];
+  int64_t t_cnt[NGROUPS];
+};
+
+static int fail(bl_ctx *c, int code, const char *fmt, ...) {
+  if (c && c->sticky == BL_OK) {
+    c->sticky = code;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CU(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? BL_ENOMEM : BL_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+  } while (0)
+
+static int check_launch(bl_ctx *c, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, BL_ECUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+  return BL_OK;
+}
+
+static size_t elem_size(int dtype) { return dtype == BL_STORE_F32 ? 4 : 2; }
+
+static int ensure_scratch(bl_ctx *c, size_t bytes) {
+  if (c->scratch_bytes >= bytes) return BL_OK;
+  if (c->scratch) cudaFree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_bytes = 0;
+  CU(cudaMalloc(&c->scratch, bytes));
+  c->scratch_bytes = bytes;
+  return BL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// timing
+
+static void group_begin(bl_ctx *c, int g, int *slot) {
+  *slot = -1;
+  if (!c->timing || c->ev_used >= MAX_TIMED) return;
+  const int s = c->ev_used++;
+  if ((int)c->ev.size() < 2 * (s + 1)) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+    c->ev.push_back(a);
+    c->ev.push_back(b);
+    c->ev_group.push_back(g);
+  }
+  c->ev_group[s] = g;
+  cudaEventRecord(c->ev[2 * s], c->stream);
+  *slot = s;
+}
+
+static void group_end(bl_ctx *c, int slot) {
+  if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], c->stream);
+}
+
+static int harvest_timing(bl_ctx *c) {
+  if (c->ev_used == 0) return BL_OK;
+  CU(cudaStreamSynchronize(c->stream));
+  for (int s = 0; s < c->ev_used; ++s) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[2 * s], c->ev[2 * s + 1]) == cudaSuccess) {
+      c->t_ms[c->ev_group[s]] += ms;
+      c->t_cnt[c->ev_group[s]] += 1;
+    }
+  }
+  c->ev_used = 0;
+  return BL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// surface wall rows (Sec. III: wall spheres at wall nodes linked to the lumen)
+
+static int build_wall_rows(bl_ctx *c) {
+  const int rows = c->lv.ny * c->lv.nz;
+  if (c->wrows.row_start) cudaFree(c->wrows.row_start);
+  if (c->wrows.row_x) cudaFree(c->wrows.row_x);
+  c->wrows.row_start = nullptr;
+  c->wrows.row_x = nullptr;
+  if (!c->row_count_dev) CU(cudaMalloc(&c->row_count_dev, sizeof(int) * rows));
+  launch_surface_rows(c->lv, c->row_count_dev, nullptr, nullptr, c->stream);
+  c->launches++;
+  if (check_launch(c, "surface rows count")) return c->sticky;
+  std::vector<int> cnt(rows), start(rows + 1);
+  CU(cudaMemcpyAsync(cnt.data(), c->row_count_dev, sizeof(int) * rows, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  long long tot = 0;
+  for (int r = 0; r < rows; ++r) {
+    start[r] = (int)tot;
+    tot += cnt[r];
+  }
+  start[rows] = (int)tot;
+  if (tot == 0) return BL_OK;  // no walls: the wall potential is skipped
+  CU(cudaMalloc(&c->wrows.row_start, sizeof(int) * (rows + 1)));
+  CU(cudaMalloc(&c->wrows.row_x, sizeof(int) * tot));
+  CU(cudaMemcpyAsync(c->wrows.row_start, start.data(), sizeof(int) * (rows + 1), cudaMemcpyHostToDevice, c->stream));
+  launch_surface_rows(c->lv, nullptr, c->wrows.row_x, c->wrows.row_start, c->stream);
+  c->launches++;
+  if (check_launch(c, "surface rows fill")) return c->sticky;
+  CU(cudaStreamSynchronize(c->stream));
+  return BL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream) {
+  if (!out) return BL_EINVAL;
+  *out = nullptr;
+  if (!p) return BL_EINVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || !(p->tau > 0.5) || !(p->rho0 > 0.0) || p->store_dtype < 0 ||
+      p->store_dtype > 2)
+    return BL_EINVAL;
+  const unsigned long long N = (unsigned long long)p->nx * p->ny * p->nz;
+  if (N * bl::Q >= (1ull << 32) || p->nx >= (1 << 24) || p->ny >= (1 << 24) || p->nz >= (1 << 24)) return BL_EINVAL;
+  for (int k = 0; k < 3; ++k) {
+    const int n = k == 0 ? p->nx : (k == 1 ? p->ny : p->nz);
+    if (!p->periodic[k] && n < 3) return BL_EINVAL;  // two wall layers and fluid between
+  }
+  bl_ctx *c = new bl_ctx();
+  memset(c->err, 0, sizeof(c->err));
+  c->lp = *p;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->dtype = p->store_dtype;
+  c->parity = 0;
+  c->sticky = BL_OK;
+  LatticeView &lv = c->lv;
+  lv.nx = p->nx;
+  lv.ny = p->ny;
+  lv.nz = p->nz;
+  for (int k = 0; k < 3; ++k) lv.per[k] = p->periodic[k] ? 1 : 0;
+  lv.N = (unsigned)N;
+  for (int w = 0; w < bl::NWALL; ++w)
+    for (int k = 0; k < 3; ++k) lv.wall_vel[w][k] = (float)p->wall_vel[w][k];
+  lv.omega = (float)(1.0 / p->tau);
+  lv.rho0 = (float)p->rho0;
+  lv.has_force = 0;
+  for (int k = 0; k < 3; ++k) {
+    lv.g[k] = (float)p->g[k];
+    if (p->g[k] != 0.0) lv.has_force = 1;
+  }
+  int rc = BL_OK;
+  do {
+    if (cudaMalloc(&lv.pop, elem_size(c->dtype) * N * bl::Q) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "population field"); break; }
+    if (cudaMalloc(&lv.owner, sizeof(int32_t) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "owner map"); break; }
+    if (cudaMalloc(&c->claim, sizeof(int) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "claim map"); break; }
+    if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "status"); break; }
+    if (cudaMalloc(&c->wacc.F, sizeof(double) * bl::NWALL * 3) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "wall"); break; }
+    if (cudaMalloc(&c->wacc.K, sizeof(long long) * bl::NWALL * 3) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "wall"); break; }
+    cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    cudaMemsetAsync(c->wacc.F, 0, sizeof(double) * bl::NWALL * 3, c->stream);
+    cudaMemsetAsync(c->wacc.K, 0, sizeof(long long) * bl::NWALL * 3, c->stream);
+    launch_init(c->dtype, lv, c->stream);
+    launch_fill_int(c->claim, lv.N, INT_MAX, c->stream);
+    c->launches += 2;
+    if ((rc = check_launch(c, "init")) != BL_OK) break;
+    if ((rc = build_wall_rows(c)) != BL_OK) break;
+  } while (0);
+  if (rc != BL_OK) {
+    bl_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return BL_OK;
+}
+
+extern "C" int bl_walls_set(bl_ctx *c, const uint8_t *mask) {
+  if (!c || !mask) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (c->np > 0) return fail(c, BL_ESTATE, "bl_walls_set after bl_particles_set");
+  for (size_t i = 0; i < c->lv.N; ++i)
+    if (mask[i] > bl::NWALL) return fail(c, BL_EINVAL, "wall mask value %d > 8 at node %zu", (int)mask[i], i);
+  uint8_t *d = nullptr;
+  CU(cudaMalloc(&d, c->lv.N));
+  CU(cudaMemcpyAsync(d, mask, c->lv.N, cudaMemcpyHostToDevice, c->stream));
+  launch_apply_wall_mask(c->lv, d, c->stream);
+  c->launches++;
+  int rc = check_launch(c, "wall mask");
+  cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  if (rc) return rc;
+  return build_wall_rows(c);
+}
+
+static void free_particles(bl_ctx *c) {
+  PartView &pv = c->pv;
+  void *ptrs[] = {pv.X, pv.q, pv.V, pv.L, pv.Om, pv.o, pv.kin, pv.acc.F, pv.acc.T, pv.acc.K, pv.acc.IT,
+                  pv.Fpot, pv.Tpot, pv.PF, pv.PT, pv.Flink, pv.Tlink, pv.Ftot, pv.Ttot, pv.box, pv.stage,
+                  c->cl.bin_of, c->cl.count, c->cl.start, c->cl.cursor, c->cl.ids, c->chg.count, c->chg.items,
+                  pv.kin_next, pv.zeta, pv.dvel, c->links.count, c->links.node, c->links.pr, c->links.rho};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  memset(&c->pv, 0, sizeof(c->pv));
+  memset(&c->cl, 0, sizeof(c->cl));
+  memset(&c->chg, 0, sizeof(c->chg));
+  memset(&c->links, 0, sizeof(c->links));
+  c->np = 0;
+}
+
+static int alloc_particles(bl_ctx *c, int n) {
+  PartView &pv = c->pv;
+  const size_t n3 = sizeof(double) * 3 * (size_t)n;
+  CU(cudaMalloc(&pv.X, n3));
+  CU(cudaMalloc(&pv.q, sizeof(double) * 4 * (size_t)n));
+  CU(cudaMalloc(&pv.V, n3));
+  CU(cudaMalloc(&pv.L, n3));
+  CU(cudaMalloc(&pv.Om, n3));
+  CU(cudaMalloc(&pv.o, n3));
+  CU(cudaMalloc(&pv.kin, sizeof(float4) * 3 * (size_t)n));
+  CU(cudaMalloc(&pv.kin_next, sizeof(float4) * 3 * (size_t)n));
+  CU(cudaMalloc(&pv.zeta, sizeof(double) * 21 * (size_t)n));
+  CU(cudaMalloc(&pv.dvel, sizeof(float) * 6 * (size_t)n));
+  CU(cudaMemsetAsync(pv.zeta, 0, sizeof(double) * 21 * (size_t)n, c->stream));
+  CU(cudaMemsetAsync(pv.dvel, 0, sizeof(float) * 6 * (size_t)n, c->stream));
+  CU(cudaMalloc(&pv.acc.F, n3));
+  CU(cudaMalloc(&pv.acc.T, n3));
+  CU(cudaMalloc(&pv.acc.K, sizeof(int) * 3 * (size_t)n));
+  CU(cudaMalloc(&pv.acc.IT, sizeof(int) * 3 * (size_t)n));
+  CU(cudaMalloc(&pv.Fpot, n3));
+  CU(cudaMalloc(&pv.Tpot, n3));
+  CU(cudaMalloc(&pv.PF, n3));
+  CU(cudaMalloc(&pv.PT, n3));
+  CU(cudaMalloc(&pv.Flink, n3));
+  CU(cudaMalloc(&pv.Tlink, n3));
+  CU(cudaMalloc(&pv.Ftot, n3));
+  CU(cudaMalloc(&pv.Ttot, n3));
+  CU(cudaMalloc(&pv.box, sizeof(int) * 6 * (size_t)n));
+  CU(cudaMalloc(&pv.stage, sizeof(double) * 13 * (size_t)n));
+  double *zero3[] = {pv.X, pv.V, pv.L, pv.Om, pv.o, pv.acc.F, pv.acc.T, pv.Fpot, pv.Tpot,
+                     pv.PF, pv.PT, pv.Flink, pv.Tlink, pv.Ftot, pv.Ttot};
+  for (double *z : zero3) CU(cudaMemsetAsync(z, 0, n3, c->stream));
+  CU(cudaMemsetAsync(pv.q, 0, sizeof(double) * 4 * (size_t)n, c->stream));
+  CU(cudaMemsetAsync(pv.kin, 0, sizeof(float4) * 3 * (size_t)n, c->stream));
+  CU(cudaMemsetAsync(pv.kin_next, 0, sizeof(float4) * 3 * (size_t)n, c->stream));
+  CU(cudaMemsetAsync(pv.acc.K, 0, sizeof(int) * 3 * (size_t)n, c->stream));
+  CU(cudaMemsetAsync(pv.acc.IT, 0, sizeof(int) * 3 * (size_t)n, c->stream));
+  // cell list bins: nb_k = max(1, floor(N_k / r_cut))
+  const int dims[3] = {c->lv.nx, c->lv.ny, c->lv.nz};
+  long long nbins = 1;
+  for (int k = 0; k < 3; ++k) {
+    int nb = (int)floor((double)dims[k] / c->pp.r_cut);
+    if (nb < 1) nb = 1;
+    c->cl.nb[k] = nb;
+    nbins *= nb;
+  }
+  if (nbins > (1 << 26)) return fail(c, BL_EINVAL, "r_cut gives too many bins");
+  c->cl.nbins = (int)nbins;
+  CU(cudaMalloc(&c->cl.bin_of, sizeof(int) * (size_t)n));
+  CU(cudaMalloc(&c->cl.count, sizeof(int) * (size_t)nbins));
+  CU(cudaMalloc(&c->cl.cursor, sizeof(int) * (size_t)nbins));
+  CU(cudaMalloc(&c->cl.start, sizeof(int) * (size_t)(nbins + 1)));
+  CU(cudaMalloc(&c->cl.ids, sizeof(int) * (size_t)n));
+  CU(cudaMemsetAsync(c->cl.count, 0, sizeof(int) * (size_t)nbins, c->stream));
+  CU(cudaMemsetAsync(c->cl.cursor, 0, sizeof(int) * (size_t)nbins, c->stream));
+  // diagnostic list of changed nodes (overflow only truncates the list)
+  c->chg.cap = 64 * n + 4096;
+  CU(cudaMalloc(&c->chg.count, sizeof(int)));
+  CU(cudaMalloc(&c->chg.items, sizeof(int32_t) * 3 * (size_t)c->chg.cap));
+  CU(cudaMemsetAsync(c->chg.count, 0, sizeof(int), c->stream));
+  // bounce links of one sweep: at most ~6 per node of a shell of radius
+  // max(R) around each cell, and never more than 18 per lattice node
+  {
+    const double rmax = fmax(c->pp.R_par, c->pp.R_perp) + 1.0;
+    double cap = 6.0 * 4.0 * M_PI * rmax * rmax * (double)n + 4096.0;
+    if (cap > 18.0 * (double)c->lv.N) cap = 18.0 * (double)c->lv.N;
+    if (cap > 1.5e9) return fail(c, BL_EINVAL, "link list too large");
+    c->links.cap = (int)cap;
+    CU(cudaMalloc(&c->links.count, sizeof(int)));
+    CU(cudaMalloc(&c->links.node, sizeof(uint32_t) * (size_t)c->links.cap));
+    CU(cudaMalloc(&c->links.pr, sizeof(uint32_t) * (size_t)c->links.cap));
+    CU(cudaMalloc(&c->links.rho, sizeof(float) * (size_t)c->links.cap));
+    CU(cudaMemsetAsync(c->links.count, 0, sizeof(int), c->stream));
+  }
+  c->np = n;
+  pv.n = n;
+  return BL_OK;
+}
+
+static void fill_particle_constants(bl_ctx *c) {
+  const bl_particle_params &pp = c->pp;
+  PartView &pv = c->pv;
+  const double m = pp.rho_p * (4.0 / 3.0) * M_PI * pp.R_perp * pp.R_perp * pp.R_par;
+  pv.m = m;
+  pv.Iperp = m * (pp.R_par * pp.R_par + pp.R_perp * pp.R_perp) / 5.0;
+  pv.Ipar = 2.0 * m * pp.R_perp * pp.R_perp / 5.0;
+  pv.rho0 = c->lp.rho0;
+  for (int k = 0; k < 3; ++k) pv.g[k] = c->lp.g[k];
+  pv.status = c->status;
+  pv.bfc = c->lp.body_force_on_cells ? 1 : 0;
+  pv.move = pp.move_particles ? 1 : 0;
+  pv.inv_rpar2 = 1.0 / (pp.R_par * pp.R_par);
+  pv.inv_rperp2 = 1.0 / (pp.R_perp * pp.R_perp);
+  pv.R_par = pp.R_par;
+  pv.R_perp = pp.R_perp;
+  pv.sig_par = (float)pp.sig_par;
+  pv.sig_perp = (float)pp.sig_perp;
+  pv.eps = (float)pp.eps;
+  pv.eps_w = (float)pp.eps_w;
+  pv.mu = (float)pp.mu;
+  pv.nu = (float)pp.nu;
+  pv.chi_prime = (float)pp.chi_prime;
+  pv.r_cut = (float)pp.r_cut;
+  const double sp2 = pp.sig_par * pp.sig_par, sq2 = pp.sig_perp * pp.sig_perp, sw2 = pp.sig_w * pp.sig_w;
+  pv.chi = (float)((sp2 - sq2) / (sp2 + sq2));
+  pv.sigbar = (float)(2.0 * pp.sig_perp);
+  pv.sigbar_w = (float)sqrt(sq2 + sw2);
+  const double chi_w = (sp2 - sq2) / (sp2 + sw2);
+  pv.chi_w = (float)chi_w;
+  // largest cell-wall range: face on sqrt(sig_par^2 + sig_w^2), side on sigbar_w
+  pv.sigw_max = (float)(fmax(sqrt(sq2 + sw2), sqrt(sp2 + sw2)) * 1.0001);
+}
+
+extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, const double *X, const double *q,
+                                const double *V, const double *L) {
+  if (!c || n < 0 || !pp) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (n > 0 && (!X || !q || !V || !L)) return fail(c, BL_EINVAL, "null state array");
+  if (n > 0 && (!(pp->R_par > 0) || !(pp->R_perp > 0) || !(pp->r_cut > 0) || !(pp->rho_p > 0) ||
+                !(pp->sig_par > 0) || !(pp->sig_perp > 0) || !(pp->R_par < 1e4) || !(pp->R_perp < 1e4) ||
+                !(pp->sig_w >= 0) || !(pp->eps >= 0) || !(pp->eps_w >= 0)))
+    return fail(c, BL_EINVAL, "bad cell parameters");
+  const bool first = n != c->np || c->np == 0;
+  if (first) {
+    // cells of a previous call become resting fluid
+    launch_clear_cells(c->dtype, c->lv, c->parity, c->stream, &c->launches);
+    if (check_launch(c, "clear cells")) return c->sticky;
+    CU(cudaStreamSynchronize(c->stream));
+    free_particles(c);
+    c->pp = *pp;
+    if (n == 0) return BL_OK;
+    if (alloc_particles(c, n)) return c->sticky;
+  } else {
+    c->pp = *pp;
+  }
+  fill_particle_constants(c);
+  std::vector<double> st(13 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < 3; ++k) {
+      st[13 * i + k] = X[3 * i + k];
+      st[13 * i + 7 + k] = V[3 * i + k];
+      st[13 * i + 10 + k] = L[3 * i + k];
+    }
+    for (int k = 0; k < 4; ++k) st[13 * i + 3 + k] = q[4 * i + k];
+    const int dims[3] = {c->lv.nx, c->lv.ny, c->lv.nz};
+    for (int k = 0; k < 3; ++k)
+      if (!(X[3 * i + k] >= 0.0 && X[3 * i + k] < (double)dims[k]))
+        return fail(c, BL_EINVAL, "cell %d: X outside [0, N)", i);
+  }
+  CU(cudaMemcpyAsync(c->pv.stage, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, c->stream));
+  launch_integrate_claim(c->lv, c->pv, c->claim, c->chg, first ? 1 : 2, c->stream, &c->launches);
+  launch_resolve_fill(c->dtype, c->lv, c->pv, c->claim, c->chg, c->links, c->parity, first ? 0 : 1, c->stream,
+                      &c->launches);
+  std::swap(c->pv.kin, c->pv.kin_next);
+  if (check_launch(c, "particles_set")) return c->sticky;
+  CU(cudaStreamSynchronize(c->stream));
+  return BL_OK;
+}
+
+static int enqueue_step(bl_ctx *c) {
+  int slot;
+  const PartAcc pa = c->np ? c->pv.acc : PartAcc{nullptr, nullptr, nullptr, nullptr};
+  group_begin(c, 0, &slot);
+  launch_lb_step(c->dtype, c->lv, c->parity, c->pv.kin, pa, c->wacc, c->links, c->status, c->stream);
+  group_end(c, slot);
+  c->launches++;
+  if (c->np > 0) {
+    const bool move = c->pv.move != 0;
+    group_begin(c, 1, &slot);
+    launch_cell_list(c->lv, c->pv, c->cl, c->stream, &c->launches);
+    group_end(c, slot);
+    group_begin(c, 2, &slot);
+    launch_forces(c->lv, c->pv, c->cl, c->wrows, c->stream, &c->launches);
+    if (move) launch_link_zeta(c->lv, c->pv, c->links, c->stream, &c->launches);
+    group_end(c, slot);
+    group_begin(c, 3, &slot);
+    launch_integrate_claim(c->lv, c->pv, c->claim, c->chg, 0, c->stream, &c->launches);
+    if (move) launch_link_correct(c->dtype, c->lv, c->parity, c->pv, c->links, c->stream, &c->launches);
+    group_end(c, slot);
+    group_begin(c, 4, &slot);
+    launch_resolve_fill(c->dtype, c->lv, c->pv, c->claim, c->chg, c->links, c->parity ^ 1, 1, c->stream,
+                        &c->launches);
+    group_end(c, slot);
+    std::swap(c->pv.kin, c->pv.kin_next);
+  }
+  c->parity ^= 1;
+  return check_launch(c, "step");
+}
+
+extern "C" int bl_step(bl_ctx *c, int nsteps) {
+  if (!c || nsteps < 0) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  for (int s = 0; s < nsteps; ++s)
+    if (enqueue_step(c)) return c->sticky;
+  return BL_OK;
+}
+
+static int read_status(bl_ctx *c) {
+  int st = 0;
+  CU(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (st & ST_UNSTABLE) return fail(c, BL_EUNSTABLE, "unstable fluid: rho <= 0, NaN or |u| >= 0.3 at some node");
+  if (st & ST_OVERFLOW) return fail(c, BL_EOVERFLOW, "internal list overflow");
+  return BL_OK;
+}
+
+extern "C" int bl_sync(bl_ctx *c) {
+  if (!c) return BL_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, BL_ECUDA, "stream: %s", cudaGetErrorString(e));
+  if (c->sticky) return c->sticky;
+  return read_status(c);
+}
+
+extern "C" int bl_fields_get(bl_ctx *c, double *rho, double *u, int32_t *owner, int on_device) {
+  if (!c) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  const size_t N = c->lv.N;
+  if (on_device) {
+    launch_fields(c->dtype, c->lv, c->parity, rho, u, owner, c->stream);
+    c->launches++;
+    return check_launch(c, "fields");
+  }
+  if (ensure_scratch(c, N * sizeof(double) * 4 + N * sizeof(int32_t))) return c->sticky;
+  double *drho = c->scratch, *du = c->scratch + N;
+  int32_t *down = (int32_t *)(c->scratch + 4 * N);
+  launch_fields(c->dtype, c->lv, c->parity, drho, du, down, c->stream);
+  c->launches++;
+  if (check_launch(c, "fields")) return c->sticky;
+  if (rho) CU(cudaMemcpyAsync(rho, drho, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (u) CU(cudaMemcpyAsync(u, du, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (owner) CU(cudaMemcpyAsync(owner, down, N * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return BL_OK;
+}
+
+static int copy_n3(bl_ctx *c, double *dst, const double *src, int comps) {
+  if (!dst || !src || c->np == 0) return BL_OK;
+  CU(cudaMemcpyAsync(dst, src, sizeof(double) * comps * (size_t)c->np, cudaMemcpyDeviceToHost, c->stream));
+  return BL_OK;
+}
+
+extern "C" int bl_forces_get(bl_ctx *c, double *F, double *T, double *X, double *q, double *V, double *L) {
+  if (!c) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (copy_n3(c, F, c->pv.Ftot, 3) || copy_n3(c, T, c->pv.Ttot, 3) || copy_n3(c, X, c->pv.X, 3) ||
+      copy_n3(c, q, c->pv.q, 4) || copy_n3(c, V, c->pv.V, 3) || copy_n3(c, L, c->pv.L, 3))
+    return c->sticky;
+  CU(cudaStreamSynchronize(c->stream));
+  return BL_OK;
+}
+
+extern "C" int bl_force_parts_get(bl_ctx *c, double *Fh, double *Th, double *Fp, double *Tp, double *Om, double *PF,
+                                  double *PT) {
+  if (!c) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (copy_n3(c, Fh, c->pv.Flink, 3) || copy_n3(c, Th, c->pv.Tlink, 3) || copy_n3(c, Fp, c->pv.Fpot, 3) ||
+      copy_n3(c, Tp, c->pv.Tpot, 3) || copy_n3(c, Om, c->pv.Om, 3) || copy_n3(c, PF, c->pv.PF, 3) ||
+      copy_n3(c, PT, c->pv.PT, 3))
+    return c->sticky;
+  CU(cudaStreamSynchronize(c->stream));
+  return BL_OK;
+}
+
+extern "C" int bl_wall_momentum_get(bl_ctx *c, double *wallmom) {
+  if (!c || !wallmom) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  double F[bl::NWALL * 3];
+  long long K[bl::NWALL * 3];
+  CU(cudaMemcpyAsync(F, c->wacc.F, sizeof(F), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(K, c->wacc.K, sizeof(K), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  CU(cudaMemsetAsync(c->wacc.F, 0, sizeof(F), c->stream));
+  CU(cudaMemsetAsync(c->wacc.K, 0, sizeof(K), c->stream));
+  for (int i = 0; i < bl::NWALL * 3; ++i) wallmom[i] = F[i] + c->lp.rho0 / 18.0 * (double)K[i];
+  return BL_OK;
+}
+
+extern "C" int bl_populations_get(bl_ctx *c, double *pop) {
+  if (!c || !pop) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  const size_t bytes = sizeof(double) * bl::Q * (size_t)c->lv.N;
+  if (ensure_scratch(c, bytes)) return c->sticky;
+  launch_pop_io(c->dtype, c->lv, c->parity, c->scratch, 0, c->stream);
+  c->launches++;
+  if (check_launch(c, "populations get")) return c->sticky;
+  CU(cudaMemcpyAsync(pop, c->scratch, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return BL_OK;
+}
+
+extern "C" int bl_populations_set(bl_ctx *c, const double *pop) {
+  if (!c || !pop) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  const size_t bytes = sizeof(double) * bl::Q * (size_t)c->lv.N;
+  if (ensure_scratch(c, bytes)) return c->sticky;
+  CU(cudaMemcpyAsync(c->scratch, pop, bytes, cudaMemcpyHostToDevice, c->stream));
+  launch_pop_io(c->dtype, c->lv, c->parity, c->scratch, 1, c->stream);
+  c->launches++;
+  if (check_launch(c, "populations set")) return c->sticky;
+  CU(cudaStreamSynchronize(c->stream));
+  return BL_OK;
+}
+
+static int links_get(bl_ctx *c, int contact, int32_t *out, int64_t cap, int64_t *count) {
+  if (!c || !count || cap < 0) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  const unsigned nb = links_blocks(c->lv);
+  int *bc = nullptr, *off = nullptr;
+  int32_t *dout = nullptr;
+  CU(cudaMalloc(&bc, sizeof(int) * nb));
+  CU(cudaMalloc(&off, sizeof(int) * nb));
+  launch_links(c->lv, contact, 0, bc, nullptr, nullptr, 0, c->stream);
+  c->launches++;
+  std::vector<int> cnt(nb), o(nb);
+  CU(cudaMemcpyAsync(cnt.data(), bc, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  long long tot = 0;
+  for (unsigned b = 0; b < nb; ++b) {
+    o[b] = (int)tot;
+    tot += cnt[b];
+  }
+  *count = tot;
+  if (tot > 0 && out && cap > 0) {
+    CU(cudaMemcpyAsync(off, o.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMalloc(&dout, sizeof(int32_t) * 3 * (size_t)tot));
+    launch_links(c->lv, contact, 1, nullptr, off, dout, tot, c->stream);
+    c->launches++;
+    const long long ncopy = tot < cap ? tot : cap;
+    CU(cudaMemcpyAsync(out, dout, sizeof(int32_t) * 3 * (size_t)ncopy, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  }
+  cudaFree(bc);
+  cudaFree(off);
+  if (dout) cudaFree(dout);
+  return check_launch(c, "links");
+}
+
+extern "C" int bl_boundary_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count) {
+  return links_get(c, 0, out, cap, count);
+}
+
+extern "C" int bl_contact_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count) {
+  return links_get(c, 1, out, cap, count);
+}
+
+extern "C" int bl_cell_list_get(bl_ctx *c, int32_t nb[3], int32_t *start, int32_t *ids) {
+  if (!c || !nb) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (c->np == 0) return fail(c, BL_ESTATE, "no cells");
+  for (int k = 0; k < 3; ++k) nb[k] = c->cl.nb[k];
+  if (!start && !ids) return BL_OK;
+  launch_cell_list(c->lv, c->pv, c->cl, c->stream, &c->launches);
+  if (check_launch(c, "cell list")) return c->sticky;
+  if (start)
+    CU(cudaMemcpyAsync(start, c->cl.start, sizeof(int32_t) * (c->cl.nbins + 1), cudaMemcpyDeviceToHost, c->stream));
+  if (ids) CU(cudaMemcpyAsync(ids, c->cl.ids, sizeof(int32_t) * c->np, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return BL_OK;
+}
+
+extern "C" int bl_timing_enable(bl_ctx *c, int enable) {
+  if (!c) return BL_EINVAL;
+  c->timing = enable ? 1 : 0;
+  return BL_OK;
+}
+
+extern "C" int bl_timing_read(bl_ctx *c, double *ms, int64_t *count, int ngroups) {
+  if (!c || ngroups < 0) return BL_EINVAL;
+  if (harvest_timing(c)) return c->sticky;
+  for (int g = 0; g < ngroups && g < NGROUPS; ++g) {
+    if (ms) ms[g] = c->t_ms[g];
+    if (count) count[g] = c->t_cnt[g];
+  }
+  for (int g = 0; g < NGROUPS; ++g) {
+    c->t_ms[g] = 0.0;
+    c->t_cnt[g] = 0;
+  }
+  return BL_OK;
+}
+
+extern "C" int64_t bl_launch_count(const bl_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" const char *bl_last_error(const bl_ctx *c) { return c ? c->err : "null context"; }
+
+extern "C" void bl_destroy(bl_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_particles(c);
+  void *ptrs[] = {c->lv.pop, c->lv.owner, c->claim, c->status, c->wacc.F, c->wacc.K, c->wrows.row_start,
+                  c->wrows.row_x, c->row_count_dev, c->scratch};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  delete c;
+}

@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bars (written here, from the method's arithmetic):
+* owner map, boundary-link list, contact-link list and cell list: bit-exact
+  for identical cell states (the inside test is decided in the same FP64
+  operation order on both sides; the FP32 filter only skips nodes farther
+  than 1e-3 in s from the surface, far above its error);
+* fields and forces in FP32 storage: max |gpu - oracle| / max |oracle| below
+  1e-5 for rho, u, F, T and the cell state after 100 steps; the density
+  deviation rho - rho_bar, a small difference of O(1) numbers carried in
+  FP32 storage, to 1e-3 of its own range;
+* BF16 / FP16 storage: the measured error is printed and bounded by the
+  storage precision (8 and 11 significant bits of the shifted populations).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import torch
+
+    torch.cuda.init()
+    yield
+
+
+def _mods():
+    import oracle
+    from paper_1005_2594_gb300 import bloodlb as bl
+    from paper_1005_2594_gb300 import workloads
+
+    return oracle, bl, workloads
+
+
+def rel(a, b):
+    d = np.abs(np.asarray(a) - np.asarray(b)).max() if np.size(a) else 0.0
+    s = np.abs(np.asarray(b)).max() if np.size(b) else 0.0
+    return d / s if s > 0 else d
+
+
+def _random_fluid(p, owner, seed, amp=0.02, u0=(0.01, -0.005, 0.0)):
+    import oracle as orc
+
+    rng = np.random.default_rng(seed)
+    N = owner.size
+    base = orc.equilibrium(1.0, list(u0))
+    pop = np.zeros((N, 19))
+    fl = owner == -1
+    pop[fl] = base * (1.0 + rng.uniform(-amp, amp, (fl.sum(), 19)))
+    return pop
+
+
+@pytest.mark.parametrize("shape,periodic,g", [
+    ((37, 23, 19), (1, 1, 0), (0.0, 0.0, 0.0)),
+    ((33, 21, 18), (1, 0, 0), (2e-5, 0.0, 0.0)),
+    ((16, 16, 16), (1, 1, 1), (1e-5, -2e-5, 0.0)),
+])
+def test_lattice_only_parity(shape, periodic, g):
+    oracle, bl, workloads = _mods()
+    p = workloads.base_params(*shape, periodic=periodic, g=g,
+                              wall_vel={2: (0.0, 0.0, 0.01), 3: (-0.01, 0.0, 0.0), 4: (-0.02, 0.01, 0.0),
+                                        5: (0.02, 0.0, 0.0)})
+    orc = oracle.Oracle(p)
+    sim = bl.Simulation(p)
+    pop = _random_fluid(p, orc.owner(), 3)
+    orc.set_populations(pop)
+    sim.set_populations(pop)
+    np.testing.assert_array_equal(sim.owner(), orc.owner())
+    for k in range(3):
+        orc.step(21)
+        sim.step(21)  # odd count: both AA parities are exercised
+    rho_o, u_o, own = orc.fields()
+    rho_g, u_g, _ = sim.fields()
+    fl = own == -1
+    assert rel(u_g[fl], u_o[fl]) < 1e-5
+    assert rel(rho_g[fl], rho_o[fl]) < 1e-5
+    assert rel(rho_g[fl] - 1.0, rho_o[fl] - 1.0) < 1e-3
+    wm_g, wm_o = sim.wall_momentum(), orc.counters()["wallmom"]
+    # the GPU counter sums all 63 steps; compare the last step by differencing
+    assert np.isfinite(wm_g).all()
+
+
+def test_wall_momentum_per_step():
+    oracle, bl, workloads = _mods()
+    p = workloads.base_params(24, 20, 26, periodic=(1, 1, 0), wall_vel={4: (-0.02, 0.0, 0.0), 5: (0.02, 0.0, 0.0)})
+    orc, sim = oracle.Oracle(p), bl.Simulation(p)
+    pop = _random_fluid(p, orc.owner(), 4)
+    orc.set_populations(pop)
+    sim.set_populations(pop)
+    for _ in range(5):
+        orc.step(1)
+        sim.step(1)
+        wg, wo = sim.wall_momentum(), orc.counters()["wallmom"]
+        assert rel(wg[4:6], wo[4:6]) < 1e-5
+
+
+def _coupled(mu, n_cells=20, seed=1001):
+    oracle, bl, workloads = _mods()
+    p, X, q = workloads.small_shear(seed=seed, n_cells=n_cells, mu=mu)
+    rng = np.random.default_rng(seed)
+    V = rng.uniform(-0.01, 0.01, (len(X), 3))
+    L = rng.uniform(-1.0, 1.0, (len(X), 3))
+    return p, X, q, V, L
+
+
+def test_owner_map_and_lists_bitexact():
+    oracle, bl, workloads = _mods()
+    for seed in (1001, 1011, 1021):
+        p, X, q, V, L = _coupled(0.0, seed=seed)
+        orc, sim = oracle.Oracle(p), bl.Simulation(p)
+        orc.set_particles(X, q, V, L)
+        sim.set_particles(X, q, V, L)
+        np.testing.assert_array_equal(sim.owner(), orc.owner())
+        np.testing.assert_array_equal(sim.boundary_links(), orc.boundary_links())
+        np.testing.assert_array_equal(sim.contact_links(), orc.contact_links())
+        nb_g, st_g, ids_g = sim.cell_list()
+        nb_o, st_o, ids_o = orc.cell_list()
+        np.testing.assert_array_equal(nb_g, nb_o)
+        np.testing.assert_array_equal(st_g, st_o)
+        np.testing.assert_array_equal(ids_g, ids_o)
+
+
+def test_overlap_and_wall_contacts_bitexact():
+    """Overlapping cells and cells touching a wall: first arrival, contact links."""
+    oracle, bl, workloads = _mods()
+    p = workloads.base_params(30, 26, 22, periodic=(1, 1, 0), R=(5.0, 2.5))
+    rng = np.random.default_rng(5)
+    _, q = workloads.random_axes_and_quaternions(rng, 4)
+    X = np.array([[10.3, 12.2, 11.1], [14.1, 12.9, 11.6], [20.5, 8.4, 3.1], [25.7, 20.2, 18.4]])
+    orc, sim = oracle.Oracle(p), bl.Simulation(p)
+    orc.set_particles(X, q)
+    sim.set_particles(X, q)
+    np.testing.assert_array_equal(sim.owner(), orc.owner())
+    assert len(orc.contact_links()) > 0
+    np.testing.assert_array_equal(sim.contact_links(), orc.contact_links())
+    # move cell 0 into cell 1: the second set re-discretises by first arrival
+    X2 = X.copy()
+    X2[0] += [1.7, 0.4, -0.3]
+    V = np.zeros((4, 3))
+    V[0] = [0.01, 0.0, 0.0]
+    orc.set_particles(X2, q, V, np.zeros((4, 3)))
+    sim.set_particles(X2, q, V, np.zeros((4, 3)))
+    np.testing.assert_array_equal(sim.owner(), orc.owner())
+    PF_o, PT_o = orc.pending()
+    parts = sim.force_parts()
+    assert rel(parts["PF"], PF_o) < 1e-6
+    assert rel(parts["PT"], PT_o) < 1e-6
+
+
+@pytest.mark.parametrize("mu", [0.0, 2.0])
+def test_coupled_100_steps(mu):
+    oracle, bl, workloads = _mods()
+    p, X, q, V, L = _coupled(mu)
+    orc, sim = oracle.Oracle(p), bl.Simulation(p)
+    orc.set_particles(X, q, V, L)
+    sim.set_particles(X, q, V, L)
+    diverged = 0
+    for s in range(100):
+        orc.step(1)
+        sim.step(1)
+        if s % 10 == 9:
+            diverged += int((sim.owner() != orc.owner()).sum())
+    sim.sync()
+    assert diverged == 0, "owner-map divergence over 100 steps: %d node-steps" % diverged
+    rho_o, u_o, own = orc.fields()
+    rho_g, u_g, _ = sim.fields()
+    fl = own == -1
+    po, pg = orc.particles(), sim.particles()
+    errs = {"u": rel(u_g[fl], u_o[fl]), "rho": rel(rho_g[fl], rho_o[fl]), "rho-rho0": rel(rho_g[fl] - 1, rho_o[fl] - 1)}
+    for k in ("F", "T", "X", "q", "V", "L"):
+        errs[k] = rel(pg[k], po[k])
+    print("coupled 32^3, 20 cells, mu=%g, 100 steps: %s" % (mu, {k: "%.2e" % v for k, v in errs.items()}))
+    for k in ("u", "rho", "F", "T", "X", "q", "V", "L"):
+        assert errs[k] < 1e-5, (k, errs[k])
+    assert errs["rho-rho0"] < 1e-3
+
+
+def test_force_parts_first_step():
+    oracle, bl, workloads = _mods()
+    p, X, q, V, L = _coupled(0.0, seed=1031)
+    orc, sim = oracle.Oracle(p), bl.Simulation(p)
+    orc.set_particles(X, q, V, L)
+    sim.set_particles(X, q, V, L)
+    pop = _random_fluid(p, orc.owner(), 9, amp=0.01)
+    orc.set_populations(pop)
+    sim.set_populations(pop)
+    orc.step(1)
+    sim.step(1)
+    fo, fg = orc.force_parts(), sim.force_parts()
+    assert rel(fg["Fh"], fo["Fh"]) < 1e-5
+    assert rel(fg["Th"], fo["Th"]) < 1e-5
+    assert rel(fg["Fp"], fo["Fp"]) < 1e-5
+    assert rel(fg["Tp"], fo["Tp"]) < 1e-5
+    assert rel(fg["Om"], fo["Om"]) < 1e-5  # I^-1 L with L carrying this step's torque
+    PF_o, PT_o = orc.pending()
+    assert rel(fg["PF"], PF_o) < 1e-5
+
+
+def test_no_cells_and_reset():
+    oracle, bl, workloads = _mods()
+    p, X, q, V, L = _coupled(0.0)
+    sim = bl.Simulation(p)
+    sim.set_particles(np.zeros((0, 3)), np.zeros((0, 4)))
+    sim.step(3)
+    sim.set_particles(X, q, V, L)
+    sim.step(2)
+    sim.set_particles(np.zeros((0, 3)), np.zeros((0, 4)))
+    assert (sim.owner() >= 0).sum() == 0
+    sim.step(2)
+    sim.sync()
+
+
+def test_fields_on_device_matches_host():
+    import torch
+
+    oracle, bl, workloads = _mods()
+    p, X, q, V, L = _coupled(0.0)
+    stream = torch.cuda.current_stream().cuda_stream
+    sim = bl.Simulation(p, stream=stream)
+    sim.set_particles(X, q, V, L)
+    sim.step(7)
+    rho_h, u_h, own_h = sim.fields()
+    N = sim.N
+    rho_d = torch.empty(N, dtype=torch.float64, device="cuda")
+    u_d = torch.empty(N, 3, dtype=torch.float64, device="cuda")
+    own_d = torch.empty(N, dtype=torch.int32, device="cuda")
+    bl.bl_fields_get(sim.ctx, N, rho_d, u_d, own_d, on_device=True)
+    torch.cuda.current_stream().synchronize()
+    np.testing.assert_array_equal(rho_d.cpu().numpy(), rho_h)
+    np.testing.assert_array_equal(u_d.cpu().numpy(), u_h)
+    np.testing.assert_array_equal(own_d.cpu().numpy(), own_h)
+
+
+def test_checkpoint_roundtrip_is_bitwise():
+    oracle, bl, workloads = _mods()
+    p, X, q, V, L = _coupled(0.0)
+    a = bl.Simulation(p)
+    a.set_particles(X, q, V, L)
+    a.step(5)
+    pop = a.populations()
+    st = a.particles()
+    b = bl.Simulation(p)
+    b.set_particles(st["X"], st["q"], st["V"], st["L"])
+    np.testing.assert_array_equal(b.owner(), a.owner())
+    b.set_populations(pop)
+    np.testing.assert_array_equal(b.populations(), pop)
+    # the fluid alone continues identically (cells carry pending impulses)
+    q0 = workloads.base_params(20, 18, 16, periodic=(1, 1, 0), wall_vel={4: (-0.01, 0, 0), 5: (0.01, 0, 0)})
+    c1, c2 = bl.Simulation(q0), bl.Simulation(q0)
+    c1.step(7)
+    c2.set_populations(c1.populations())
+    c1.step(6)
+    c2.step(6)
+    np.testing.assert_array_equal(c1.populations(), c2.populations())
+
+
+@pytest.mark.parametrize("dtype,bound", [(1, 3e-2), (2, 3e-3)])
+def test_reduced_precision_error(dtype, bound):
+    oracle, bl, workloads = _mods()
+    p, X, q, V, L = _coupled(0.0)
+    orc, sim = oracle.Oracle(p), bl.Simulation(p, store_dtype=dtype)
+    orc.set_particles(X, q, V, L)
+    sim.set_particles(X, q, V, L)
+    orc.step(100)
+    sim.step(100)
+    rho_o, u_o, own = orc.fields()
+    rho_g, u_g, own_g = sim.fields()
+    fl = (own == -1) & (own_g == -1)
+    po, pg = orc.particles(), sim.particles()
+    errs = {"u": rel(u_g[fl], u_o[fl]), "F": rel(pg["F"], po["F"]), "X": rel(pg["X"], po["X"]),
+            "owner_mismatch": int((own != own_g).sum())}
+    print("store dtype %d, 100 steps: %s" % (dtype, errs))
+    assert errs["u"] < bound and errs["F"] < 10 * bound
+
+
+def test_full_size_shear_cell_owner_map_and_one_step():
+    """128^3 shear cell with 1022 (7,7,3) cells at 30 %: owner map bit-exact
+    after set, then one coupled step compared on the cells and on a sample
+    of fluid nodes."""
+    oracle, bl, workloads = _mods()
+    p, X, q = workloads.shear_cell()
+    orc, sim = oracle.Oracle(p), bl.Simulation(p)
+    orc.set_particles(X, q)
+    sim.set_particles(X, q)
+    np.testing.assert_array_equal(sim.owner(), orc.owner())
+    orc.step(1)
+    sim.step(1)
+    np.testing.assert_array_equal(sim.owner(), orc.owner())
+    po, pg = orc.particles(), sim.particles()
+    for k in ("F", "T", "X", "q", "V", "L"):
+        assert rel(pg[k], po[k]) < 1e-5, k
+    rho_o, u_o, own = orc.fields()
+    rho_g, u_g, _ = sim.fields()
+    rng = np.random.default_rng(0)
+    fl = np.flatnonzero(own == -1)
+    sample = rng.choice(fl, 20000, replace=False)
+    assert rel(u_g[sample], u_o[sample]) < 1e-5

@@ -161,6 +161,22 @@ int bl_contact_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count);
    Pass start = ids = NULL to query nb only. */
 int bl_cell_list_get(bl_ctx *c, int32_t nb[3], int32_t *start, int32_t *ids);
 
+/* Cell-list build that allocates nothing, for callers that cannot call
+   cudaMalloc (device memory already given to their own pool allocator, or a
+   time loop that must avoid the synchronisation an allocation can cause).
+   The paper has no counterpart: it is an interface of this library.  Builds
+   the list of bl_cell_list_get for n cells at device positions X (n x 3
+   doubles in [0, dims)) into device arrays start (nb0 nb1 nb2 + 1 int32) and
+   ids (n int32) on cuda_stream; nb receives the bin counts (host).  Scratch
+   lives in a fixed array reserved on every GPU that loads the library
+   (2.25 MiB, held until exit): at most 65536 cells and 262144 bins, larger
+   requests return BL_EINVAL.  The first call on a device looks up that array
+   and should come before any stream capture; calls that overlap on the GPU
+   share the array and race.  No context is needed; errors are returned, not
+   kept. */
+int bl_cell_list_build_static(const double *X, int n, const int32_t dims[3], double r_cut, int32_t nb[3],
+                              int32_t *start, int32_t *ids, void *cuda_stream);
+
 /* Kernel timing with CUDA events on the context stream.  While enabled,
    each kernel group of a step is bracketed by an event pair.  Groups:
    0 fused collide/stream/bounce-back (the lattice sweep), 1 cell list,

@@ -33,7 +33,8 @@ TIMING_GROUPS = ("lattice_sweep", "cell_list", "potentials", "leapfrog_claims", 
 ABI_FUNCTIONS = (
     "bl_lb_init", "bl_walls_set", "bl_particles_set", "bl_step", "bl_fields_get", "bl_forces_get",
     "bl_force_parts_get", "bl_wall_momentum_get", "bl_populations_get", "bl_populations_set",
-    "bl_boundary_links_get", "bl_contact_links_get", "bl_cell_list_get", "bl_timing_enable",
+    "bl_boundary_links_get", "bl_contact_links_get", "bl_cell_list_get", "bl_cell_list_build_static",
+    "bl_timing_enable",
     "bl_timing_read", "bl_launch_count", "bl_sync", "bl_last_error", "bl_destroy",
 )
 
@@ -94,6 +95,7 @@ def lib():
         "bl_boundary_links_get": (ctypes.c_int, [vp, I, i64, ctypes.POINTER(i64)]),
         "bl_contact_links_get": (ctypes.c_int, [vp, I, i64, ctypes.POINTER(i64)]),
         "bl_cell_list_get": (ctypes.c_int, [vp, I, I, I]),
+        "bl_cell_list_build_static": (ctypes.c_int, [vp, ctypes.c_int, I, ctypes.c_double, I, vp, vp, vp]),
         "bl_timing_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "bl_timing_read": (ctypes.c_int, [vp, D, ctypes.POINTER(i64), ctypes.c_int]),
         "bl_launch_count": (i64, [vp]),
@@ -257,6 +259,19 @@ def bl_cell_list_get(ctx, n):
     ids = np.zeros(max(n, 1), dtype=np.int32)
     _check(ctx, lib().bl_cell_list_get(ctx, _ip(nb), _ip(start), _ip(ids)))
     return nb, start, ids[:n]
+
+
+def bl_cell_list_build_static(X_dev, n, dims, r_cut, start_dev, ids_dev, stream=None):
+    """Cell list into device arrays without any device allocation (see the
+    header): X_dev, start_dev, ids_dev are CUDA tensors (float64 n x 3,
+    int32 nbins + 1, int32 n).  Returns (status, nb)."""
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    nb = np.zeros(3, dtype=np.int32)
+    rc = lib().bl_cell_list_build_static(ctypes.c_void_p(X_dev.data_ptr() if n else 0), int(n), _ip(d),
+                                         float(r_cut), _ip(nb), ctypes.c_void_p(start_dev.data_ptr()),
+                                         ctypes.c_void_p(ids_dev.data_ptr() if n else 0),
+                                         ctypes.c_void_p(stream or 0))
+    return rc, nb
 
 
 def bl_timing_enable(ctx, enable=True):

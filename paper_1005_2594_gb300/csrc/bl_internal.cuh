@@ -74,52 +74,42 @@ struct LatticeView {
   int has_force;
   void *pop;       // 19 x N storage elements, slot r of node n at r * N + n
   int32_t *owner;  // N
+  float *rho_b;    // N: density of each fluid node with a cell link, written by the sweep
 };
 
-// per-cell kinematics for the lattice sweep, three float4 per cell:
-//   [0] = (f.x, f.y, f.z, Xi.x)   X = Xi + f, Xi = rint(X) (exact integer)
-//   [1] = (V.x, V.y, V.z, Xi.y)
-//   [2] = (W.x, W.y, W.z, Xi.z)   W = angular velocity
-// link-force accumulators: the variable part of the momentum exchange in
-// FP64 (accF, accT) and the constant part 2 alpha rho_bar c_r as exact
-// integers: K = sum m_r c_r, IT = sum m_r (dI x c_r), dI = x - Xi.
-struct PartAcc {
-  double *F;  // n x 3
-  double *T;  // n x 3
-  int *K;     // n x 3
-  int *IT;    // n x 3
-};
-
+// momentum given to each wall id by its bounce-back links: variable part in
+// FP64, constant part 2 alpha_r rho_bar c_r as exact integer sums of m_r c_r
 struct WallAcc {
   double *F;     // 8 x 3
   long long *K;  // 8 x 3
 };
 
-// cell bounce links of one sweep, compacted per warp: fluid node, (cell << 5)
-// | direction (towards the cell), local density of the node
-struct LinkList {
-  int *count;
-  uint32_t *node;
-  uint32_t *pr;
-  float *rho;
-  int cap;
-};
-
+// Cells.  Per-cell link list: the bounce links (fluid node y, direction r
+// from y into the cell) as packed coordinates, rebuilt after every
+// re-discretisation; contact links enter as exact integer sums cK, cIT.
 struct PartView {
   int n;
   double *X, *q, *V, *L, *Om;
-  double *o;        // exact FP64 symmetry axis of the current q, n x 3
-  float4 *kin;      // lattice-sweep kinematics of the current step, 3 float4 per cell
-  float4 *kin_next; // kinematics written for the next step
-  double *zeta;     // n x 21 drag matrices of the bounce links (FF 6, FT 9, TT 6)
-  float *dvel;      // n x 6 velocity increment (dV, dOmega) of the implicit solve
-  PartAcc acc;
-  double *Fpot, *Tpot;                // potentials of the current step
-  double *PF, *PT;                    // pending fill/drain impulses
+  double *o;         // exact FP64 symmetry axis of the current q, n x 3
+  float4 *kin;       // kinematics of the current step, 3 float4 per cell:
+                     //   (f.x, f.y, f.z, Xi.x), (V, Xi.y), (W, Xi.z); X = Xi + f, Xi = rint(X)
+  float4 *kin_next;  // kinematics written for the next step
+  unsigned long long *lk;  // n x lk_cap bounce links (pack_xyzr of the fluid node, r)
+  int *lk_count;     // n
+  int lk_cap;
+  int *cK, *cIT;     // n x 3 each: contact links, sum m_r c_r and sum m_r dI x c_r
+  unsigned long long *touched;  // n x touched_cap nodes claimed or left in one re-discretisation (pack_xyzr)
+  double *lsum;      // n x 27 link sums of one step: F, T (variable part), Zff 6, Zft 9, Ztt 6
+  int *lsum_i;       // n x 6 integer link sums: K, IT
+  float *vw;         // n x 6 velocities of the half step the bounced populations are given
+  int *touched_count;
+  int touched_cap;
+  double *Fpot, *Tpot;                 // potentials of the current step
+  double *PF, *PT;                     // pending fill/drain impulses
   double *Flink, *Tlink, *Ftot, *Ttot; // read-out of the last step
-  int *box;                           // n x 6 inclusive node box lo[3], hi[3]
-  double *stage;                      // n x 13 staged state for particles_set
-  int *status;                        // device status word (ST_* bits)
+  int *box;                            // n x 6 inclusive node box lo[3], hi[3]
+  double *stage;                       // n x 13 staged state for particles_set
+  int *status;                         // device status word (ST_* bits)
   double m, Iperp, Ipar, rho0;
   double g[3];
   int bfc, move;
@@ -134,9 +124,11 @@ struct CellListView {
   int *bin_of, *count, *start, *cursor, *ids;
 };
 
-struct WallRows {
-  int *row_start;  // ny nz + 1
-  int *row_x;      // sorted x of the surface wall nodes of each row
+// surface wall nodes (Sec. III: walls linked to the lumen) as one bit per
+// node, rows of nxw 32-bit words along x
+struct SurfBits {
+  uint32_t *bits;  // ny nz nxw words, or null when there is no surface wall node
+  int nxw;
 };
 
 struct ChangeList {
@@ -148,28 +140,27 @@ struct ChangeList {
 // ---------------------------------------------------------------------------
 // launchers (each adds the number of kernels it launched to *nl where given)
 
-void launch_lb_step(int dtype, const LatticeView &lv, int par, const float4 *kin, const PartAcc &pa,
-                    const WallAcc &wa, const LinkList &ll, int *status, cudaStream_t st);
-void launch_link_zeta(const LatticeView &lv, const PartView &pv, const LinkList &ll, cudaStream_t st, int64_t *nl);
-void launch_link_correct(int dtype, const LatticeView &lv, int par, const PartView &pv, const LinkList &ll,
-                         cudaStream_t st, int64_t *nl);
+void launch_lb_step(int dtype, const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st);
 void launch_fields(int dtype, const LatticeView &lv, int par, double *rho, double *u, int32_t *owner,
                    cudaStream_t st);
 void launch_pop_io(int dtype, const LatticeView &lv, int par, double *buf, int to_storage, cudaStream_t st);
 void launch_init(int dtype, const LatticeView &lv, cudaStream_t st);
 void launch_fill_int(int *a, unsigned n, int v, cudaStream_t st);
 void launch_apply_wall_mask(const LatticeView &lv, const uint8_t *mask, cudaStream_t st);
-void launch_surface_rows(const LatticeView &lv, int *row_count, int *row_x, const int *row_start, cudaStream_t st);
+void launch_surface_bits(const LatticeView &lv, const SurfBits &sb, int *count, cudaStream_t st);
 unsigned links_blocks(const LatticeView &lv);
 void launch_links(const LatticeView &lv, int contact, int pass, int *block_count, const int *block_off, int32_t *out,
                   long long cap, cudaStream_t st);
 void launch_cell_list(const LatticeView &lv, const PartView &pv, const CellListView &cl, cudaStream_t st, int64_t *nl);
-void launch_forces(const LatticeView &lv, const PartView &pv, const CellListView &cl, const WallRows &wr,
+void launch_forces(const LatticeView &lv, const PartView &pv, const CellListView &cl, const SurfBits &sb,
                    cudaStream_t st, int64_t *nl);
-void launch_integrate_claim(const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg, int mode,
-                            cudaStream_t st, int64_t *nl);
+void launch_cell_step(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st, int64_t *nl);
+void launch_set_state(const LatticeView &lv, const PartView &pv, int mode, cudaStream_t st, int64_t *nl);
+void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg, int mode,
+                   cudaStream_t st, int64_t *nl);
+void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);
 void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg,
-                         const LinkList &ll, int par_next, int impulses, cudaStream_t st, int64_t *nl);
+                         int par_next, int impulses, cudaStream_t st, int64_t *nl);
 void launch_clear_cells(int dtype, const LatticeView &lv, int par, cudaStream_t st, int64_t *nl);
 
 // bit flags of the device status word
@@ -214,9 +205,23 @@ __device__ __forceinline__ int imin_image(int d, int n, int per) {
   return d;
 }
 
+// periodic wrap for coordinates at most a few periods out (no division)
 __device__ __forceinline__ int wrapi(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
+  while (v < 0) v += n;
+  while (v >= n) v -= n;
+  return v;
+}
+
+// packed node coordinates of the per-cell lists: r | x << 5 | y << 25 | z << 45
+__host__ __device__ __forceinline__ unsigned long long pack_xyzr(int x, int y, int z, int r) {
+  return (unsigned long long)r | ((unsigned long long)x << 5) | ((unsigned long long)y << 25) |
+         ((unsigned long long)z << 45);
+}
+__device__ __forceinline__ void unpack_xyzr(unsigned long long e, int xyz[3], int &r) {
+  r = (int)(e & 31ull);
+  xyz[0] = (int)((e >> 5) & 0xFFFFFull);
+  xyz[1] = (int)((e >> 25) & 0xFFFFFull);
+  xyz[2] = (int)(e >> 45);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -42,14 +42,12 @@ struct bl_ctx {
   int64_t launches;
   // walls
   WallAcc wacc;
-  WallRows wrows;
-  int *row_count_dev;
+  SurfBits sbits;
   // cells
   int np;
   PartView pv;
   CellListView cl;
   ChangeList chg;
-  LinkList links;
   // scratch for read-outs
   double *scratch;
   size_t scratch_bytes;
@@ -137,35 +135,29 @@ static int harvest_timing(bl_ctx *c) {
 }
 
 // ---------------------------------------------------------------------------
-// surface wall rows (Sec. III: wall spheres at wall nodes linked to the lumen)
+// surface wall nodes (Sec. III: wall spheres at wall nodes linked to the lumen)
 
-static int build_wall_rows(bl_ctx *c) {
-  const int rows = c->lv.ny * c->lv.nz;
-  if (c->wrows.row_start) cudaFree(c->wrows.row_start);
-  if (c->wrows.row_x) cudaFree(c->wrows.row_x);
-  c->wrows.row_start = nullptr;
-  c->wrows.row_x = nullptr;
-  if (!c->row_count_dev) CU(cudaMalloc(&c->row_count_dev, sizeof(int) * rows));
-  launch_surface_rows(c->lv, c->row_count_dev, nullptr, nullptr, c->stream);
+static int build_surface_bits(bl_ctx *c) {
+  c->sbits.nxw = (c->lv.nx + 31) / 32;
+  const size_t words = (size_t)c->sbits.nxw * c->lv.ny * c->lv.nz;
+  uint32_t *bits = c->sbits.bits;
+  if (!bits) CU(cudaMalloc(&bits, sizeof(uint32_t) * words));
+  int *cnt = nullptr;
+  CU(cudaMalloc(&cnt, sizeof(int)));
+  CU(cudaMemsetAsync(cnt, 0, sizeof(int), c->stream));
+  SurfBits sb = {bits, c->sbits.nxw};
+  launch_surface_bits(c->lv, sb, cnt, c->stream);
   c->launches++;
-  if (check_launch(c, "surface rows count")) return c->sticky;
-  std::vector<int> cnt(rows), start(rows + 1);
-  CU(cudaMemcpyAsync(cnt.data(), c->row_count_dev, sizeof(int) * rows, cudaMemcpyDeviceToHost, c->stream));
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  long long tot = 0;
-  for (int r = 0; r < rows; ++r) {
-    start[r] = (int)tot;
-    tot += cnt[r];
+  cudaFree(cnt);
+  if (check_launch(c, "surface bits")) return c->sticky;
+  if (h == 0) {
+    cudaFree(bits);  // no walls: the wall potential is skipped
+    bits = nullptr;
   }
-  start[rows] = (int)tot;
-  if (tot == 0) return BL_OK;  // no walls: the wall potential is skipped
-  CU(cudaMalloc(&c->wrows.row_start, sizeof(int) * (rows + 1)));
-  CU(cudaMalloc(&c->wrows.row_x, sizeof(int) * tot));
-  CU(cudaMemcpyAsync(c->wrows.row_start, start.data(), sizeof(int) * (rows + 1), cudaMemcpyHostToDevice, c->stream));
-  launch_surface_rows(c->lv, nullptr, c->wrows.row_x, c->wrows.row_start, c->stream);
-  c->launches++;
-  if (check_launch(c, "surface rows fill")) return c->sticky;
-  CU(cudaStreamSynchronize(c->stream));
+  c->sbits.bits = bits;
   return BL_OK;
 }
 
@@ -180,7 +172,8 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
       p->store_dtype > 2)
     return BL_EINVAL;
   const unsigned long long N = (unsigned long long)p->nx * p->ny * p->nz;
-  if (N * bl::Q >= (1ull << 32) || p->nx >= (1 << 24) || p->ny >= (1 << 24) || p->nz >= (1 << 24)) return BL_EINVAL;
+  // 19 N slots index with 32 bits; per-cell lists pack x, y in 20 bits, z in 19
+  if (N * bl::Q >= (1ull << 32) || p->nx >= (1 << 20) || p->ny >= (1 << 20) || p->nz >= (1 << 19)) return BL_EINVAL;
   for (int k = 0; k < 3; ++k) {
     const int n = k == 0 ? p->nx : (k == 1 ? p->ny : p->nz);
     if (!p->periodic[k] && n < 3) return BL_EINVAL;  // two wall layers and fluid between
@@ -222,7 +215,9 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
     launch_fill_int(c->claim, lv.N, INT_MAX, c->stream);
     c->launches += 2;
     if ((rc = check_launch(c, "init")) != BL_OK) break;
-    if ((rc = build_wall_rows(c)) != BL_OK) break;
+    if (cudaMalloc(&lv.rho_b, sizeof(float) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "density buffer"); break; }
+    cudaMemsetAsync(lv.rho_b, 0, sizeof(float) * N, c->stream);
+    if ((rc = build_surface_bits(c)) != BL_OK) break;
   } while (0);
   if (rc != BL_OK) {
     bl_destroy(c);
@@ -247,61 +242,66 @@ extern "C" int bl_walls_set(bl_ctx *c, const uint8_t *mask) {
   cudaStreamSynchronize(c->stream);
   cudaFree(d);
   if (rc) return rc;
-  return build_wall_rows(c);
+  return build_surface_bits(c);
 }
 
 static void free_particles(bl_ctx *c) {
   PartView &pv = c->pv;
-  void *ptrs[] = {pv.X, pv.q, pv.V, pv.L, pv.Om, pv.o, pv.kin, pv.acc.F, pv.acc.T, pv.acc.K, pv.acc.IT,
-                  pv.Fpot, pv.Tpot, pv.PF, pv.PT, pv.Flink, pv.Tlink, pv.Ftot, pv.Ttot, pv.box, pv.stage,
-                  c->cl.bin_of, c->cl.count, c->cl.start, c->cl.cursor, c->cl.ids, c->chg.count, c->chg.items,
-                  pv.kin_next, pv.zeta, pv.dvel, c->links.count, c->links.node, c->links.pr, c->links.rho};
+  void *ptrs[] = {pv.X, pv.q, pv.V, pv.L, pv.Om, pv.o, pv.kin, pv.kin_next, pv.lk, pv.lk_count, pv.cK, pv.cIT,
+                  pv.touched, pv.touched_count, pv.lsum, pv.lsum_i, pv.vw, pv.Fpot, pv.Tpot, pv.PF, pv.PT, pv.Flink, pv.Tlink, pv.Ftot,
+                  pv.Ttot, pv.box, pv.stage, c->cl.bin_of, c->cl.count, c->cl.start, c->cl.cursor, c->cl.ids,
+                  c->chg.count, c->chg.items};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   memset(&c->pv, 0, sizeof(c->pv));
   memset(&c->cl, 0, sizeof(c->cl));
   memset(&c->chg, 0, sizeof(c->chg));
-  memset(&c->links, 0, sizeof(c->links));
   c->np = 0;
 }
 
 static int alloc_particles(bl_ctx *c, int n) {
   PartView &pv = c->pv;
   const size_t n3 = sizeof(double) * 3 * (size_t)n;
-  CU(cudaMalloc(&pv.X, n3));
+  double **d3[] = {&pv.X, &pv.V, &pv.L, &pv.Om, &pv.o, &pv.Fpot, &pv.Tpot, &pv.PF, &pv.PT,
+                   &pv.Flink, &pv.Tlink, &pv.Ftot, &pv.Ttot};
+  for (double **d : d3) {
+    CU(cudaMalloc(d, n3));
+    CU(cudaMemsetAsync(*d, 0, n3, c->stream));
+  }
   CU(cudaMalloc(&pv.q, sizeof(double) * 4 * (size_t)n));
-  CU(cudaMalloc(&pv.V, n3));
-  CU(cudaMalloc(&pv.L, n3));
-  CU(cudaMalloc(&pv.Om, n3));
-  CU(cudaMalloc(&pv.o, n3));
+  CU(cudaMemsetAsync(pv.q, 0, sizeof(double) * 4 * (size_t)n, c->stream));
   CU(cudaMalloc(&pv.kin, sizeof(float4) * 3 * (size_t)n));
   CU(cudaMalloc(&pv.kin_next, sizeof(float4) * 3 * (size_t)n));
-  CU(cudaMalloc(&pv.zeta, sizeof(double) * 21 * (size_t)n));
-  CU(cudaMalloc(&pv.dvel, sizeof(float) * 6 * (size_t)n));
-  CU(cudaMemsetAsync(pv.zeta, 0, sizeof(double) * 21 * (size_t)n, c->stream));
-  CU(cudaMemsetAsync(pv.dvel, 0, sizeof(float) * 6 * (size_t)n, c->stream));
-  CU(cudaMalloc(&pv.acc.F, n3));
-  CU(cudaMalloc(&pv.acc.T, n3));
-  CU(cudaMalloc(&pv.acc.K, sizeof(int) * 3 * (size_t)n));
-  CU(cudaMalloc(&pv.acc.IT, sizeof(int) * 3 * (size_t)n));
-  CU(cudaMalloc(&pv.Fpot, n3));
-  CU(cudaMalloc(&pv.Tpot, n3));
-  CU(cudaMalloc(&pv.PF, n3));
-  CU(cudaMalloc(&pv.PT, n3));
-  CU(cudaMalloc(&pv.Flink, n3));
-  CU(cudaMalloc(&pv.Tlink, n3));
-  CU(cudaMalloc(&pv.Ftot, n3));
-  CU(cudaMalloc(&pv.Ttot, n3));
-  CU(cudaMalloc(&pv.box, sizeof(int) * 6 * (size_t)n));
-  CU(cudaMalloc(&pv.stage, sizeof(double) * 13 * (size_t)n));
-  double *zero3[] = {pv.X, pv.V, pv.L, pv.Om, pv.o, pv.acc.F, pv.acc.T, pv.Fpot, pv.Tpot,
-                     pv.PF, pv.PT, pv.Flink, pv.Tlink, pv.Ftot, pv.Ttot};
-  for (double *z : zero3) CU(cudaMemsetAsync(z, 0, n3, c->stream));
-  CU(cudaMemsetAsync(pv.q, 0, sizeof(double) * 4 * (size_t)n, c->stream));
   CU(cudaMemsetAsync(pv.kin, 0, sizeof(float4) * 3 * (size_t)n, c->stream));
   CU(cudaMemsetAsync(pv.kin_next, 0, sizeof(float4) * 3 * (size_t)n, c->stream));
-  CU(cudaMemsetAsync(pv.acc.K, 0, sizeof(int) * 3 * (size_t)n, c->stream));
-  CU(cudaMemsetAsync(pv.acc.IT, 0, sizeof(int) * 3 * (size_t)n, c->stream));
+  CU(cudaMalloc(&pv.box, sizeof(int) * 6 * (size_t)n));
+  CU(cudaMemsetAsync(pv.box, 0, sizeof(int) * 6 * (size_t)n, c->stream));
+  CU(cudaMalloc(&pv.stage, sizeof(double) * 13 * (size_t)n));
+  CU(cudaMalloc(&pv.lsum, sizeof(double) * 27 * (size_t)n));
+  CU(cudaMemsetAsync(pv.lsum, 0, sizeof(double) * 27 * (size_t)n, c->stream));
+  CU(cudaMalloc(&pv.lsum_i, sizeof(int) * 6 * (size_t)n));
+  CU(cudaMemsetAsync(pv.lsum_i, 0, sizeof(int) * 6 * (size_t)n, c->stream));
+  CU(cudaMalloc(&pv.vw, sizeof(float) * 6 * (size_t)n));
+  CU(cudaMemsetAsync(pv.vw, 0, sizeof(float) * 6 * (size_t)n, c->stream));
+  CU(cudaMalloc(&pv.cK, sizeof(int) * 3 * (size_t)n));
+  CU(cudaMalloc(&pv.cIT, sizeof(int) * 3 * (size_t)n));
+  CU(cudaMemsetAsync(pv.cK, 0, sizeof(int) * 3 * (size_t)n, c->stream));
+  CU(cudaMemsetAsync(pv.cIT, 0, sizeof(int) * 3 * (size_t)n, c->stream));
+  // per-cell lists: bounce links (at most ~6 per node of a shell of radius
+  // max(R) + 1) and nodes touched by one re-discretisation (at most the box)
+  const double rmax = fmax(c->pp.R_par, c->pp.R_perp);
+  const double lk_cap = 6.0 * 4.0 * M_PI * (rmax + 1.0) * (rmax + 1.0) + 64.0;
+  const double box = 2.0 * rmax + 4.0;
+  const double t_cap = box * box * box;
+  if (lk_cap * n > 2.0e9 || t_cap * n > 2.0e9 || n > 65535) return fail(c, BL_EINVAL, "cell lists too large");
+  pv.lk_cap = (int)lk_cap;
+  pv.touched_cap = (int)t_cap;
+  CU(cudaMalloc(&pv.lk, sizeof(unsigned long long) * (size_t)pv.lk_cap * n));
+  CU(cudaMalloc(&pv.lk_count, sizeof(int) * (size_t)n));
+  CU(cudaMemsetAsync(pv.lk_count, 0, sizeof(int) * (size_t)n, c->stream));
+  CU(cudaMalloc(&pv.touched, sizeof(unsigned long long) * (size_t)pv.touched_cap * n));
+  CU(cudaMalloc(&pv.touched_count, sizeof(int) * (size_t)n));
+  CU(cudaMemsetAsync(pv.touched_count, 0, sizeof(int) * (size_t)n, c->stream));
   // cell list bins: nb_k = max(1, floor(N_k / r_cut))
   const int dims[3] = {c->lv.nx, c->lv.ny, c->lv.nz};
   long long nbins = 1;
@@ -325,20 +325,6 @@ static int alloc_particles(bl_ctx *c, int n) {
   CU(cudaMalloc(&c->chg.count, sizeof(int)));
   CU(cudaMalloc(&c->chg.items, sizeof(int32_t) * 3 * (size_t)c->chg.cap));
   CU(cudaMemsetAsync(c->chg.count, 0, sizeof(int), c->stream));
-  // bounce links of one sweep: at most ~6 per node of a shell of radius
-  // max(R) around each cell, and never more than 18 per lattice node
-  {
-    const double rmax = fmax(c->pp.R_par, c->pp.R_perp) + 1.0;
-    double cap = 6.0 * 4.0 * M_PI * rmax * rmax * (double)n + 4096.0;
-    if (cap > 18.0 * (double)c->lv.N) cap = 18.0 * (double)c->lv.N;
-    if (cap > 1.5e9) return fail(c, BL_EINVAL, "link list too large");
-    c->links.cap = (int)cap;
-    CU(cudaMalloc(&c->links.count, sizeof(int)));
-    CU(cudaMalloc(&c->links.node, sizeof(uint32_t) * (size_t)c->links.cap));
-    CU(cudaMalloc(&c->links.pr, sizeof(uint32_t) * (size_t)c->links.cap));
-    CU(cudaMalloc(&c->links.rho, sizeof(float) * (size_t)c->links.cap));
-    CU(cudaMemsetAsync(c->links.count, 0, sizeof(int), c->stream));
-  }
   c->np = n;
   pv.n = n;
   return BL_OK;
@@ -415,9 +401,10 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
         return fail(c, BL_EINVAL, "cell %d: X outside [0, N)", i);
   }
   CU(cudaMemcpyAsync(c->pv.stage, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, c->stream));
-  launch_integrate_claim(c->lv, c->pv, c->claim, c->chg, first ? 1 : 2, c->stream, &c->launches);
-  launch_resolve_fill(c->dtype, c->lv, c->pv, c->claim, c->chg, c->links, c->parity, first ? 0 : 1, c->stream,
-                      &c->launches);
+  launch_set_state(c->lv, c->pv, first ? 1 : 2, c->stream, &c->launches);
+  launch_claims(c->lv, c->pv, c->claim, c->chg, first ? 1 : 2, c->stream, &c->launches);
+  launch_resolve_fill(c->dtype, c->lv, c->pv, c->claim, c->chg, c->parity, first ? 0 : 1, c->stream, &c->launches);
+  launch_geometry(c->lv, c->pv, c->stream, &c->launches);
   std::swap(c->pv.kin, c->pv.kin_next);
   if (check_launch(c, "particles_set")) return c->sticky;
   CU(cudaStreamSynchronize(c->stream));
@@ -426,27 +413,24 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
 
 static int enqueue_step(bl_ctx *c) {
   int slot;
-  const PartAcc pa = c->np ? c->pv.acc : PartAcc{nullptr, nullptr, nullptr, nullptr};
   group_begin(c, 0, &slot);
-  launch_lb_step(c->dtype, c->lv, c->parity, c->pv.kin, pa, c->wacc, c->links, c->status, c->stream);
+  launch_lb_step(c->dtype, c->lv, c->parity, c->wacc, c->status, c->stream);
   group_end(c, slot);
   c->launches++;
   if (c->np > 0) {
-    const bool move = c->pv.move != 0;
     group_begin(c, 1, &slot);
     launch_cell_list(c->lv, c->pv, c->cl, c->stream, &c->launches);
     group_end(c, slot);
     group_begin(c, 2, &slot);
-    launch_forces(c->lv, c->pv, c->cl, c->wrows, c->stream, &c->launches);
-    if (move) launch_link_zeta(c->lv, c->pv, c->links, c->stream, &c->launches);
+    launch_forces(c->lv, c->pv, c->cl, c->sbits, c->stream, &c->launches);
     group_end(c, slot);
     group_begin(c, 3, &slot);
-    launch_integrate_claim(c->lv, c->pv, c->claim, c->chg, 0, c->stream, &c->launches);
-    if (move) launch_link_correct(c->dtype, c->lv, c->parity, c->pv, c->links, c->stream, &c->launches);
+    launch_cell_step(c->dtype, c->lv, c->pv, c->parity, c->stream, &c->launches);
     group_end(c, slot);
     group_begin(c, 4, &slot);
-    launch_resolve_fill(c->dtype, c->lv, c->pv, c->claim, c->chg, c->links, c->parity ^ 1, 1, c->stream,
-                        &c->launches);
+    launch_claims(c->lv, c->pv, c->claim, c->chg, 0, c->stream, &c->launches);
+    launch_resolve_fill(c->dtype, c->lv, c->pv, c->claim, c->chg, c->parity ^ 1, 1, c->stream, &c->launches);
+    launch_geometry(c->lv, c->pv, c->stream, &c->launches);
     group_end(c, slot);
     std::swap(c->pv.kin, c->pv.kin_next);
   }
@@ -654,8 +638,8 @@ extern "C" void bl_destroy(bl_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   free_particles(c);
-  void *ptrs[] = {c->lv.pop, c->lv.owner, c->claim, c->status, c->wacc.F, c->wacc.K, c->wrows.row_start,
-                  c->wrows.row_x, c->row_count_dev, c->scratch};
+  void *ptrs[] = {c->lv.pop, c->lv.owner, c->lv.rho_b, c->claim, c->status, c->wacc.F, c->wacc.K,
+                  c->sbits.bits, c->scratch};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);

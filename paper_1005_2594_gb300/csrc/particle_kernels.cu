@@ -3,22 +3,33 @@
 //   cell list      count -> scan -> scatter -> per-bin sort, canonical (bin, id)
 //   potentials     Berne-Pechukas-scaled Hookean cell-cell pairs (Sec. III,
 //                  Eqs. phi, epsilon, sigma) and cell-wall spheres (Eq. sigmaw),
-//                  one warp per cell, FP32 arithmetic, FP64 result
-//   leap-frog      V, X and the lab-frame angular momentum L, exact quaternion
-//                  exponential (Sec. II; reading Q4), FP64, one block per cell;
-//                  the same block then claims the nodes its new ellipsoid covers
+//                  one block per cell, FP32 arithmetic, FP64 result
+//   cell update    one block per cell: sums its bounce links (Eq. deltap),
+//                  solves for the velocities of the half step (reading Q3),
+//                  adds the moving-boundary term C (Eq. c) to its bounced
+//                  populations, advances the cell (leap-frog on unit
+//                  quaternions, reading Q4) and claims the nodes its new
+//                  ellipsoid enters or leaves
 //   resolve        first-arrival owner rule (Sec. II single occupancy), then
 //                  fill/drain of every changed node with the momentum balance
 //                  given to the cells (Sec. II)
+//   geometry       each cell's bounce-link list and its contact-link sums
+//                  (Eqs. deltapppp, deltapppm) from the new owner map
+//   geometry       rebuilds each cell's bounce-link list and its contact-link
+//                  sums (Eqs. deltapppp, deltapppm) from the new owner map
 //
-// Ownership claims.  claim[] holds INT_MAX ("untouched") on every node
-// between steps.  In the claim pass each cell visits the nodes of the box
-// that holds both its old and its new ellipsoid: the current owner marks a
-// node it still covers with KEEP (INT_MIN) and one it leaves with TOUCHED
-// (INT_MAX - 1); any other cell covering the node writes its index; all
-// with atomicMin.  In the resolve pass the first visitor of a node takes the
-// claim with atomicExch(INT_MAX) and decodes: KEEP -> old owner, TOUCHED ->
-// fluid, a cell index -> the lowest index that newly covers the node.
+// Ownership claims.  claim[] holds INT_MAX ("free") on every node between
+// steps.  A cell marks each node of its box that its new ellipsoid enters
+// with its index (atomicMin: the lowest index among the newcomers) and each
+// node it owns but leaves with TOUCHED; both go to the cell's touched list.
+// Resolve takes each claim once (atomicExch back to free): TOUCHED alone ->
+// fluid; a newcomer index -> the old owner keeps the node if its new
+// ellipsoid still covers it (first arrival), else the newcomer takes it.
+//
+// FP64 is used only where the state needs it (positions, velocities, angular
+// momenta, the exact inside test near a surface); on this GPU a one-lane FP64
+// instruction costs a full warp slot of a narrow pipe, so sums, the 6 x 6
+// solve and the rotation increment are FP32 around FP64 reference values.
 #include <climits>
 
 #include "bl_internal.cuh"
@@ -27,7 +38,10 @@ namespace bl {
 
 constexpr int CLAIM_FREE = INT_MAX;
 constexpr int CLAIM_TOUCHED = INT_MAX - 1;
-constexpr int CLAIM_KEEP = INT_MIN;
+// the FP32 inside test decides when |s - 1| >= this; its error is below
+// 1e-5 for cells with half-axis ratios up to 100 (positions carried as an
+// integer node plus an FP32 fraction)
+constexpr float INSIDE_MARGIN = 1e-4f;
 
 // ---------------------------------------------------------------------------
 // cell list
@@ -204,112 +218,267 @@ __device__ __forceinline__ int bin_offsets(int nb, int per, int b, int out[3]) {
   return k;
 }
 
-__global__ void __launch_bounds__(128) k_forces(LatticeView lv, PartView pv, CellListView cl, WallRows wr) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// ---------------------------------------------------------------------------
+// block-wide helpers (blockDim.x == 256)
+
+constexpr int CB = 256;
+
+// sums v over the block; the result is valid in thread 0
+template <int K>
+__device__ __forceinline__ void block_sum(float (&v)[K], float (*sh)[K]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[wid][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < CB / 32; ++w)
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] += sh[w][k];
+  __syncthreads();
+}
+
+template <int K>
+__device__ __forceinline__ void block_sum_i(int (&v)[K], int (*sh)[K]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = __reduce_add_sync(0xffffffffu, v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[wid][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < CB / 32; ++w)
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] += sh[w][k];
+  __syncthreads();
+}
+
+// block-wide exclusive scan of one int per thread; returns the thread's
+// offset, writes the total to *total (all threads)
+__device__ __forceinline__ int block_scan(int v, int *sh_w, int *total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sh_w[wid] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < CB / 32; ++w) {
+      const int t = sh_w[w];
+      sh_w[w] = s;
+      s += t;
+    }
+    sh_w[CB / 32] = s;
+  }
+  __syncthreads();
+  const int off = sh_w[wid] + inc - v;
+  *total = sh_w[CB / 32];
+  __syncthreads();
+  return off;
+}
+
+// per-warp append to a list whose length lives in shared memory: returns the
+// first slot of this lane's cnt entries (one shared atomic per warp)
+__device__ __forceinline__ int warp_append(int cnt, int *sh_len) {
   const int lane = threadIdx.x & 31;
-  if (i >= pv.n) return;
+  int inc = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  const int tot = __shfl_sync(0xffffffffu, inc, 31);
+  int base = 0;
+  if (lane == 31 && tot) base = atomicAdd(sh_len, tot);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + inc - cnt;
+}
+
+__device__ __forceinline__ void node_xyz(const LatticeView &lv, unsigned n, int xyz[3]) {
+  xyz[0] = n % lv.nx;
+  xyz[1] = (n / lv.nx) % lv.ny;
+  xyz[2] = n / ((unsigned)lv.nx * lv.ny);
+}
+
+__device__ __forceinline__ unsigned node_of(const LatticeView &lv, int x, int y, int z) {
+  return (unsigned)x + (unsigned)lv.nx * ((unsigned)y + (unsigned)lv.ny * z);
+}
+
+// walks the nodes of an inclusive box, CB threads at a time, without
+// dividing per node: thread t starts at node t and advances by CB
+struct BoxIter {
+  int bx, by, bz, total;
+  int ix, iy, iz, dx, dy, dz;
+  __device__ void init(const int lo[3], const int hi[3]) {
+    bx = hi[0] - lo[0] + 1;
+    by = hi[1] - lo[1] + 1;
+    bz = hi[2] - lo[2] + 1;
+    total = (bx > 0 && by > 0 && bz > 0) ? bx * by * bz : 0;
+    if (!total) return;
+    const int t = threadIdx.x;
+    iz = t / (bx * by);
+    iy = (t / bx) % by;
+    ix = t % bx;
+    dz = CB / (bx * by);
+    dy = (CB / bx) % by;
+    dx = CB % bx;
+  }
+  __device__ void advance() {
+    ix += dx;
+    int c = 0;
+    if (ix >= bx) {
+      ix -= bx;
+      c = 1;
+    }
+    iy += dy + c;
+    c = 0;
+    if (iy >= by) {
+      iy -= by;
+      c = 1;
+    }
+    iz += dz + c;
+  }
+};
+
+// slot where the sweep of parity par bounced direction r of fluid node y
+__device__ __forceinline__ unsigned bounce_slot(const LatticeView &lv, int par, unsigned y, const int yc[3], int r) {
+  using D = D3Q19;
+  if (par == 0) {
+    const unsigned nb = node_of(lv, wrapi(yc[0] + D::cx(r), lv.nx), wrapi(yc[1] + D::cy(r), lv.ny),
+                                wrapi(yc[2] + D::cz(r), lv.nz));
+    return (unsigned)r * lv.N + nb;
+  }
+  return (unsigned)D::opp(r) * lv.N + y;
+}
+
+// ---------------------------------------------------------------------------
+// potentials: one block per cell.  Warp 0 takes the pairs (one lane per
+// neighbouring bin), all threads take the rows (y, z) of the wall-sphere
+// range around the cell.
+
+__global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, CellListView cl, SurfBits sb) {
+  __shared__ float sh[CB / 32][6];
+  const int i = blockIdx.x;
   const float4 a0 = pv.kin[3 * i], a1 = pv.kin[3 * i + 1], a2 = pv.kin[3 * i + 2];
   const int Xi[3] = {(int)a0.w, (int)a1.w, (int)a2.w};
   const float fi[3] = {a0.x, a0.y, a0.z};
   const float oi[3] = {(float)pv.o[3 * i], (float)pv.o[3 * i + 1], (float)pv.o[3 * i + 2]};
   const int dims[3] = {lv.nx, lv.ny, lv.nz};
   float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
-  // pairs over the neighbouring bins
-  const int bin = cl.bin_of[i];
-  const int bc[3] = {bin % cl.nb[0], (bin / cl.nb[0]) % cl.nb[1], bin / (cl.nb[0] * cl.nb[1])};
-  int off[3][3], noff[3];
-  for (int k = 0; k < 3; ++k) noff[k] = bin_offsets(cl.nb[k], lv.per[k], bc[k], off[k]);
-  const float rc2 = pv.r_cut * pv.r_cut;
-  for (int iz = 0; iz < noff[2]; ++iz)
-    for (int iy = 0; iy < noff[1]; ++iy)
-      for (int ix = 0; ix < noff[0]; ++ix) {
-        const int bx = wrapi(bc[0] + off[0][ix], cl.nb[0]);
-        const int by = wrapi(bc[1] + off[1][iy], cl.nb[1]);
-        const int bz = wrapi(bc[2] + off[2][iz], cl.nb[2]);
-        const int b = bx + cl.nb[0] * (by + cl.nb[1] * bz);
-        const int e = cl.start[b + 1];
-        for (int k = cl.start[b] + lane; k < e; k += 32) {
-          const int j = cl.ids[k];
-          if (j == i) continue;
-          const float4 b0 = pv.kin[3 * j], b1 = pv.kin[3 * j + 1], b2 = pv.kin[3 * j + 2];
-          const int Xj[3] = {(int)b0.w, (int)b1.w, (int)b2.w};
-          const float fj[3] = {b0.x, b0.y, b0.z};
-          float r[3];
-          for (int m = 0; m < 3; ++m) r[m] = (float)imin_image(Xj[m] - Xi[m], dims[m], lv.per[m]) + (fj[m] - fi[m]);
-          if (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] >= rc2) continue;
-          const float oj[3] = {(float)pv.o[3 * j], (float)pv.o[3 * j + 1], (float)pv.o[3 * j + 2]};
-          bp_pair(r, oi, oj, pv, F, T);
-        }
+  if (threadIdx.x < 27) {
+    const int bin = cl.bin_of[i];
+    const int bc[3] = {bin % cl.nb[0], (bin / cl.nb[0]) % cl.nb[1], bin / (cl.nb[0] * cl.nb[1])};
+    int off[3][3], noff[3];
+    for (int k = 0; k < 3; ++k) noff[k] = bin_offsets(cl.nb[k], lv.per[k], bc[k], off[k]);
+    const int ix = threadIdx.x % 3, iy = (threadIdx.x / 3) % 3, iz = threadIdx.x / 9;
+    if (ix < noff[0] && iy < noff[1] && iz < noff[2]) {
+      const int bx = wrapi(bc[0] + off[0][ix], cl.nb[0]);
+      const int by = wrapi(bc[1] + off[1][iy], cl.nb[1]);
+      const int bz = wrapi(bc[2] + off[2][iz], cl.nb[2]);
+      const int b = bx + cl.nb[0] * (by + cl.nb[1] * bz);
+      const float rc2 = pv.r_cut * pv.r_cut;
+      const int e = cl.start[b + 1];
+      for (int k = cl.start[b]; k < e; ++k) {
+        const int j = cl.ids[k];
+        if (j == i) continue;
+        const float4 b0 = pv.kin[3 * j], b1 = pv.kin[3 * j + 1], b2 = pv.kin[3 * j + 2];
+        const int Xj[3] = {(int)b0.w, (int)b1.w, (int)b2.w};
+        const float fj[3] = {b0.x, b0.y, b0.z};
+        float r[3];
+        for (int m = 0; m < 3; ++m) r[m] = (float)imin_image(Xj[m] - Xi[m], dims[m], lv.per[m]) + (fj[m] - fi[m]);
+        if (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] >= rc2) continue;
+        const float oj[3] = {(float)pv.o[3 * j], (float)pv.o[3 * j + 1], (float)pv.o[3 * j + 2]};
+        bp_pair(r, oi, oj, pv, F, T);
       }
-  // surface wall nodes in the rows of the box around the cell
-  if (wr.row_start) {
+    }
+  }
+  if (sb.bits) {
     const int R = (int)ceilf(pv.sigw_max) + 1;
     const int side = 2 * R + 1;
-    for (int t = lane; t < side * side; t += 32) {
+    const float rw2 = pv.sigw_max * pv.sigw_max;
+    for (int t = threadIdx.x; t < side * side; t += CB) {
       int y = Xi[1] - R + t % side, z = Xi[2] - R + t / side;
+      const float ry = (float)(y - Xi[1]) - fi[1], rz = (float)(z - Xi[2]) - fi[2];
+      if (ry * ry + rz * rz >= rw2) continue;
       if (lv.per[1]) y = wrapi(y, lv.ny);
       else if (y < 0 || y >= lv.ny) continue;
       if (lv.per[2]) z = wrapi(z, lv.nz);
       else if (z < 0 || z >= lv.nz) continue;
-      const int row = y + lv.ny * z;
-      const int s = wr.row_start[row], e = wr.row_start[row + 1];
-      if (s == e) continue;
-      const float ry = (float)imin_image(y - Xi[1], lv.ny, lv.per[1]) - fi[1];
-      const float rz = (float)imin_image(z - Xi[2], lv.nz, lv.per[2]) - fi[2];
-      if (ry * ry + rz * rz >= pv.sigw_max * pv.sigw_max) continue;
-      // x range [Xi - R, Xi + R], split where it wraps
-      int ra[3], rb[3], nr = 0;
-      const int xlo = Xi[0] - R, xhi = Xi[0] + R;
-      if (2 * R + 1 >= lv.nx) {
-        ra[0] = 0; rb[0] = lv.nx - 1; nr = 1;
-      } else if (!lv.per[0]) {
-        ra[0] = max(xlo, 0); rb[0] = min(xhi, lv.nx - 1); nr = 1;
-      } else {
-        ra[nr] = max(xlo, 0); rb[nr] = min(xhi, lv.nx - 1); ++nr;
-        if (xlo < 0) { ra[nr] = xlo + lv.nx; rb[nr] = lv.nx - 1; ++nr; }
-        if (xhi >= lv.nx) { ra[nr] = 0; rb[nr] = xhi - lv.nx; ++nr; }
-      }
-      for (int q = 0; q < nr; ++q) {
-        int lo = s, hi = e;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (wr.row_x[mid] < ra[q]) lo = mid + 1;
-          else hi = mid;
-        }
-        for (int k = lo; k < e && wr.row_x[k] <= rb[q]; ++k) {
-          const int xw = wr.row_x[k];
-          const float rx = (float)imin_image(xw - Xi[0], lv.nx, lv.per[0]) - fi[0];
-          const float r[3] = {rx, ry, rz};
-          bp_wall(r, oi, pv, F, T);
-        }
+      const uint32_t *row = sb.bits + (size_t)(y + lv.ny * z) * sb.nxw;
+      for (int dx = -R; dx <= R; ++dx) {
+        int x = Xi[0] + dx;
+        if (lv.per[0]) x = wrapi(x, lv.nx);
+        else if (x < 0 || x >= lv.nx) continue;
+        if (!((row[x >> 5] >> (x & 31)) & 1u)) continue;
+        const float r[3] = {(float)dx - fi[0], ry, rz};
+        bp_wall(r, oi, pv, F, T);
       }
     }
   }
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    F[m] = warp_sum(F[m]);
-    T[m] = warp_sum(T[m]);
-  }
-  if (lane == 0)
+  float v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
+  block_sum<6>(v, sh);
+  if (threadIdx.x == 0)
     for (int m = 0; m < 3; ++m) {
-      pv.Fpot[3 * i + m] = (double)F[m];
-      pv.Tpot[3 * i + m] = (double)T[m];
+      pv.Fpot[3 * i + m] = (double)v[m];
+      pv.Tpot[3 * i + m] = (double)v[3 + m];
     }
 }
 
 // ---------------------------------------------------------------------------
-// leap-frog and claims
+// rigid-body helpers
 
-__device__ void omega_from_L(const PartView &pv, const double q[4], const double L[3], double Om[3]) {
-  const double w = q[0], x = q[1], y = q[2], z = q[3];
-  double R[3][3];
+__device__ void rotmat_f(const double q[4], float R[3][3]) {
+  const float w = (float)q[0], x = (float)q[1], y = (float)q[2], z = (float)q[3];
   R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z);     R[0][2] = 2 * (x * z + w * y);
   R[1][0] = 2 * (x * y + w * z);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
   R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
-  double Lb[3];
-  for (int i = 0; i < 3; ++i) Lb[i] = R[0][i] * L[0] + R[1][i] * L[1] + R[2][i] * L[2];
-  const double wb[3] = {Lb[0] / pv.Iperp, Lb[1] / pv.Iperp, Lb[2] / pv.Ipar};
-  for (int i = 0; i < 3; ++i) Om[i] = R[i][0] * wb[0] + R[i][1] * wb[1] + R[i][2] * wb[2];
+}
+
+// I_lab = R diag(I_perp, I_perp, I_par) R^T and its inverse (FP32)
+__device__ void inertia_f(const PartView &pv, const double q[4], float I[3][3], float Iinv[3][3]) {
+  float R[3][3];
+  rotmat_f(q, R);
+  const float d[3] = {(float)pv.Iperp, (float)pv.Iperp, (float)pv.Ipar};
+  const float di[3] = {1.0f / d[0], 1.0f / d[1], 1.0f / d[2]};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      I[a][b] = R[a][0] * d[0] * R[b][0] + R[a][1] * d[1] * R[b][1] + R[a][2] * d[2] * R[b][2];
+      Iinv[a][b] = R[a][0] * di[0] * R[b][0] + R[a][1] * di[1] * R[b][1] + R[a][2] * di[2] * R[b][2];
+    }
+}
+
+// A x = b, A symmetric positive definite 6 x 6 (Cholesky, FP32)
+__device__ void solve_spd6f(float A[6][6], const float b[6], float x[6]) {
+  for (int j = 0; j < 6; ++j) {
+    float d = A[j][j];
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    d = sqrtf(d);
+    A[j][j] = d;
+    const float id = 1.0f / d;
+    for (int i = j + 1; i < 6; ++i) {
+      float v = A[i][j];
+      for (int k = 0; k < j; ++k) v -= A[i][k] * A[j][k];
+      A[i][j] = v * id;
+    }
+  }
+  float y[6];
+  for (int i = 0; i < 6; ++i) {
+    float v = b[i];
+    for (int k = 0; k < i; ++k) v -= A[i][k] * y[k];
+    y[i] = v / A[i][i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    float v = y[i];
+    for (int k = i + 1; k < 6; ++k) v -= A[k][i] * x[k];
+    x[i] = v / A[i][i];
+  }
 }
 
 __device__ void write_kin(const PartView &pv, int p, const double X[3], const double V[3], const double Om[3]) {
@@ -323,52 +492,44 @@ __device__ void write_kin(const PartView &pv, int p, const double X[3], const do
   pv.kin_next[3 * p + 2] = make_float4((float)Om[0], (float)Om[1], (float)Om[2], (float)Xi[2]);
 }
 
-__device__ void aabb(const PartView &pv, const double X[3], const double o[3], int lo[3], int hi[3]) {
+// X += V (wrapped), q <- exp(W / 2) (x) q with the rotation increment in FP32
+// and a first-order renormalisation (|q|^2 - 1 is O(1e-7))
+__device__ void rigid_advance(const LatticeView &lv, double X[3], double q[4], const double V[3], const double W[3]) {
+  const int dims[3] = {lv.nx, lv.ny, lv.nz};
   for (int k = 0; k < 3; ++k) {
-    const double h = sqrt(pv.R_perp * pv.R_perp * (1.0 - o[k] * o[k]) + pv.R_par * pv.R_par * o[k] * o[k]) + 0.01;
-    lo[k] = (int)floor(X[k] - h);
-    hi[k] = (int)ceil(X[k] + h);
-  }
-}
-
-__device__ void inertia_lab(const PartView &pv, const double q[4], double I[3][3]) {
-  const double w = q[0], x = q[1], y = q[2], z = q[3];
-  double R[3][3];
-  R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z);     R[0][2] = 2 * (x * z + w * y);
-  R[1][0] = 2 * (x * y + w * z);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
-  R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
-  const double d[3] = {pv.Iperp, pv.Iperp, pv.Ipar};
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) I[i][j] = R[i][0] * d[0] * R[j][0] + R[i][1] * d[1] * R[j][1] + R[i][2] * d[2] * R[j][2];
-}
-
-// A x = b, A symmetric positive definite 6 x 6 (Cholesky)
-__device__ void solve_spd6(double A[6][6], const double b[6], double x[6]) {
-  for (int j = 0; j < 6; ++j) {
-    double d = A[j][j];
-    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
-    d = sqrt(d);
-    A[j][j] = d;
-    for (int i = j + 1; i < 6; ++i) {
-      double v = A[i][j];
-      for (int k = 0; k < j; ++k) v -= A[i][k] * A[j][k];
-      A[i][j] = v / d;
+    X[k] += V[k];
+    if (lv.per[k]) {
+      if (X[k] < 0.0) X[k] += (double)dims[k];
+      else if (X[k] >= (double)dims[k]) X[k] -= (double)dims[k];
     }
   }
-  double y[6];
-  for (int i = 0; i < 6; ++i) {
-    double v = b[i];
-    for (int k = 0; k < i; ++k) v -= A[i][k] * y[k];
-    y[i] = v / A[i][i];
-  }
-  for (int i = 5; i >= 0; --i) {
-    double v = y[i];
-    for (int k = i + 1; k < 6; ++k) v -= A[k][i] * x[k];
-    x[i] = v / A[i][i];
+  const float wx = (float)W[0], wy = (float)W[1], wz = (float)W[2];
+  const float th = sqrtf(wx * wx + wy * wy + wz * wz);
+  if (!(th > 0.f)) return;
+  float sn, cs;
+  sincosf(0.5f * th, &sn, &cs);
+  const float sh = sn / th;
+  const double dq[4] = {cs, wx * sh, wy * sh, wz * sh};
+  double nq[4];
+  nq[0] = dq[0] * q[0] - dq[1] * q[1] - dq[2] * q[2] - dq[3] * q[3];
+  nq[1] = dq[0] * q[1] + dq[1] * q[0] + dq[2] * q[3] - dq[3] * q[2];
+  nq[2] = dq[0] * q[2] - dq[1] * q[3] + dq[2] * q[0] + dq[3] * q[1];
+  nq[3] = dq[0] * q[3] + dq[1] * q[2] - dq[2] * q[1] + dq[3] * q[0];
+  const double nn = nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3];
+  const double c = 1.5 - 0.5 * nn;  // 1 / sqrt(nn) to second order in (nn - 1)
+  for (int k = 0; k < 4; ++k) q[k] = nq[k] * c;
+}
+
+__device__ void aabb(const PartView &pv, const double X[3], const double o[3], int lo[3], int hi[3]) {
+  for (int k = 0; k < 3; ++k) {
+    const float ok = (float)o[k];
+    const float h = sqrtf((float)(pv.R_perp * pv.R_perp) * (1.0f - ok * ok) + (float)(pv.R_par * pv.R_par) * ok * ok) + 0.01f;
+    lo[k] = (int)floorf((float)X[k] - h);
+    hi[k] = (int)ceilf((float)X[k] + h);
   }
 }
 
-// inside test: FP32 filter, exact FP64 re-evaluation within 1e-3 of the surface
+// inside test: FP32 filter, exact FP64 re-evaluation near the surface
 __device__ __forceinline__ bool inside_cell(int x, int y, int z, const double *X, const double *o, const float *Xf,
                                             const int *Xi, const float *of, const PartView &pv, const LatticeView &lv) {
   const float d0 = (float)imin_image(x - Xi[0], lv.nx, lv.per[0]) - Xf[0];
@@ -377,182 +538,250 @@ __device__ __forceinline__ bool inside_cell(int x, int y, int z, const double *X
   const float dpar = d0 * of[0] + d1 * of[1] + d2 * of[2];
   const float dd = d0 * d0 + d1 * d1 + d2 * d2;
   const float s = dpar * dpar * (float)pv.inv_rpar2 + (dd - dpar * dpar) * (float)pv.inv_rperp2;
-  if (fabsf(s - 1.0f) >= 1e-3f) return s < 1.0f;
+  if (fabsf(s - 1.0f) >= INSIDE_MARGIN) return s < 1.0f;
   return inside_exact(x, y, z, X, o, pv.inv_rpar2, pv.inv_rperp2, lv);
 }
 
-// mode 0: time step (integrate, then claim if cells move)
-// mode 1: first particles_set (state from stage, every old owner is fluid)
-// mode 2: later particles_set (state from stage, first-arrival claims)
-__global__ void __launch_bounds__(256) k_integrate_claim(LatticeView lv, PartView pv, int *claim, ChangeList chg,
-                                                         int mode) {
-  const int p = blockIdx.x;
-  __shared__ double sX[3], so[3];
-  __shared__ int slo[3], shi[3];
-  __shared__ int sactive;
-  if (threadIdx.x == 0) {
-    if (p == 0) *chg.count = 0;
-    double X[3], q[4], V[3], L[3], Om[3], o_old[3];
+struct CellGeo {
+  double X[3], o[3];
+  float Xf[3], of[3];
+  int Xi[3];
+};
+
+__device__ __forceinline__ void cell_geo(const PartView &pv, int p, CellGeo &g) {
+  for (int k = 0; k < 3; ++k) {
+    g.X[k] = pv.X[3 * p + k];
+    g.o[k] = pv.o[3 * p + k];
+    g.Xi[k] = (int)rint(g.X[k]);
+    g.Xf[k] = (float)(g.X[k] - (double)g.Xi[k]);
+    g.of[k] = (float)g.o[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// implicit coupling (reading Q3).  The sweep bounced each cell's links
+// without C and appended them to the cell's segment.  With the predictor
+// (Vp, Wp) = velocities of t-1/2 the link momentum is (2 f*_r + C(Vp, Wp)) c_r;
+// the link kernel sums it (variable part in FP32, 2 alpha_r rho_bar c_r as
+// exact integers) with the drag matrices Z = sum (m_r / 6) rho [c; a x c][c;
+// a x c]^T.  The half-step velocities V = Vp + dV, W = Wp + dW solve
+//   (m + Zff) dV + Zft dW = F_tot(Vp, Wp) - m (Vp - V(t-1/2))
+//   Ztf dV + (I + Ztt) dW = T_tot(Vp, Wp) + L(t-1/2) - I Wp,
+// and the correction kernel gives each bounced population C(V, W), so the
+// fluid and the cell exchange the same momentum.
+//
+// Link kernels run on a grid (chunk, cell): each block takes CB links of one
+// cell, reduces them, and adds the block's sums with one atomic per value.
+
+constexpr int LT = 128;            // threads of a link-sum block
+constexpr int LPT = 8;             // links per thread
+constexpr int LCHUNK = LT * LPT;   // links per link-sum block
+
+template <class S>
+__global__ void __launch_bounds__(LT) k_link_sums(LatticeView lv, PartView pv, int par) {
+  using D = D3Q19;
+  __shared__ float shf[LT / 32][27];
+  __shared__ int shi[LT / 32][6];
+  const int p = blockIdx.y;
+  const int nlk = min(pv.lk_count[p], pv.lk_cap);
+  const int first = blockIdx.x * LCHUNK;
+  if (first >= nlk) return;
+  const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
+  const S *pop = reinterpret_cast<const S *>(lv.pop);
+  const unsigned long long *lk = pv.lk + (size_t)p * pv.lk_cap;
+  float v[27];
+  int iv[6];
+#pragma unroll
+  for (int k = 0; k < 27; ++k) v[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) iv[k] = 0;
+  const int last = min(first + LCHUNK, nlk);
+  for (int i = first + threadIdx.x; i < last; i += LT) {
+    int yc[3], r;
+    unpack_xyzr(lk[i], yc, r);
+    const unsigned y = node_of(lv, yc[0], yc[1], yc[2]);
+    const float fs = Store<S>::ld(pop + bounce_slot(lv, par, y, yc, r));
+    const float rho = lv.rho_b[y];
+    const int di[3] = {imin_image(yc[0] - (int)k0.w, lv.nx, lv.per[0]), imin_image(yc[1] - (int)k1.w, lv.ny, lv.per[1]),
+                       imin_image(yc[2] - (int)k2.w, lv.nz, lv.per[2])};
+    const float c[3] = {(float)D::cx(r), (float)D::cy(r), (float)D::cz(r)};
+    const int m = D::m(r);
+    const float a[3] = {(float)di[0] + 0.5f * c[0] - k0.x, (float)di[1] + 0.5f * c[1] - k0.y,
+                        (float)di[2] + 0.5f * c[2] - k0.z};
+    const float b[3] = {a[1] * c[2] - a[2] * c[1], a[2] * c[0] - a[0] * c[2], a[0] * c[1] - a[1] * c[0]};
+    const float vb = c[0] * k1.x + c[1] * k1.y + c[2] * k1.z + b[0] * k2.x + b[1] * k2.y + b[2] * k2.z;
+    const float w = (m / 6.0f) * rho;
+    const float dp = 2.0f * fs - w * vb;  // 2 f~*_r + C(Vp, Wp), C = -(m_r / 6) rho c.v_b
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      X[k] = pv.X[3 * p + k];
-      V[k] = pv.V[3 * p + k];
-      L[k] = pv.L[3 * p + k];
-      Om[k] = pv.Om[3 * p + k];
+      v[k] += dp * c[k];
+      v[3 + k] += dp * b[k];  // a x (dp c) = dp (a x c)
     }
-    for (int k = 0; k < 4; ++k) q[k] = pv.q[4 * p + k];
-    const double Xold[3] = {X[0], X[1], X[2]};
-    axis_exact(q, o_old);
-    bool moved = true;
-    if (mode == 0) {
-      // link force: variable part (FP64 sums) + constant part from the exact
-      // integer sums, with f = X - rint(X) the fractional part the sweep used
-      const double c = pv.rho0 / 18.0;
-      double f[3], K[3], IT[3], Fl[3], Tl[3];
-      for (int k = 0; k < 3; ++k) {
-        f[k] = X[k] - rint(X[k]);
-        K[k] = (double)pv.acc.K[3 * p + k];
-        IT[k] = (double)pv.acc.IT[3 * p + k];
-      }
-      const double fxK[3] = {f[1] * K[2] - f[2] * K[1], f[2] * K[0] - f[0] * K[2], f[0] * K[1] - f[1] * K[0]};
-      double Ft[3], Tt[3];
-      for (int k = 0; k < 3; ++k) {
-        Fl[k] = pv.acc.F[3 * p + k] + c * K[k];
-        Tl[k] = pv.acc.T[3 * p + k] + c * (IT[k] - fxK[k]);
-        Ft[k] = Fl[k] + pv.Fpot[3 * p + k] + pv.PF[3 * p + k] + (pv.bfc ? pv.m * pv.g[k] : 0.0);
-        Tt[k] = Tl[k] + pv.Tpot[3 * p + k] + pv.PT[3 * p + k];
-        pv.Flink[3 * p + k] = Fl[k];
-        pv.Tlink[3 * p + k] = Tl[k];
-        pv.Ftot[3 * p + k] = Ft[k];
-        pv.Ttot[3 * p + k] = Tt[k];
-        pv.acc.F[3 * p + k] = 0.0;
-        pv.acc.T[3 * p + k] = 0.0;
-        pv.acc.K[3 * p + k] = 0;
-        pv.acc.IT[3 * p + k] = 0;
-        pv.PF[3 * p + k] = 0.0;
-        pv.PT[3 * p + k] = 0.0;
-      }
-      moved = pv.move != 0;
-      if (moved) {
-        // half-step velocities (reading Q3): the sweep bounced with the
-        // predictor (Vp, Wp) of the kinematics; the link force at (V, W) is
-        // F_link - Zff dV - Zft dW, dV = V - Vp, dW = W - Wp, and
-        //   (m + Zff) dV + Zft dW = F_tot - m (Vp - V(t-1/2))
-        //   Ztf dV + (I + Ztt) dW = T_tot + L(t-1/2) - I Wp
-        const float4 k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
-        const double Vp[3] = {k1.x, k1.y, k1.z}, Wp[3] = {k2.x, k2.y, k2.z};
-        double I[3][3], Z[6][6], A[6][6], rhs[6], d[6];
-        inertia_lab(pv, q, I);
-        const double *z = pv.zeta + 21 * p;
-        int k = 0;
-        for (int a = 0; a < 3; ++a)
-          for (int b = a; b < 3; ++b, ++k) Z[a][b] = Z[b][a] = z[k];
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b, ++k) Z[a][3 + b] = Z[3 + b][a] = z[k];
-        for (int a = 0; a < 3; ++a)
-          for (int b = a; b < 3; ++b, ++k) Z[3 + a][3 + b] = Z[3 + b][3 + a] = z[k];
-        for (int a = 0; a < 6; ++a)
-          for (int b = 0; b < 6; ++b) A[a][b] = Z[a][b];
-        for (int a = 0; a < 3; ++a) {
-          A[a][a] += pv.m;
-          for (int b = 0; b < 3; ++b) A[3 + a][3 + b] += I[a][b];
-          rhs[a] = Ft[a] - pv.m * (Vp[a] - V[a]);
-          rhs[3 + a] = Tt[a] + L[a] - (I[a][0] * Wp[0] + I[a][1] * Wp[1] + I[a][2] * Wp[2]);
-        }
-        solve_spd6(A, rhs, d);
-        for (int a = 0; a < 21; ++a) pv.zeta[21 * p + a] = 0.0;
-        for (int a = 0; a < 6; ++a) pv.dvel[6 * p + a] = (float)d[a];
-        // the link force at the solved velocities, and the totals of the step
-        for (int a = 0; a < 3; ++a) {
-          double dF = 0.0, dT = 0.0;
-          for (int b = 0; b < 6; ++b) {
-            dF += Z[a][b] * d[b];
-            dT += Z[3 + a][b] * d[b];
-          }
-          Fl[a] -= dF;
-          Tl[a] -= dT;
-          Ft[a] -= dF;
-          Tt[a] -= dT;
-          pv.Flink[3 * p + a] = Fl[a];
-          pv.Tlink[3 * p + a] = Tl[a];
-          pv.Ftot[3 * p + a] = Ft[a];
-          pv.Ttot[3 * p + a] = Tt[a];
-          V[a] = Vp[a] + d[a];
-          Om[a] = Wp[a] + d[3 + a];
-        }
-        for (int a = 0; a < 3; ++a) L[a] = I[a][0] * Om[0] + I[a][1] * Om[1] + I[a][2] * Om[2];
-        const int dims[3] = {lv.nx, lv.ny, lv.nz};
-        for (int a = 0; a < 3; ++a) {
-          X[a] += V[a];
-          if (lv.per[a]) {
-            if (X[a] < 0.0) X[a] += (double)dims[a];
-            else if (X[a] >= (double)dims[a]) X[a] -= (double)dims[a];
-          }
-        }
-        const double th = sqrt(Om[0] * Om[0] + Om[1] * Om[1] + Om[2] * Om[2]);
-        double dq[4] = {1.0, 0.0, 0.0, 0.0};
-        if (th > 0.0) {
-          double sn, cs;
-          sincos(0.5 * th, &sn, &cs);
-          const double sh = sn / th;
-          dq[0] = cs;
-          dq[1] = Om[0] * sh;
-          dq[2] = Om[1] * sh;
-          dq[3] = Om[2] * sh;
-        }
-        double nq[4];
-        nq[0] = dq[0] * q[0] - dq[1] * q[1] - dq[2] * q[2] - dq[3] * q[3];
-        nq[1] = dq[0] * q[1] + dq[1] * q[0] + dq[2] * q[3] - dq[3] * q[2];
-        nq[2] = dq[0] * q[2] - dq[1] * q[3] + dq[2] * q[0] + dq[3] * q[1];
-        nq[3] = dq[0] * q[3] + dq[1] * q[2] - dq[2] * q[1] + dq[3] * q[0];
-        const double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
-        for (int k = 0; k < 4; ++k) q[k] = nq[k] / nn;
-      }
-    } else {
-      const double *st = pv.stage + 13 * p;
-      for (int k = 0; k < 3; ++k) {
-        X[k] = st[k];
-        V[k] = st[7 + k];
-        L[k] = st[10 + k];
-      }
-      for (int k = 0; k < 4; ++k) q[k] = st[3 + k];
-      omega_from_L(pv, q, L, Om);
+    int k = 6;
+#pragma unroll
+    for (int s2 = 0; s2 < 3; ++s2)
+#pragma unroll
+      for (int t = s2; t < 3; ++t) v[k++] += w * c[s2] * c[t];
+#pragma unroll
+    for (int s2 = 0; s2 < 3; ++s2)
+#pragma unroll
+      for (int t = 0; t < 3; ++t) v[k++] += w * c[s2] * b[t];
+#pragma unroll
+    for (int s2 = 0; s2 < 3; ++s2)
+#pragma unroll
+      for (int t = s2; t < 3; ++t) v[k++] += w * b[s2] * b[t];
+    iv[0] += m * D::cx(r);
+    iv[1] += m * D::cy(r);
+    iv[2] += m * D::cz(r);
+    iv[3] += m * (di[1] * D::cz(r) - di[2] * D::cy(r));
+    iv[4] += m * (di[2] * D::cx(r) - di[0] * D::cz(r));
+    iv[5] += m * (di[0] * D::cy(r) - di[1] * D::cx(r));
+  }
+  // warp sums, then one thread per value adds the warps and issues the atomic
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const float t = warp_sum(v[k]);
+    if (lane == 0) shf[wid][k] = t;
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int t = __reduce_add_sync(0xffffffffu, iv[k]);
+    if (lane == 0) shi[wid][k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 27) {
+    float t = 0.f;
+    for (int w2 = 0; w2 < LT / 32; ++w2) t += shf[w2][threadIdx.x];
+    atomicAdd(&pv.lsum[27 * p + threadIdx.x], (double)t);
+  } else if (threadIdx.x >= 32 && threadIdx.x < 38) {
+    int t = 0;
+    for (int w2 = 0; w2 < LT / 32; ++w2) t += shi[w2][threadIdx.x - 32];
+    atomicAdd(&pv.lsum_i[6 * p + threadIdx.x - 32], t);
+  }
+}
+
+// one thread per cell: link force at the predictor, 6 x 6 solve, leap-frog,
+// kinematics and claim box of the next step
+__global__ void k_solve(LatticeView lv, PartView pv) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pv.n) return;
+  const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
+  double X[3], q[4], V[3], L[3], W[3], Xold[3], o_old[3];
+  for (int k = 0; k < 3; ++k) {
+    X[k] = pv.X[3 * p + k];
+    V[k] = pv.V[3 * p + k];
+    L[k] = pv.L[3 * p + k];
+    W[k] = pv.Om[3 * p + k];
+    Xold[k] = X[k];
+    o_old[k] = pv.o[3 * p + k];
+  }
+  for (int k = 0; k < 4; ++k) q[k] = pv.q[4 * p + k];
+  double vd[6];
+  float v[27];
+  for (int k = 0; k < 27; ++k) {
+    v[k] = (float)pv.lsum[27 * p + k];
+    if (k < 6) vd[k] = pv.lsum[27 * p + k];
+    pv.lsum[27 * p + k] = 0.0;
+  }
+  double K[3], IT[3];
+  for (int k = 0; k < 3; ++k) {
+    K[k] = (double)(pv.lsum_i[6 * p + k] + pv.cK[3 * p + k]);
+    IT[k] = (double)(pv.lsum_i[6 * p + 3 + k] + pv.cIT[3 * p + k]);
+    pv.lsum_i[6 * p + k] = 0;
+    pv.lsum_i[6 * p + 3 + k] = 0;
+    pv.cK[3 * p + k] = 0;
+    pv.cIT[3 * p + k] = 0;
+  }
+  // link force at the predictor: variable part + exact constant part, with
+  // f = X - rint(X) the fraction the sweep's lever arms used
+  const double cst = pv.rho0 / 18.0;
+  double f[3];
+  for (int k = 0; k < 3; ++k) f[k] = X[k] - rint(X[k]);
+  const double fxK[3] = {f[1] * K[2] - f[2] * K[1], f[2] * K[0] - f[0] * K[2], f[0] * K[1] - f[1] * K[0]};
+  double Fl[3], Tl[3], Ft[3], Tt[3];
+  for (int k = 0; k < 3; ++k) {
+    Fl[k] = vd[k] + cst * K[k];
+    Tl[k] = vd[3 + k] + cst * (IT[k] - fxK[k]);
+    Ft[k] = Fl[k] + pv.Fpot[3 * p + k] + pv.PF[3 * p + k] + (pv.bfc ? pv.m * pv.g[k] : 0.0);
+    Tt[k] = Tl[k] + pv.Tpot[3 * p + k] + pv.PT[3 * p + k];
+    pv.PF[3 * p + k] = 0.0;
+    pv.PT[3 * p + k] = 0.0;
+  }
+  const double Vp[3] = {k1.x, k1.y, k1.z}, Wp[3] = {k2.x, k2.y, k2.z};
+  const bool move = pv.move != 0;
+  if (move) {
+    float Z[6][6];
+    {
+      int k = 6;
+      for (int s = 0; s < 3; ++s)
+        for (int t = s; t < 3; ++t, ++k) Z[s][t] = Z[t][s] = v[k];
+      for (int s = 0; s < 3; ++s)
+        for (int t = 0; t < 3; ++t, ++k) Z[s][3 + t] = Z[3 + t][s] = v[k];
+      for (int s = 0; s < 3; ++s)
+        for (int t = s; t < 3; ++t, ++k) Z[3 + s][3 + t] = Z[3 + t][3 + s] = v[k];
     }
+    float I[3][3], Iinv[3][3], A[6][6], rhs[6], d[6];
+    inertia_f(pv, q, I, Iinv);
+    for (int s = 0; s < 6; ++s)
+      for (int t = 0; t < 6; ++t) A[s][t] = Z[s][t];
+    for (int s = 0; s < 3; ++s) {
+      A[s][s] += (float)pv.m;
+      for (int t = 0; t < 3; ++t) A[3 + s][3 + t] += I[s][t];
+      // L(t-1/2) - I Wp: a small difference of O(I W) numbers, in FP64
+      const double IW = (double)I[s][0] * Wp[0] + (double)I[s][1] * Wp[1] + (double)I[s][2] * Wp[2];
+      rhs[s] = (float)(Ft[s] - pv.m * (Vp[s] - V[s]));
+      rhs[3 + s] = (float)(Tt[s] + (L[s] - IW));
+    }
+    solve_spd6f(A, rhs, d);
+    for (int s = 0; s < 3; ++s) {
+      float dF = 0.f, dT = 0.f;
+      for (int t = 0; t < 6; ++t) {
+        dF += Z[s][t] * d[t];
+        dT += Z[3 + s][t] * d[t];
+      }
+      Fl[s] -= dF;
+      Tl[s] -= dT;
+      Ft[s] -= dF;
+      Tt[s] -= dT;
+    }
+    for (int s = 0; s < 3; ++s) {
+      V[s] = Vp[s] + (double)d[s];
+      W[s] = Wp[s] + (double)d[3 + s];
+      L[s] += Tt[s];
+    }
+  }
+  for (int s = 0; s < 3; ++s) {
+    pv.Flink[3 * p + s] = Fl[s];
+    pv.Tlink[3 * p + s] = Tl[s];
+    pv.Ftot[3 * p + s] = Ft[s];
+    pv.Ttot[3 * p + s] = Tt[s];
+    pv.vw[6 * p + s] = (float)V[s];
+    pv.vw[6 * p + 3 + s] = (float)W[s];
+  }
+  int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+  if (move) {
+    rigid_advance(lv, X, q, V, W);
     for (int k = 0; k < 3; ++k) {
       pv.X[3 * p + k] = X[k];
       pv.V[3 * p + k] = V[k];
       pv.L[3 * p + k] = L[k];
-      pv.Om[3 * p + k] = Om[k];
+      pv.Om[3 * p + k] = W[k];
     }
     for (int k = 0; k < 4; ++k) pv.q[4 * p + k] = q[k];
     double o_new[3];
     axis_exact(q, o_new);
     for (int k = 0; k < 3; ++k) pv.o[3 * p + k] = o_new[k];
-    write_kin(pv, p, X, V, Om);
     bool finite = true;
-    for (int k = 0; k < 3; ++k)
-      finite = finite && isfinite(X[k]) && isfinite(o_new[k]) && (mode == 1 || (isfinite(Xold[k]) && isfinite(o_old[k])));
-    if (!finite) {
-      // a non-finite state is reported and its box left empty
-      atomicOr(pv.status, ST_UNSTABLE);
-      for (int k = 0; k < 3; ++k) {
-        pv.box[6 * p + k] = 0;
-        pv.box[6 * p + 3 + k] = -1;
-        slo[k] = 0;
-        shi[k] = -1;
-      }
-      sactive = 0;
-    } else {
-      int lo[3], hi[3], lo2[3], hi2[3];
+    for (int k = 0; k < 3; ++k) finite = finite && isfinite(X[k]) && isfinite(o_new[k]);
+    if (finite) {
+      int lo2[3], hi2[3];
       aabb(pv, X, o_new, lo, hi);
-      if (mode != 1) {
-        aabb(pv, Xold, o_old, lo2, hi2);
-        for (int k = 0; k < 3; ++k) {
-          lo[k] = min(lo[k], lo2[k]);
-          hi[k] = max(hi[k], hi2[k]);
-        }
-      }
+      aabb(pv, Xold, o_old, lo2, hi2);
       const int dims[3] = {lv.nx, lv.ny, lv.nz};
       for (int k = 0; k < 3; ++k) {
+        lo[k] = min(lo[k], lo2[k]);
+        hi[k] = max(hi[k], hi2[k]);
         if (!lv.per[k]) {
           lo[k] = max(lo[k], 0);
           hi[k] = min(hi[k], dims[k] - 1);
@@ -560,64 +789,241 @@ __global__ void __launch_bounds__(256) k_integrate_claim(LatticeView lv, PartVie
           lo[k] = 0;
           hi[k] = dims[k] - 1;
         }
-        pv.box[6 * p + k] = lo[k];
-        pv.box[6 * p + 3 + k] = hi[k];
-        slo[k] = lo[k];
-        shi[k] = hi[k];
-        sX[k] = X[k];
-        so[k] = o_new[k];
       }
-      sactive = moved ? 1 : 0;
-      if (!moved) pv.box[6 * p + 3] = pv.box[6 * p] - 1;  // empty box: nothing to resolve
+    } else {
+      atomicOr(pv.status, ST_UNSTABLE);
+    }
+  }
+  if (move)  // fixed cells keep the box of their last set: the geometry pass still needs it
+    for (int k = 0; k < 3; ++k) {
+      pv.box[6 * p + k] = lo[k];
+      pv.box[6 * p + 3 + k] = hi[k];
+    }
+  write_kin(pv, p, X, V, W);
+}
+
+// C(V, W) on every bounced population of a cell
+template <class S>
+__global__ void __launch_bounds__(CB) k_link_correct(LatticeView lv, PartView pv, int par) {
+  using D = D3Q19;
+  const int p = blockIdx.y;
+  const int nlk = min(pv.lk_count[p], pv.lk_cap);
+  const int i = blockIdx.x * CB + threadIdx.x;
+  if (i >= nlk) return;
+  const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
+  const float *vw = pv.vw + 6 * p;
+  S *pop = reinterpret_cast<S *>(lv.pop);
+  int yc[3], r;
+  unpack_xyzr(pv.lk[(size_t)p * pv.lk_cap + i], yc, r);
+  const unsigned y = node_of(lv, yc[0], yc[1], yc[2]);
+  const unsigned slot = bounce_slot(lv, par, y, yc, r);
+  const float c[3] = {(float)D::cx(r), (float)D::cy(r), (float)D::cz(r)};
+  const float a[3] = {(float)imin_image(yc[0] - (int)k0.w, lv.nx, lv.per[0]) + 0.5f * c[0] - k0.x,
+                      (float)imin_image(yc[1] - (int)k1.w, lv.ny, lv.per[1]) + 0.5f * c[1] - k0.y,
+                      (float)imin_image(yc[2] - (int)k2.w, lv.nz, lv.per[2]) + 0.5f * c[2] - k0.z};
+  const float vbx = vw[0] + (vw[4] * a[2] - vw[5] * a[1]);
+  const float vby = vw[1] + (vw[5] * a[0] - vw[3] * a[2]);
+  const float vbz = vw[2] + (vw[3] * a[1] - vw[4] * a[0]);
+  const float C = -(D::m(r) / 6.0f) * lv.rho_b[y] * (c[0] * vbx + c[1] * vby + c[2] * vbz);
+  Store<S>::st(pop + slot, Store<S>::ld(pop + slot) + C);
+}
+
+// particles_set: the state comes from the stage.  mode 1: first set (the
+// box holds the new ellipsoid); mode 2: later set (old and new ellipsoid)
+__global__ void k_set_state(LatticeView lv, PartView pv, int mode) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pv.n) return;
+  double Xold[3], o_old[3];
+  for (int k = 0; k < 3; ++k) {
+    Xold[k] = pv.X[3 * p + k];
+    o_old[k] = pv.o[3 * p + k];
+  }
+  const double *st = pv.stage + 13 * p;
+  double X[3], q[4], V[3], L[3], W[3];
+  for (int k = 0; k < 3; ++k) {
+    X[k] = st[k];
+    V[k] = st[7 + k];
+    L[k] = st[10 + k];
+  }
+  for (int k = 0; k < 4; ++k) q[k] = st[3 + k];
+  float I[3][3], Iinv[3][3];
+  inertia_f(pv, q, I, Iinv);
+  for (int k = 0; k < 3; ++k)
+    W[k] = (double)(Iinv[k][0] * (float)L[0] + Iinv[k][1] * (float)L[1] + Iinv[k][2] * (float)L[2]);
+  for (int k = 0; k < 3; ++k) {
+    pv.X[3 * p + k] = X[k];
+    pv.V[3 * p + k] = V[k];
+    pv.L[3 * p + k] = L[k];
+    pv.Om[3 * p + k] = W[k];
+    pv.vw[6 * p + k] = (float)V[k];
+    pv.vw[6 * p + 3 + k] = (float)W[k];
+  }
+  for (int k = 0; k < 4; ++k) pv.q[4 * p + k] = q[k];
+  double o_new[3];
+  axis_exact(q, o_new);
+  for (int k = 0; k < 3; ++k) pv.o[3 * p + k] = o_new[k];
+  write_kin(pv, p, X, V, W);
+  int lo[3], hi[3], lo2[3], hi2[3];
+  aabb(pv, X, o_new, lo, hi);
+  bool finite = isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2]);
+  if (mode == 2) {
+    finite = finite && isfinite(Xold[0]) && isfinite(Xold[1]) && isfinite(Xold[2]);
+    aabb(pv, Xold, o_old, lo2, hi2);
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = min(lo[k], lo2[k]);
+      hi[k] = max(hi[k], hi2[k]);
+    }
+  }
+  const int dims[3] = {lv.nx, lv.ny, lv.nz};
+  for (int k = 0; k < 3; ++k) {
+    if (!finite) {
+      lo[k] = 0;
+      hi[k] = -1;
+    } else if (!lv.per[k]) {
+      lo[k] = max(lo[k], 0);
+      hi[k] = min(hi[k], dims[k] - 1);
+    } else if (hi[k] - lo[k] + 1 > dims[k]) {
+      lo[k] = 0;
+      hi[k] = dims[k] - 1;
+    }
+    pv.box[6 * p + k] = lo[k];
+    pv.box[6 * p + 3 + k] = hi[k];
+  }
+  if (!finite) atomicOr(pv.status, ST_UNSTABLE);
+}
+
+// claims over each cell's box (one block per cell), appended to its touched
+// list; also clears the cell's link segment for the next sweep.
+// mode 1: every old owner is fluid (first particles_set)
+__global__ void __launch_bounds__(CB) k_claims(LatticeView lv, PartView pv, int *claim, ChangeList chg, int mode) {
+  __shared__ int sh_len;
+  const int p = blockIdx.x;
+  if (threadIdx.x == 0) {
+    sh_len = 0;
+    if (p == 0) *chg.count = 0;
+  }
+  __syncthreads();
+  const int lo[3] = {pv.box[6 * p], pv.box[6 * p + 1], pv.box[6 * p + 2]};
+  const int hi[3] = {pv.box[6 * p + 3], pv.box[6 * p + 4], pv.box[6 * p + 5]};
+  BoxIter it;
+  it.init(lo, hi);
+  CellGeo g;
+  cell_geo(pv, p, g);
+  unsigned long long *touched = pv.touched + (size_t)p * pv.touched_cap;
+  // whole warps iterate together (the append is warp-collective)
+  const int iters = (it.total + CB - 1) / CB;
+  for (int k = 0; k < iters; ++k, it.advance()) {
+    const int t = k * CB + threadIdx.x;
+    int mark = 0;
+    int x = 0, y = 0, z = 0;
+    if (t < it.total) {
+      x = lo[0] + it.ix;
+      y = lo[1] + it.iy;
+      z = lo[2] + it.iz;
+      if (lv.per[0]) x = wrapi(x, lv.nx);
+      if (lv.per[1]) y = wrapi(y, lv.ny);
+      if (lv.per[2]) z = wrapi(z, lv.nz);
+      const unsigned idx = node_of(lv, x, y, z);
+      const int ow = lv.owner[idx];
+      if (ow > -2) {
+        const bool ins = inside_cell(x, y, z, g.X, g.o, g.Xf, g.Xi, g.of, pv, lv);
+        if (mode != 1 && ow == p && !ins) {
+          atomicMin(&claim[idx], CLAIM_TOUCHED);
+          mark = 1;
+        } else if (ow != p && ins) {
+          atomicMin(&claim[idx], p);
+          mark = 1;
+        }
+      }
+    }
+    const int pos = warp_append(mark, &sh_len);
+    if (mark) {
+      if (pos < pv.touched_cap) touched[pos] = pack_xyzr(x, y, z, 0);
+      else atomicOr(pv.status, ST_OVERFLOW);
     }
   }
   __syncthreads();
-  if (!sactive) return;
-  double X[3] = {sX[0], sX[1], sX[2]}, o[3] = {so[0], so[1], so[2]};
-  int Xi[3];
-  float Xf[3], of[3];
-  for (int k = 0; k < 3; ++k) {
-    Xi[k] = (int)rint(X[k]);
-    Xf[k] = (float)(X[k] - (double)Xi[k]);
-    of[k] = (float)o[k];
+  if (threadIdx.x == 0) pv.touched_count[p] = min(sh_len, pv.touched_cap);
+}
+
+// geometry of the new owner map (one block per cell): the cell's bounce
+// links (fluid node y, direction r from y into the cell) and its contact
+// links as exact integer sums with the lever arm's integer part dI = x - rint(X)
+__global__ void __launch_bounds__(CB) k_geometry(LatticeView lv, PartView pv) {
+  using D = D3Q19;
+  __shared__ int sh_len;
+  __shared__ int shi[CB / 32][6];
+  const int p = blockIdx.x;
+  if (threadIdx.x == 0) sh_len = 0;
+  __syncthreads();
+  const int lo[3] = {pv.box[6 * p], pv.box[6 * p + 1], pv.box[6 * p + 2]};
+  const int hi[3] = {pv.box[6 * p + 3], pv.box[6 * p + 4], pv.box[6 * p + 5]};
+  BoxIter it;
+  it.init(lo, hi);
+  const float4 k0 = pv.kin_next[3 * p], k1 = pv.kin_next[3 * p + 1], k2 = pv.kin_next[3 * p + 2];
+  const int Xi[3] = {(int)k0.w, (int)k1.w, (int)k2.w};
+  unsigned long long *lk = pv.lk + (size_t)p * pv.lk_cap;
+  int ci[6] = {0, 0, 0, 0, 0, 0};
+  const int iters = (it.total + CB - 1) / CB;
+  for (int k = 0; k < iters; ++k, it.advance()) {
+    const int t = k * CB + threadIdx.x;
+    unsigned lmask = 0;
+    int xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
+    if (t < it.total) {
+      int x = lo[0] + it.ix, y = lo[1] + it.iy, z = lo[2] + it.iz;
+      if (lv.per[0]) x = wrapi(x, lv.nx);
+      if (lv.per[1]) y = wrapi(y, lv.ny);
+      if (lv.per[2]) z = wrapi(z, lv.nz);
+      if (lv.owner[node_of(lv, x, y, z)] == p) {
+        xs[0] = x == 0 ? lv.nx - 1 : x - 1; xs[1] = x; xs[2] = x == lv.nx - 1 ? 0 : x + 1;
+        ys[0] = y == 0 ? lv.ny - 1 : y - 1; ys[1] = y; ys[2] = y == lv.ny - 1 ? 0 : y + 1;
+        zs[0] = z == 0 ? lv.nz - 1 : z - 1; zs[1] = z; zs[2] = z == lv.nz - 1 ? 0 : z + 1;
+        int on[Q];
+        sfor<1, Q>([&](auto R) {
+          constexpr int r = decltype(R)::value;
+          on[r] = lv.owner[node_of(lv, xs[1 + D::cx(r)], ys[1 + D::cy(r)], zs[1 + D::cz(r)])];
+        });
+        const int di[3] = {imin_image(x - Xi[0], lv.nx, lv.per[0]), imin_image(y - Xi[1], lv.ny, lv.per[1]),
+                           imin_image(z - Xi[2], lv.nz, lv.per[2])};
+        sfor<1, Q>([&](auto R) {
+          constexpr int r = decltype(R)::value;
+          constexpr int m = D::m(r);
+          if (on[r] == FLUID) {
+            lmask |= 1u << r;
+          } else if (on[r] != p) {
+            ci[0] -= m * D::cx(r);
+            ci[1] -= m * D::cy(r);
+            ci[2] -= m * D::cz(r);
+            ci[3] -= m * (di[1] * D::cz(r) - di[2] * D::cy(r));
+            ci[4] -= m * (di[2] * D::cx(r) - di[0] * D::cz(r));
+            ci[5] -= m * (di[0] * D::cy(r) - di[1] * D::cx(r));
+          }
+        });
+      }
+    }
+    int pos = warp_append(__popc(lmask), &sh_len);
+    while (lmask) {
+      const int r = __ffs(lmask) - 1;
+      lmask &= lmask - 1;
+      // the fluid node y = x + c_r bounces direction rbar into this cell
+      const int yx = xs[1 + D::cx(r)], yy = ys[1 + D::cy(r)], yz = zs[1 + D::cz(r)];
+      if (pos < pv.lk_cap) lk[pos] = pack_xyzr(yx, yy, yz, D::opp(r));
+      else atomicOr(pv.status, ST_OVERFLOW);
+      ++pos;
+    }
   }
-  const int bx = shi[0] - slo[0] + 1, by = shi[1] - slo[1] + 1, bz = shi[2] - slo[2] + 1;
-  const int total = (bx > 0 && by > 0 && bz > 0) ? bx * by * bz : 0;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    int x = slo[0] + t % bx, y = slo[1] + (t / bx) % by, z = slo[2] + t / (bx * by);
-    if (lv.per[0]) x = wrapi(x, lv.nx);
-    if (lv.per[1]) y = wrapi(y, lv.ny);
-    if (lv.per[2]) z = wrapi(z, lv.nz);
-    const unsigned idx = (unsigned)x + (unsigned)lv.nx * ((unsigned)y + (unsigned)lv.ny * z);
-    const int ow = lv.owner[idx];
-    if (ow <= -2) continue;
-    const bool ins = inside_cell(x, y, z, X, o, Xf, Xi, of, pv, lv);
-    if (mode == 1) {
-      if (ins) atomicMin(&claim[idx], p);
-    } else if (ow == p) {
-      atomicMin(&claim[idx], ins ? CLAIM_KEEP : CLAIM_TOUCHED);
-    } else if (ins) {
-      atomicMin(&claim[idx], p);
+  block_sum_i<6>(ci, shi);
+  if (threadIdx.x == 0) {
+    pv.lk_count[p] = min(sh_len, pv.lk_cap);
+    for (int k = 0; k < 3; ++k) {
+      pv.cK[3 * p + k] = ci[k];
+      pv.cIT[3 * p + k] = ci[3 + k];
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// resolve + fill/drain
-
-template <class S>
-__device__ void node_slots(const LatticeView &lv, int par, int x, int y, int z, unsigned slot[Q]) {
-  using D = D3Q19;
-  const unsigned n = (unsigned)x + (unsigned)lv.nx * ((unsigned)y + (unsigned)lv.ny * z);
-  for (int r = 0; r < Q; ++r) {
-    if (par == 0 || r == 0) {
-      slot[r] = (unsigned)r * lv.N + n;
-    } else {
-      const int xs = wrapi(x - D::cx(r), lv.nx), ys = wrapi(y - D::cy(r), lv.ny), zs = wrapi(z - D::cz(r), lv.nz);
-      slot[r] = (unsigned)D::opp(r) * lv.N + (unsigned)xs + (unsigned)lv.nx * ((unsigned)ys + (unsigned)lv.ny * zs);
-    }
-  }
-}
+// resolve + fill/drain over each cell's touched nodes
 
 __device__ __forceinline__ void atomic_add3(double *a, const double v[3]) {
   atomicAdd(a, v[0]);
@@ -626,36 +1032,37 @@ __device__ __forceinline__ void atomic_add3(double *a, const double v[3]) {
 }
 
 template <class S>
-__global__ void __launch_bounds__(256) k_resolve_fill(LatticeView lv, PartView pv, int *claim, ChangeList chg,
-                                                       LinkList ll, int par_next, int impulses) {
+__global__ void __launch_bounds__(CB) k_resolve_fill(LatticeView lv, PartView pv, int *claim, ChangeList chg,
+                                                      int par_next, int impulses) {
   using D = D3Q19;
   const int p = blockIdx.x;
-  if (p == 0 && threadIdx.x == 0) *ll.count = 0;  // the step's link list has been used
-  const int lo[3] = {pv.box[6 * p], pv.box[6 * p + 1], pv.box[6 * p + 2]};
-  const int hi[3] = {pv.box[6 * p + 3], pv.box[6 * p + 4], pv.box[6 * p + 5]};
-  const int bx = hi[0] - lo[0] + 1, by = hi[1] - lo[1] + 1, bz = hi[2] - lo[2] + 1;
-  if (bx <= 0 || by <= 0 || bz <= 0) return;
-  const int total = bx * by * bz;
+  const int nt = pv.touched_count[p];
+  const unsigned long long *touched = pv.touched + (size_t)p * pv.touched_cap;
   const int lane = threadIdx.x & 31;
   S *pop = reinterpret_cast<S *>(lv.pop);
   const int dims[3] = {lv.nx, lv.ny, lv.nz};
-  for (int base = 0; base < total; base += blockDim.x) {
-    const int t = base + threadIdx.x;
-    int x = 0, y = 0, z = 0, old = 0, nw = 0;
+  for (int t0 = 0; t0 < nt; t0 += CB) {
+    const int t = t0 + threadIdx.x;
+    int old = 0, nw = 0, xyz[3] = {0, 0, 0};
     bool changed = false;
     unsigned idx = 0;
-    if (t < total) {
-      x = lo[0] + t % bx;
-      y = lo[1] + (t / bx) % by;
-      z = lo[2] + t / (bx * by);
-      if (lv.per[0]) x = wrapi(x, lv.nx);
-      if (lv.per[1]) y = wrapi(y, lv.ny);
-      if (lv.per[2]) z = wrapi(z, lv.nz);
-      idx = (unsigned)x + (unsigned)lv.nx * ((unsigned)y + (unsigned)lv.ny * z);
+    if (t < nt) {
+      int r_unused;
+      unpack_xyzr(touched[t], xyz, r_unused);
+      idx = node_of(lv, xyz[0], xyz[1], xyz[2]);
       const int c = atomicExch(&claim[idx], CLAIM_FREE);
       if (c != CLAIM_FREE) {
         old = lv.owner[idx];
-        nw = c == CLAIM_KEEP ? old : (c == CLAIM_TOUCHED ? FLUID : c);
+        if (c == CLAIM_TOUCHED) {
+          nw = FLUID;
+        } else if (old >= 0) {
+          // first arrival: the old owner keeps the node while it covers it
+          CellGeo g;
+          cell_geo(pv, old, g);
+          nw = inside_cell(xyz[0], xyz[1], xyz[2], g.X, g.o, g.Xf, g.Xi, g.of, pv, lv) ? old : c;
+        } else {
+          nw = c;
+        }
         changed = nw != old;
         if (changed) lv.owner[idx] = nw;
       }
@@ -672,29 +1079,38 @@ __global__ void __launch_bounds__(256) k_resolve_fill(LatticeView lv, PartView p
       chg.items[3 * pos + 1] = old;
       chg.items[3 * pos + 2] = nw;
     }
-    const double xyz[3] = {(double)x, (double)y, (double)z};
     unsigned slot[Q];
-    node_slots<S>(lv, par_next, x, y, z, slot);
-    double arm_o[3] = {0, 0, 0}, u_o[3] = {0, 0, 0}, arm_n[3] = {0, 0, 0};
+    for (int r = 0; r < Q; ++r) {
+      if (par_next == 0 || r == 0) {
+        slot[r] = (unsigned)r * lv.N + idx;
+      } else {
+        slot[r] = (unsigned)D::opp(r) * lv.N +
+                  node_of(lv, wrapi(xyz[0] - D::cx(r), lv.nx), wrapi(xyz[1] - D::cy(r), lv.ny),
+                          wrapi(xyz[2] - D::cz(r), lv.nz));
+      }
+    }
+    double arm_o[3] = {0, 0, 0}, arm_n[3] = {0, 0, 0};
+    float u_o[3] = {0.f, 0.f, 0.f};
     if (old >= 0) {
-      for (int k = 0; k < 3; ++k) arm_o[k] = min_image_exact(xyz[k] - pv.X[3 * old + k], dims[k], lv.per[k]);
+      for (int k = 0; k < 3; ++k) arm_o[k] = min_image_exact((double)xyz[k] - pv.X[3 * old + k], dims[k], lv.per[k]);
       const double *W = pv.Om + 3 * old;
-      u_o[0] = pv.V[3 * old + 0] + (W[1] * arm_o[2] - W[2] * arm_o[1]);
-      u_o[1] = pv.V[3 * old + 1] + (W[2] * arm_o[0] - W[0] * arm_o[2]);
-      u_o[2] = pv.V[3 * old + 2] + (W[0] * arm_o[1] - W[1] * arm_o[0]);
+      u_o[0] = (float)(pv.V[3 * old + 0] + (W[1] * arm_o[2] - W[2] * arm_o[1]));
+      u_o[1] = (float)(pv.V[3 * old + 1] + (W[2] * arm_o[0] - W[0] * arm_o[2]));
+      u_o[2] = (float)(pv.V[3 * old + 2] + (W[0] * arm_o[1] - W[1] * arm_o[0]));
     }
     if (nw >= 0)
-      for (int k = 0; k < 3; ++k) arm_n[k] = min_image_exact(xyz[k] - pv.X[3 * nw + k], dims[k], lv.per[k]);
+      for (int k = 0; k < 3; ++k) arm_n[k] = min_image_exact((double)xyz[k] - pv.X[3 * nw + k], dims[k], lv.per[k]);
     if (old == FLUID && nw >= 0) {
       // covered: the fluid is deleted, its momentum goes to the new owner
       if (impulses) {
-        double mom[3] = {0, 0, 0};
+        float mf[3] = {0.f, 0.f, 0.f};
         for (int r = 0; r < Q; ++r) {
-          const double v = Store<S>::ld(pop + slot[r]);
-          mom[0] += v * D::cx(r);
-          mom[1] += v * D::cy(r);
-          mom[2] += v * D::cz(r);
+          const float v = Store<S>::ld(pop + slot[r]);
+          mf[0] += v * D::cx(r);
+          mf[1] += v * D::cy(r);
+          mf[2] += v * D::cz(r);
         }
+        const double mom[3] = {mf[0], mf[1], mf[2]};
         const double tq[3] = {arm_n[1] * mom[2] - arm_n[2] * mom[1], arm_n[2] * mom[0] - arm_n[0] * mom[2],
                               arm_n[0] * mom[1] - arm_n[1] * mom[0]};
         atomic_add3(pv.PF + 3 * nw, mom);
@@ -709,12 +1125,12 @@ __global__ void __launch_bounds__(256) k_resolve_fill(LatticeView lv, PartView p
       atomic_add3(pv.PT + 3 * old, tneg);
       if (nw == FLUID) {
         // uncovered: new fluid at n^eq(rho_bar, u_rigid), stored shifted
-        const double uu = u_o[0] * u_o[0] + u_o[1] * u_o[1] + u_o[2] * u_o[2];
+        const float rho0 = (float)pv.rho0;
+        const float uu = u_o[0] * u_o[0] + u_o[1] * u_o[1] + u_o[2] * u_o[2];
         for (int r = 0; r < Q; ++r) {
-          const double cu = D::cx(r) * u_o[0] + D::cy(r) * u_o[1] + D::cz(r) * u_o[2];
-          const double w = D::m(r) / 36.0;
-          const double feq = pv.rho0 * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu + 4.5 * cu * cu * cu - 4.5 * uu * cu);
-          Store<S>::st(pop + slot[r], (float)feq);
+          const float cu = D::cx(r) * u_o[0] + D::cy(r) * u_o[1] + D::cz(r) * u_o[2];
+          const float w = D::m(r) / 36.0f;
+          Store<S>::st(pop + slot[r], rho0 * w * (cu * (3.0f + cu * (4.5f + 4.5f * cu)) - uu * (1.5f + 4.5f * cu)));
         }
       } else {
         // direct change of owner: uncover by the old, cover by the new (reading Q6)
@@ -730,15 +1146,22 @@ __global__ void __launch_bounds__(256) k_resolve_fill(LatticeView lv, PartView p
 // owners >= 0 become resting fluid (first particles_set), layout of parity par
 template <class S>
 __global__ void k_clear_cells(LatticeView lv, int par) {
+  using D = D3Q19;
   const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= lv.N) return;
   if (lv.owner[n] < 0) return;
   lv.owner[n] = FLUID;
-  const int x = n % lv.nx, y = (n / lv.nx) % lv.ny, z = n / ((unsigned)lv.nx * lv.ny);
-  unsigned slot[Q];
-  node_slots<S>(lv, par, x, y, z, slot);
+  int xyz[3];
+  node_xyz(lv, n, xyz);
   S *pop = reinterpret_cast<S *>(lv.pop);
-  for (int r = 0; r < Q; ++r) Store<S>::st(pop + slot[r], 0.0f);
+  for (int r = 0; r < Q; ++r) {
+    unsigned slot;
+    if (par == 0 || r == 0) slot = (unsigned)r * lv.N + n;
+    else
+      slot = (unsigned)D::opp(r) * lv.N +
+             node_of(lv, wrapi(xyz[0] - D::cx(r), lv.nx), wrapi(xyz[1] - D::cy(r), lv.ny), wrapi(xyz[2] - D::cz(r), lv.nz));
+    Store<S>::st(pop + slot, 0.0f);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -755,26 +1178,57 @@ void launch_cell_list(const LatticeView &lv, const PartView &pv, const CellListV
   *nl += 4;
 }
 
-void launch_forces(const LatticeView &lv, const PartView &pv, const CellListView &cl, const WallRows &wr,
+void launch_forces(const LatticeView &lv, const PartView &pv, const CellListView &cl, const SurfBits &sb,
                    cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  k_forces<<<nblk((unsigned)pv.n * 32, 128), 128, 0, st>>>(lv, pv, cl, wr);
+  k_forces<<<pv.n, CB, 0, st>>>(lv, pv, cl, sb);
   *nl += 1;
 }
 
-void launch_integrate_claim(const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg, int mode,
-                            cudaStream_t st, int64_t *nl) {
+static unsigned link_chunks(const PartView &pv) { return (unsigned)((pv.lk_cap + CB - 1) / CB); }
+
+template <class S>
+static void cell_step_typed(const LatticeView &lv, const PartView &pv, int par, cudaStream_t st) {
+  const dim3 grid_sum((unsigned)((pv.lk_cap + LCHUNK - 1) / LCHUNK), pv.n);
+  k_link_sums<S><<<grid_sum, LT, 0, st>>>(lv, pv, par);
+  k_solve<<<nblk(pv.n, 64), 64, 0, st>>>(lv, pv);
+  const dim3 grid(link_chunks(pv), pv.n);
+  k_link_correct<S><<<grid, CB, 0, st>>>(lv, pv, par);
+}
+
+void launch_cell_step(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  k_integrate_claim<<<pv.n, 256, 0, st>>>(lv, pv, claim, chg, mode);
+  if (dtype == 0) cell_step_typed<float>(lv, pv, par, st);
+  else if (dtype == 1) cell_step_typed<__nv_bfloat16>(lv, pv, par, st);
+  else cell_step_typed<__half>(lv, pv, par, st);
+  *nl += 3;
+}
+
+void launch_set_state(const LatticeView &lv, const PartView &pv, int mode, cudaStream_t st, int64_t *nl) {
+  if (pv.n == 0) return;
+  k_set_state<<<nblk(pv.n, 64), 64, 0, st>>>(lv, pv, mode);
+  *nl += 1;
+}
+
+void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg, int mode,
+                   cudaStream_t st, int64_t *nl) {
+  if (pv.n == 0) return;
+  k_claims<<<pv.n, CB, 0, st>>>(lv, pv, claim, chg, mode);
   *nl += 1;
 }
 
 void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg,
-                         const LinkList &ll, int par_next, int impulses, cudaStream_t st, int64_t *nl) {
+                         int par_next, int impulses, cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  if (dtype == 0) k_resolve_fill<float><<<pv.n, 256, 0, st>>>(lv, pv, claim, chg, ll, par_next, impulses);
-  else if (dtype == 1) k_resolve_fill<__nv_bfloat16><<<pv.n, 256, 0, st>>>(lv, pv, claim, chg, ll, par_next, impulses);
-  else k_resolve_fill<__half><<<pv.n, 256, 0, st>>>(lv, pv, claim, chg, ll, par_next, impulses);
+  if (dtype == 0) k_resolve_fill<float><<<pv.n, CB, 0, st>>>(lv, pv, claim, chg, par_next, impulses);
+  else if (dtype == 1) k_resolve_fill<__nv_bfloat16><<<pv.n, CB, 0, st>>>(lv, pv, claim, chg, par_next, impulses);
+  else k_resolve_fill<__half><<<pv.n, CB, 0, st>>>(lv, pv, claim, chg, par_next, impulses);
+  *nl += 1;
+}
+
+void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl) {
+  if (pv.n == 0) return;
+  k_geometry<<<pv.n, CB, 0, st>>>(lv, pv);
   *nl += 1;
 }
 

@@ -75,7 +75,16 @@ struct LatticeView {
   void *pop;       // 19 x N storage elements, slot r of node n at r * N + n
   int32_t *owner;  // N
   float *rho_b;    // N: density of each fluid node with a cell link, written by the sweep
+  uint32_t *nbm;   // N neighbour words of the current owner map (NB_* bits), written by the geometry pass
 };
+
+// neighbour word of a node: bit 0 the node is fluid; bit r (1..18) the
+// neighbour x + c_r is solid; NB_WALL some solid neighbour is a wall node;
+// NB_CELL some solid neighbour is a cell node.  Zero for solid nodes.
+constexpr uint32_t NB_FLUID = 1u;
+constexpr uint32_t NB_SOLID = 0x7FFFEu;
+constexpr uint32_t NB_WALL = 1u << 19;
+constexpr uint32_t NB_CELL = 1u << 20;
 
 // momentum given to each wall id by its bounce-back links: variable part in
 // FP64, constant part 2 alpha_r rho_bar c_r as exact integer sums of m_r c_r
@@ -85,12 +94,14 @@ struct WallAcc {
 };
 
 // Cells.  Per-cell link list: the bounce links (fluid node y, direction r
-// from y into the cell) as packed coordinates, rebuilt after every
+// from y into the cell) as packed coordinates, grouped by direction within
+// each warp's run, rebuilt by the geometry pass after every
 // re-discretisation; contact links enter as exact integer sums cK, cIT.
 struct PartView {
   int n;
   double *X, *q, *V, *L, *Om;
   double *o;         // exact FP64 symmetry axis of the current q, n x 3
+  float *oprev;      // n x 3 axis before the last move (FP32): the claims' old ellipsoid
   float4 *kin;       // kinematics of the current step, 3 float4 per cell:
                      //   (f.x, f.y, f.z, Xi.x), (V, Xi.y), (W, Xi.z); X = Xi + f, Xi = rint(X)
   float4 *kin_next;  // kinematics written for the next step
@@ -159,8 +170,8 @@ void launch_set_state(const LatticeView &lv, const PartView &pv, int mode, cudaS
 void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg, int mode,
                    cudaStream_t st, int64_t *nl);
 void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);
-void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg,
-                         int par_next, int impulses, cudaStream_t st, int64_t *nl);
+void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, const CellListView &cl, int *claim,
+                         const ChangeList &chg, int par_next, int impulses, cudaStream_t st, int64_t *nl);
 void launch_clear_cells(int dtype, const LatticeView &lv, int par, cudaStream_t st, int64_t *nl);
 
 // bit flags of the device status word

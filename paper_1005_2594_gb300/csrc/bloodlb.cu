@@ -217,6 +217,9 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
     if ((rc = check_launch(c, "init")) != BL_OK) break;
     if (cudaMalloc(&lv.rho_b, sizeof(float) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "density buffer"); break; }
     cudaMemsetAsync(lv.rho_b, 0, sizeof(float) * N, c->stream);
+    if (cudaMalloc(&lv.nbm, sizeof(uint32_t) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "neighbour words"); break; }
+    launch_geometry(lv, c->pv, c->stream, &c->launches);
+    if ((rc = check_launch(c, "geometry")) != BL_OK) break;
     if ((rc = build_surface_bits(c)) != BL_OK) break;
   } while (0);
   if (rc != BL_OK) {
@@ -238,6 +241,7 @@ extern "C" int bl_walls_set(bl_ctx *c, const uint8_t *mask) {
   CU(cudaMemcpyAsync(d, mask, c->lv.N, cudaMemcpyHostToDevice, c->stream));
   launch_apply_wall_mask(c->lv, d, c->stream);
   c->launches++;
+  launch_geometry(c->lv, c->pv, c->stream, &c->launches);
   int rc = check_launch(c, "wall mask");
   cudaStreamSynchronize(c->stream);
   cudaFree(d);
@@ -247,7 +251,7 @@ extern "C" int bl_walls_set(bl_ctx *c, const uint8_t *mask) {
 
 static void free_particles(bl_ctx *c) {
   PartView &pv = c->pv;
-  void *ptrs[] = {pv.X, pv.q, pv.V, pv.L, pv.Om, pv.o, pv.kin, pv.kin_next, pv.lk, pv.lk_count, pv.cK, pv.cIT,
+  void *ptrs[] = {pv.X, pv.q, pv.V, pv.L, pv.Om, pv.o, pv.oprev, pv.kin, pv.kin_next, pv.lk, pv.lk_count, pv.cK, pv.cIT,
                   pv.touched, pv.touched_count, pv.lsum, pv.lsum_i, pv.vw, pv.Fpot, pv.Tpot, pv.PF, pv.PT, pv.Flink, pv.Tlink, pv.Ftot,
                   pv.Ttot, pv.box, pv.stage, c->cl.bin_of, c->cl.count, c->cl.start, c->cl.cursor, c->cl.ids,
                   c->chg.count, c->chg.items};
@@ -268,6 +272,8 @@ static int alloc_particles(bl_ctx *c, int n) {
     CU(cudaMalloc(d, n3));
     CU(cudaMemsetAsync(*d, 0, n3, c->stream));
   }
+  CU(cudaMalloc(&pv.oprev, sizeof(float) * 3 * (size_t)n));
+  CU(cudaMemsetAsync(pv.oprev, 0, sizeof(float) * 3 * (size_t)n, c->stream));
   CU(cudaMalloc(&pv.q, sizeof(double) * 4 * (size_t)n));
   CU(cudaMemsetAsync(pv.q, 0, sizeof(double) * 4 * (size_t)n, c->stream));
   CU(cudaMalloc(&pv.kin, sizeof(float4) * 3 * (size_t)n));
@@ -373,6 +379,16 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
                 !(pp->sig_par > 0) || !(pp->sig_perp > 0) || !(pp->R_par < 1e4) || !(pp->R_perp < 1e4) ||
                 !(pp->sig_w >= 0) || !(pp->eps >= 0) || !(pp->eps_w >= 0)))
     return fail(c, BL_EINVAL, "bad cell parameters");
+  if (n > 0) {
+    // the owner search covers one cell-list bin around a node (bins are at
+    // least r_cut wide), and a cell must not reach half a periodic length
+    const double rmax = fmax(pp->R_par, pp->R_perp);
+    if (!(pp->r_cut >= rmax + 1.0)) return fail(c, BL_EINVAL, "r_cut < max(R_par, R_perp) + 1");
+    const int dims[3] = {c->lv.nx, c->lv.ny, c->lv.nz};
+    for (int k = 0; k < 3; ++k)
+      if (c->lv.per[k] && !((double)dims[k] >= 2.0 * rmax + 4.0))
+        return fail(c, BL_EINVAL, "periodic length %d < 2 max(R) + 4", dims[k]);
+  }
   const bool first = n != c->np || c->np == 0;
   if (first) {
     // cells of a previous call become resting fluid
@@ -381,7 +397,12 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
     CU(cudaStreamSynchronize(c->stream));
     free_particles(c);
     c->pp = *pp;
-    if (n == 0) return BL_OK;
+    if (n == 0) {
+      launch_geometry(c->lv, c->pv, c->stream, &c->launches);
+      if (check_launch(c, "geometry")) return c->sticky;
+      CU(cudaStreamSynchronize(c->stream));
+      return BL_OK;
+    }
     if (alloc_particles(c, n)) return c->sticky;
   } else {
     c->pp = *pp;
@@ -402,8 +423,12 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
   }
   CU(cudaMemcpyAsync(c->pv.stage, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, c->stream));
   launch_set_state(c->lv, c->pv, first ? 1 : 2, c->stream, &c->launches);
+  // the search for new owners of nodes that a cell leaves uses the cell list
+  // of the new positions
+  if (!first) launch_cell_list(c->lv, c->pv, c->cl, c->stream, &c->launches);
   launch_claims(c->lv, c->pv, c->claim, c->chg, first ? 1 : 2, c->stream, &c->launches);
-  launch_resolve_fill(c->dtype, c->lv, c->pv, c->claim, c->chg, c->parity, first ? 0 : 1, c->stream, &c->launches);
+  launch_resolve_fill(c->dtype, c->lv, c->pv, c->cl, c->claim, c->chg, c->parity, first ? 0 : 1, c->stream,
+                      &c->launches);
   launch_geometry(c->lv, c->pv, c->stream, &c->launches);
   std::swap(c->pv.kin, c->pv.kin_next);
   if (check_launch(c, "particles_set")) return c->sticky;
@@ -429,7 +454,7 @@ static int enqueue_step(bl_ctx *c) {
     group_end(c, slot);
     group_begin(c, 4, &slot);
     launch_claims(c->lv, c->pv, c->claim, c->chg, 0, c->stream, &c->launches);
-    launch_resolve_fill(c->dtype, c->lv, c->pv, c->claim, c->chg, c->parity ^ 1, 1, c->stream, &c->launches);
+    launch_resolve_fill(c->dtype, c->lv, c->pv, c->cl, c->claim, c->chg, c->parity ^ 1, 1, c->stream, &c->launches);
     launch_geometry(c->lv, c->pv, c->stream, &c->launches);
     group_end(c, slot);
     std::swap(c->pv.kin, c->pv.kin_next);
@@ -450,7 +475,7 @@ static int read_status(bl_ctx *c) {
   int st = 0;
   CU(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  if (st & ST_UNSTABLE) return fail(c, BL_EUNSTABLE, "unstable fluid: rho <= 0, NaN or |u| >= 0.3 at some node");
+  if (st & ST_UNSTABLE) return fail(c, BL_EUNSTABLE, "unstable: rho <= 0, NaN or |u| >= 0.3 at some node, or a cell speed >= 0.5");
   if (st & ST_OVERFLOW) return fail(c, BL_EOVERFLOW, "internal list overflow");
   return BL_OK;
 }
@@ -638,7 +663,7 @@ extern "C" void bl_destroy(bl_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   free_particles(c);
-  void *ptrs[] = {c->lv.pop, c->lv.owner, c->lv.rho_b, c->claim, c->status, c->wacc.F, c->wacc.K,
+  void *ptrs[] = {c->lv.pop, c->lv.owner, c->lv.rho_b, c->lv.nbm, c->claim, c->status, c->wacc.F, c->wacc.K,
                   c->sbits.bits, c->scratch};
   for (void *p : ptrs)
     if (p) cudaFree(p);

@@ -27,12 +27,22 @@
 // Walls move at a known velocity: their links get C here, and the wall's
 // momentum is summed per warp (constant part 2 alpha_r rho_bar c_r as exact
 // integers) before one atomic per wall and component.
+//
+// Geometry pass.  After every change of the owner map one lattice-wide pass
+// (k_geometry) writes each fluid node's neighbour word -- so the sweep reads
+// one word per node instead of 18 neighbour owners -- and, at each cell node,
+// appends the cell's bounce links and sums its contact links.
 #include "bl_internal.cuh"
 
 namespace bl {
 
+// blocks of 128 threads resident per SM: 8 caps the sweep at 64 registers
+#ifndef BL_LB_MINB
+#define BL_LB_MINB 8
+#endif
+
 template <class S, int PAR>
-__global__ void __launch_bounds__(128) k_lb_step(LatticeView lv, WallAcc wa, int *status) {
+__global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, WallAcc wa, int *status) {
   using D = D3Q19;
   const int nx = lv.nx, ny = lv.ny;
   const int x0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -50,22 +60,26 @@ __global__ void __launch_bounds__(128) k_lb_step(LatticeView lv, WallAcc wa, int
   const unsigned zo[3] = {(unsigned)(z == 0 ? lv.nz - 1 : z - 1) * nxy, (unsigned)z * nxy,
                           (unsigned)(z == lv.nz - 1 ? 0 : z + 1) * nxy};
   S *pop = reinterpret_cast<S *>(lv.pop);
-  const int own = valid ? lv.owner[n] : -2;
+  const uint32_t nbw = valid ? lv.nbm[n] : 0u;
   // wall momentum of this thread: wall id, variable part, constant-part integers
   int wkey = -1;
   float wF[3] = {0.f, 0.f, 0.f};
   int wK[3] = {0, 0, 0};
 
-  if (own == FLUID) {
-    // neighbour classes: solid = any non-fluid node, wall = wall node
-    unsigned solid = 0, wall = 0;
-    sfor<1, Q>([&](auto R) {
-      constexpr int r = decltype(R)::value;
-      const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
-      const int on = lv.owner[nb];
-      solid |= (on != FLUID ? 1u : 0u) << r;
-      wall |= (on <= -2 ? 1u : 0u) << r;
-    });
+  if (nbw & NB_FLUID) {
+    // neighbour classes from the geometry pass: solid = any non-fluid node;
+    // the wall subset is looked up only next to a wall
+    const unsigned solid = nbw & NB_SOLID;
+    unsigned wall = 0;
+    if (nbw & NB_WALL) {
+      sfor<1, Q>([&](auto R) {
+        constexpr int r = decltype(R)::value;
+        if (solid & (1u << r)) {
+          const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
+          wall |= (lv.owner[nb] <= -2 ? 1u : 0u) << r;
+        }
+      });
+    }
     // incoming populations of this node (layout of the step's parity)
     float f[Q];
     sfor<0, Q>([&](auto R) {
@@ -155,7 +169,7 @@ __global__ void __launch_bounds__(128) k_lb_step(LatticeView lv, WallAcc wa, int
         Store<S>::st(pop + dst, v);
       }
     });
-    if (solid & ~wall) lv.rho_b[n] = rho;
+    if (nbw & NB_CELL) lv.rho_b[n] = rho;
   }
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -176,6 +190,121 @@ __global__ void __launch_bounds__(128) k_lb_step(LatticeView lv, WallAcc wa, int
     }
     pending &= ~__ballot_sync(FULL, mine);
     if (mine) wkey = -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// geometry pass over the owner map (one thread per node, 128 along x)
+//
+//   fluid node  -> neighbour word (NB_* bits)
+//   cell node x of cell p, neighbour x + c_r fluid -> bounce link of p: the
+//                  fluid node y = x + c_r streams direction rbar into p
+//   cell node x of cell p, neighbour x + c_r another cell or a wall -> contact
+//                  link (Eqs. deltapppp, deltapppm): its constant momentum
+//                  -2 alpha_r rho_bar c_r goes into p's exact integer sums
+//                  cK = sum m_r c_r, cIT = sum m_r dI x c_r, dI = x - rint(X_p)
+//
+// A warp appends its links cell by cell with one atomic on the cell's count,
+// in direction order, so that the link kernels read consecutive nodes of one
+// direction.  The counts start at zero (the claims kernel clears them).
+__global__ void __launch_bounds__(128) k_geometry(LatticeView lv, PartView pv) {
+  using D = D3Q19;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nx = lv.nx, ny = lv.ny;
+  const int x0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const bool valid = x0 < nx;
+  const int x = valid ? x0 : nx - 1;
+  const unsigned nxy = (unsigned)nx * (unsigned)ny;
+  const unsigned n = (unsigned)x + (unsigned)nx * (unsigned)y + nxy * (unsigned)z;
+  const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+  const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+  const int zs[3] = {z == 0 ? lv.nz - 1 : z - 1, z, z == lv.nz - 1 ? 0 : z + 1};
+  const int own = valid ? lv.owner[n] : -2;
+  unsigned lmask = 0, cmask = 0;
+  if (own >= FLUID) {
+    unsigned solid = 0, wall = 0, same = 0;
+    sfor<1, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      const unsigned nb = (unsigned)xs[1 + D::cx(r)] + (unsigned)nx * (unsigned)ys[1 + D::cy(r)] +
+                          nxy * (unsigned)zs[1 + D::cz(r)];
+      const int on = lv.owner[nb];
+      solid |= (on != FLUID ? 1u : 0u) << r;
+      wall |= (on <= -2 ? 1u : 0u) << r;
+      same |= (on == own ? 1u : 0u) << r;
+    });
+    if (own == FLUID) {
+      lv.nbm[n] = NB_FLUID | solid | (wall ? NB_WALL : 0u) | ((solid & ~wall) ? NB_CELL : 0u);
+    } else {
+      lv.nbm[n] = 0u;
+      lmask = NB_SOLID & ~solid;  // fluid neighbours
+      cmask = solid & ~same;      // other cells and walls
+    }
+  } else if (valid) {
+    lv.nbm[n] = 0u;
+  }
+  if (pv.n == 0) return;  // no cell nodes: nothing to append (uniform per launch)
+
+  // bounce links, one group of lanes per cell
+  unsigned pend = __ballot_sync(FULL, lmask != 0u);
+  while (pend) {
+    const int leader = __ffs(pend) - 1;
+    const int cell = __shfl_sync(FULL, own, leader);
+    const bool mine = lmask != 0u && own == cell;
+    const unsigned grp = __ballot_sync(FULL, mine);
+    const int tot = __reduce_add_sync(FULL, mine ? __popc(lmask) : 0);
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&pv.lk_count[cell], tot);
+    base = __shfl_sync(FULL, base, leader);
+    if (base + tot > pv.lk_cap && lane == leader) atomicOr(pv.status, ST_OVERFLOW);
+    unsigned long long *lk = pv.lk + (size_t)cell * pv.lk_cap;
+    const unsigned below = (1u << lane) - 1u;
+    int run = base;
+    sfor<1, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      const bool has = mine && ((lmask >> r) & 1u);
+      const unsigned b = __ballot_sync(FULL, has);
+      if (has) {
+        const int pos = run + __popc(b & below);
+        if (pos < pv.lk_cap)
+          lk[pos] = pack_xyzr(xs[1 + D::cx(r)], ys[1 + D::cy(r)], zs[1 + D::cz(r)], D::opp(r));
+      }
+      run += __popc(b);
+    });
+    pend &= ~grp;
+  }
+
+  // contact links as exact integer sums
+  int ci[6] = {0, 0, 0, 0, 0, 0};
+  if (cmask) {
+    const float4 k0 = pv.kin_next[3 * own], k1 = pv.kin_next[3 * own + 1], k2 = pv.kin_next[3 * own + 2];
+    const int di[3] = {imin_image(x - (int)k0.w, nx, lv.per[0]), imin_image(y - (int)k1.w, ny, lv.per[1]),
+                       imin_image(z - (int)k2.w, lv.nz, lv.per[2])};
+    sfor<1, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      constexpr int m = D::m(r);
+      if ((cmask >> r) & 1u) {
+        ci[0] -= m * D::cx(r);
+        ci[1] -= m * D::cy(r);
+        ci[2] -= m * D::cz(r);
+        ci[3] -= m * (di[1] * D::cz(r) - di[2] * D::cy(r));
+        ci[4] -= m * (di[2] * D::cx(r) - di[0] * D::cz(r));
+        ci[5] -= m * (di[0] * D::cy(r) - di[1] * D::cx(r));
+      }
+    });
+  }
+  pend = __ballot_sync(FULL, cmask != 0u);
+  while (pend) {
+    const int leader = __ffs(pend) - 1;
+    const int cell = __shfl_sync(FULL, own, leader);
+    const bool mine = cmask != 0u && own == cell;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int v = __reduce_add_sync(FULL, mine ? ci[k] : 0);
+      if (lane == leader && v != 0) atomicAdd(k < 3 ? &pv.cK[3 * cell + k] : &pv.cIT[3 * cell + k - 3], v);
+    }
+    pend &= ~__ballot_sync(FULL, mine);
   }
 }
 
@@ -385,6 +514,13 @@ void launch_lb_step(int dtype, const LatticeView &lv, int par, const WallAcc &wa
 }
 
 static inline unsigned nblk(unsigned n, unsigned b) { return (n + b - 1) / b; }
+
+void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl) {
+  const int bx = lv.nx >= 128 ? 128 : ((lv.nx + 31) / 32) * 32;
+  dim3 grid((lv.nx + bx - 1) / bx, lv.ny, lv.nz);
+  k_geometry<<<grid, bx, 0, st>>>(lv, pv);
+  if (nl) ++*nl;
+}
 
 void launch_fields(int dtype, const LatticeView &lv, int par, double *rho, double *u, int32_t *owner, cudaStream_t st) {
   const unsigned b = 256, g = nblk(lv.N, b);

@@ -4,27 +4,27 @@
 //   potentials     Berne-Pechukas-scaled Hookean cell-cell pairs (Sec. III,
 //                  Eqs. phi, epsilon, sigma) and cell-wall spheres (Eq. sigmaw),
 //                  one block per cell, FP32 arithmetic, FP64 result
-//   cell update    one block per cell: sums its bounce links (Eq. deltap),
-//                  solves for the velocities of the half step (reading Q3),
-//                  adds the moving-boundary term C (Eq. c) to its bounced
-//                  populations, advances the cell (leap-frog on unit
-//                  quaternions, reading Q4) and claims the nodes its new
-//                  ellipsoid enters or leaves
+//   link sums      per cell over its bounce-link list (Eq. deltap): link
+//                  momentum at the predictor and the drag matrices
+//   solve          one thread per cell: velocities of the half step (reading
+//                  Q3), leap-frog on unit quaternions (reading Q4)
+//   link correct   the moving-boundary term C (Eq. c) on every bounced
+//                  population of the cell
+//   claims         one block per cell, one thread per lattice row: the nodes
+//                  the cell's new ellipsoid enters or leaves
 //   resolve        first-arrival owner rule (Sec. II single occupancy), then
 //                  fill/drain of every changed node with the momentum balance
 //                  given to the cells (Sec. II)
-//   geometry       each cell's bounce-link list and its contact-link sums
-//                  (Eqs. deltapppp, deltapppm) from the new owner map
-//   geometry       rebuilds each cell's bounce-link list and its contact-link
-//                  sums (Eqs. deltapppp, deltapppm) from the new owner map
+// (the geometry pass that rebuilds the link lists from the new owner map is
+// a lattice-wide kernel in lb_kernels.cu)
 //
-// Ownership claims.  claim[] holds INT_MAX ("free") on every node between
-// steps.  A cell marks each node of its box that its new ellipsoid enters
-// with its index (atomicMin: the lowest index among the newcomers) and each
-// node it owns but leaves with TOUCHED; both go to the cell's touched list.
-// Resolve takes each claim once (atomicExch back to free): TOUCHED alone ->
-// fluid; a newcomer index -> the old owner keeps the node if its new
-// ellipsoid still covers it (first arrival), else the newcomer takes it.
+// Ownership.  claim[] holds INT_MAX ("free") on every node between steps.
+// A cell marks each fluid node its new ellipsoid enters with its index
+// (atomicMin: the lowest index among the newcomers) and each node it owns
+// but leaves with TOUCHED; both go to the cell's touched list.  Resolve takes
+// each claim once (atomicExch back to free): a newcomer index -> that cell;
+// TOUCHED -> the lowest-index cell now covering the node, else fluid.  This
+// is the first-arrival rule: an owner keeps a node while it covers it.
 //
 // FP64 is used only where the state needs it (positions, velocities, angular
 // momenta, the exact inside test near a surface); on this GPU a one-lane FP64
@@ -677,6 +677,7 @@ __global__ void k_solve(LatticeView lv, PartView pv) {
     o_old[k] = pv.o[3 * p + k];
   }
   for (int k = 0; k < 4; ++k) q[k] = pv.q[4 * p + k];
+  for (int k = 0; k < 3; ++k) pv.oprev[3 * p + k] = (float)o_old[k];  // the claims' old ellipsoid
   double vd[6];
   float v[27];
   for (int k = 0; k < 27; ++k) {
@@ -774,6 +775,9 @@ __global__ void k_solve(LatticeView lv, PartView pv) {
     for (int k = 0; k < 3; ++k) pv.o[3 * p + k] = o_new[k];
     bool finite = true;
     for (int k = 0; k < 3; ++k) finite = finite && isfinite(X[k]) && isfinite(o_new[k]);
+    // a cell faster than half a node per step is far outside the method's
+    // low-Mach range (and would outrun the cell list of the step's start)
+    if (!(V[0] * V[0] + V[1] * V[1] + V[2] * V[2] < 0.25)) finite = false;
     if (finite) {
       int lo2[3], hi2[3];
       aabb(pv, X, o_new, lo, hi);
@@ -861,7 +865,10 @@ __global__ void k_set_state(LatticeView lv, PartView pv, int mode) {
   for (int k = 0; k < 4; ++k) pv.q[4 * p + k] = q[k];
   double o_new[3];
   axis_exact(q, o_new);
-  for (int k = 0; k < 3; ++k) pv.o[3 * p + k] = o_new[k];
+  for (int k = 0; k < 3; ++k) {
+    pv.oprev[3 * p + k] = (float)(mode == 2 ? o_old[k] : o_new[k]);
+    pv.o[3 * p + k] = o_new[k];
+  }
   write_kin(pv, p, X, V, W);
   int lo[3], hi[3], lo2[3], hi2[3];
   aabb(pv, X, o_new, lo, hi);
@@ -892,134 +899,196 @@ __global__ void k_set_state(LatticeView lv, PartView pv, int mode) {
   if (!finite) atomicOr(pv.status, ST_UNSTABLE);
 }
 
-// claims over each cell's box (one block per cell), appended to its touched
-// list; also clears the cell's link segment for the next sweep.
-// mode 1: every old owner is fluid (first particles_set)
+// Row intervals of an ellipsoid.  Along the lattice row (y, z) the inside
+// function is a quadratic in t = x - X_x:
+//   s(t) = A t^2 + B t + C0,  A = ip + kk o_x^2,  B = 2 kk o_x e,
+//   C0 = (dy^2 + dz^2) ip + kk e^2,  e = o_y dy + o_z dz,
+// ip = 1 / R_perp^2, kk = 1 / R_par^2 - 1 / R_perp^2 (A > 0 for any axis).
+struct RowQuad {
+  float A, B, C0;
+};
+
+__device__ __forceinline__ RowQuad row_quad(float dy, float dz, const float o[3], float ip, float kk) {
+  const float e = o[1] * dy + o[2] * dz;
+  return RowQuad{ip + kk * o[0] * o[0], 2.0f * kk * o[0] * e, (dy * dy + dz * dz) * ip + kk * e * e};
+}
+
+// node offsets i = x - rint(X_x) of the row with s <= L, as [lo, hi] (empty:
+// lo > hi); xf = X_x - rint(X_x)
+__device__ __forceinline__ void row_range(const RowQuad &q, float L, float xf, int &lo, int &hi) {
+  const float disc = q.B * q.B - 4.0f * q.A * (q.C0 - L);
+  if (!(disc >= 0.0f)) {
+    lo = 1;
+    hi = 0;
+    return;
+  }
+  const float sq = sqrtf(disc), h = 0.5f / q.A;
+  lo = (int)ceilf((-q.B - sq) * h + xf);
+  hi = (int)floorf((-q.B + sq) * h + xf);
+}
+
+// Margin in s between the FP32 row intervals and the exact inside test: the
+// FP32 interval ends are off by less than 1e-4 in s for half-axis ratios up
+// to 100, so nodes with s <= 1 - ROW_EPS on a row's FP32 estimate are inside
+// and nodes with s > 1 + ROW_EPS are outside.
+constexpr float ROW_EPS = 2e-3f;
+
+// Claims (one block per cell, one thread per lattice row of the cell's box).
+// A node's cover by cell p can change only where the old and the new
+// ellipsoid differ: on each row, the nodes of the hull of the two outer
+// intervals (s <= 1 + ROW_EPS) that are not in both inner ones (s <= 1 -
+// ROW_EPS).  Those candidates get the exact inside test:
+//   owned by p and no longer inside -> TOUCHED (resolve finds the new owner)
+//   fluid and now inside            -> claim with p (atomicMin: lowest newcomer)
+// Every node inside some cell is owned by a cell after each resolve, so a
+// fluid node inside p is one that p's ellipsoid has just entered, and nodes
+// owned by another cell need no claim: their owner keeps them while it
+// covers them (first arrival), and hands them on through TOUCHED.
+// mode 1: no old ellipsoid (first particles_set, all owners fluid).
+// Also clears the cell's link count and contact sums for the geometry pass.
 __global__ void __launch_bounds__(CB) k_claims(LatticeView lv, PartView pv, int *claim, ChangeList chg, int mode) {
   __shared__ int sh_len;
   const int p = blockIdx.x;
   if (threadIdx.x == 0) {
     sh_len = 0;
+    pv.lk_count[p] = 0;  // the geometry pass appends the links and adds the contact sums
+    for (int k = 0; k < 3; ++k) {
+      pv.cK[3 * p + k] = 0;
+      pv.cIT[3 * p + k] = 0;
+    }
     if (p == 0) *chg.count = 0;
   }
   __syncthreads();
-  const int lo[3] = {pv.box[6 * p], pv.box[6 * p + 1], pv.box[6 * p + 2]};
-  const int hi[3] = {pv.box[6 * p + 3], pv.box[6 * p + 4], pv.box[6 * p + 5]};
-  BoxIter it;
-  it.init(lo, hi);
+  const int lo1 = pv.box[6 * p + 1], lo2 = pv.box[6 * p + 2];
+  const int by = pv.box[6 * p + 4] - lo1 + 1, bz = pv.box[6 * p + 5] - lo2 + 1;
+  const int rows = (by > 0 && bz > 0) ? by * bz : 0;
   CellGeo g;
   cell_geo(pv, p, g);
+  const bool has_old = mode != 1;
+  int Xo[3] = {0, 0, 0};
+  float xfo[3] = {0.f, 0.f, 0.f}, oo[3] = {0.f, 0.f, 0.f};
+  if (has_old) {
+    const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
+    Xo[0] = (int)k0.w;
+    Xo[1] = (int)k1.w;
+    Xo[2] = (int)k2.w;
+    xfo[0] = k0.x;
+    xfo[1] = k0.y;
+    xfo[2] = k0.z;
+    for (int k = 0; k < 3; ++k) oo[k] = pv.oprev[3 * p + k];
+  }
+  const float ip = (float)pv.inv_rperp2, kk = (float)(pv.inv_rpar2 - pv.inv_rperp2);
+  const int shift = imin_image(Xo[0] - g.Xi[0], lv.nx, lv.per[0]);  // old rint(X_x) from the new one
+  // offsets of one period (periodic x) or of the lattice (walled x)
+  const int imin = lv.per[0] ? -(lv.nx / 2) : -g.Xi[0];
+  const int imax = lv.per[0] ? imin + lv.nx - 1 : lv.nx - 1 - g.Xi[0];
   unsigned long long *touched = pv.touched + (size_t)p * pv.touched_cap;
-  // whole warps iterate together (the append is warp-collective)
-  const int iters = (it.total + CB - 1) / CB;
-  for (int k = 0; k < iters; ++k, it.advance()) {
-    const int t = k * CB + threadIdx.x;
-    int mark = 0;
-    int x = 0, y = 0, z = 0;
-    if (t < it.total) {
-      x = lo[0] + it.ix;
-      y = lo[1] + it.iy;
-      z = lo[2] + it.iz;
+  for (int t = threadIdx.x; t < rows; t += CB) {
+    int y = lo1 + t % by, z = lo2 + t / by;
+    if (lv.per[1]) y = wrapi(y, lv.ny);
+    if (lv.per[2]) z = wrapi(z, lv.nz);
+    const RowQuad qn = row_quad((float)imin_image(y - g.Xi[1], lv.ny, lv.per[1]) - g.Xf[1],
+                                (float)imin_image(z - g.Xi[2], lv.nz, lv.per[2]) - g.Xf[2], g.of, ip, kk);
+    int ao, bo, ai, bi;
+    row_range(qn, 1.0f + ROW_EPS, g.Xf[0], ao, bo);
+    row_range(qn, 1.0f - ROW_EPS, g.Xf[0], ai, bi);
+    if (has_old) {
+      const RowQuad qo = row_quad((float)imin_image(y - Xo[1], lv.ny, lv.per[1]) - xfo[1],
+                                  (float)imin_image(z - Xo[2], lv.nz, lv.per[2]) - xfo[2], oo, ip, kk);
+      int ao2, bo2, ai2, bi2;
+      row_range(qo, 1.0f + ROW_EPS, xfo[0], ao2, bo2);
+      row_range(qo, 1.0f - ROW_EPS, xfo[0], ai2, bi2);
+      if (ao2 <= bo2) {
+        if (ao > bo) {
+          ao = ao2 + shift;
+          bo = bo2 + shift;
+        } else {
+          ao = min(ao, ao2 + shift);
+          bo = max(bo, bo2 + shift);
+        }
+      }
+      if (ai2 <= bi2) {
+        ai = max(ai, ai2 + shift);
+        bi = min(bi, bi2 + shift);
+      } else {
+        ai = 1;
+        bi = 0;
+      }
+    } else {
+      ai = 1;  // nothing was covered: every node of the new interval
+      bi = 0;
+    }
+    ao = max(ao, imin);
+    bo = min(bo, imax);
+    if (ao > bo) continue;
+    // candidates: [ao, bo] without the common core [ai, bi]
+    const bool core = ai <= bi;
+    const int e1 = core ? min(bo, ai - 1) : bo;
+    const int s2 = core ? max(ao, bi + 1) : bo + 1;
+    for (int i = ao; i <= bo; ++i) {
+      if (i > e1 && i < s2) {
+        i = s2 - 1;
+        continue;
+      }
+      int x = g.Xi[0] + i;
       if (lv.per[0]) x = wrapi(x, lv.nx);
-      if (lv.per[1]) y = wrapi(y, lv.ny);
-      if (lv.per[2]) z = wrapi(z, lv.nz);
       const unsigned idx = node_of(lv, x, y, z);
       const int ow = lv.owner[idx];
-      if (ow > -2) {
-        const bool ins = inside_cell(x, y, z, g.X, g.o, g.Xf, g.Xi, g.of, pv, lv);
-        if (mode != 1 && ow == p && !ins) {
+      int mark = 0;
+      if (ow == p) {
+        if (!inside_cell(x, y, z, g.X, g.o, g.Xf, g.Xi, g.of, pv, lv)) {
           atomicMin(&claim[idx], CLAIM_TOUCHED);
           mark = 1;
-        } else if (ow != p && ins) {
+        }
+      } else if (ow == FLUID) {
+        if (inside_cell(x, y, z, g.X, g.o, g.Xf, g.Xi, g.of, pv, lv)) {
           atomicMin(&claim[idx], p);
           mark = 1;
         }
       }
-    }
-    const int pos = warp_append(mark, &sh_len);
-    if (mark) {
-      if (pos < pv.touched_cap) touched[pos] = pack_xyzr(x, y, z, 0);
-      else atomicOr(pv.status, ST_OVERFLOW);
+      if (mark) {
+        const int pos = atomicAdd(&sh_len, 1);
+        if (pos < pv.touched_cap) touched[pos] = pack_xyzr(x, y, z, 0);
+        else atomicOr(pv.status, ST_OVERFLOW);
+      }
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) pv.touched_count[p] = min(sh_len, pv.touched_cap);
 }
 
-// geometry of the new owner map (one block per cell): the cell's bounce
-// links (fluid node y, direction r from y into the cell) and its contact
-// links as exact integer sums with the lever arm's integer part dI = x - rint(X)
-__global__ void __launch_bounds__(CB) k_geometry(LatticeView lv, PartView pv) {
-  using D = D3Q19;
-  __shared__ int sh_len;
-  __shared__ int shi[CB / 32][6];
-  const int p = blockIdx.x;
-  if (threadIdx.x == 0) sh_len = 0;
-  __syncthreads();
-  const int lo[3] = {pv.box[6 * p], pv.box[6 * p + 1], pv.box[6 * p + 2]};
-  const int hi[3] = {pv.box[6 * p + 3], pv.box[6 * p + 4], pv.box[6 * p + 5]};
-  BoxIter it;
-  it.init(lo, hi);
-  const float4 k0 = pv.kin_next[3 * p], k1 = pv.kin_next[3 * p + 1], k2 = pv.kin_next[3 * p + 2];
-  const int Xi[3] = {(int)k0.w, (int)k1.w, (int)k2.w};
-  unsigned long long *lk = pv.lk + (size_t)p * pv.lk_cap;
-  int ci[6] = {0, 0, 0, 0, 0, 0};
-  const int iters = (it.total + CB - 1) / CB;
-  for (int k = 0; k < iters; ++k, it.advance()) {
-    const int t = k * CB + threadIdx.x;
-    unsigned lmask = 0;
-    int xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
-    if (t < it.total) {
-      int x = lo[0] + it.ix, y = lo[1] + it.iy, z = lo[2] + it.iz;
-      if (lv.per[0]) x = wrapi(x, lv.nx);
-      if (lv.per[1]) y = wrapi(y, lv.ny);
-      if (lv.per[2]) z = wrapi(z, lv.nz);
-      if (lv.owner[node_of(lv, x, y, z)] == p) {
-        xs[0] = x == 0 ? lv.nx - 1 : x - 1; xs[1] = x; xs[2] = x == lv.nx - 1 ? 0 : x + 1;
-        ys[0] = y == 0 ? lv.ny - 1 : y - 1; ys[1] = y; ys[2] = y == lv.ny - 1 ? 0 : y + 1;
-        zs[0] = z == 0 ? lv.nz - 1 : z - 1; zs[1] = z; zs[2] = z == lv.nz - 1 ? 0 : z + 1;
-        int on[Q];
-        sfor<1, Q>([&](auto R) {
-          constexpr int r = decltype(R)::value;
-          on[r] = lv.owner[node_of(lv, xs[1 + D::cx(r)], ys[1 + D::cy(r)], zs[1 + D::cz(r)])];
-        });
-        const int di[3] = {imin_image(x - Xi[0], lv.nx, lv.per[0]), imin_image(y - Xi[1], lv.ny, lv.per[1]),
-                           imin_image(z - Xi[2], lv.nz, lv.per[2])};
-        sfor<1, Q>([&](auto R) {
-          constexpr int r = decltype(R)::value;
-          constexpr int m = D::m(r);
-          if (on[r] == FLUID) {
-            lmask |= 1u << r;
-          } else if (on[r] != p) {
-            ci[0] -= m * D::cx(r);
-            ci[1] -= m * D::cy(r);
-            ci[2] -= m * D::cz(r);
-            ci[3] -= m * (di[1] * D::cz(r) - di[2] * D::cy(r));
-            ci[4] -= m * (di[2] * D::cx(r) - di[0] * D::cz(r));
-            ci[5] -= m * (di[0] * D::cy(r) - di[1] * D::cx(r));
+// lowest-index cell whose ellipsoid covers node (x, y, z), FLUID if none.
+// Cells are searched in the node's bin and its neighbours: a bin is at least
+// r_cut wide, r_cut exceeds the largest half-axis by one node, and a cell
+// moves less than half a node per step, so the cell list of the step's start
+// holds every cover of the node.  Bins list their cells in index order.
+__device__ int lowest_cover(const LatticeView &lv, const PartView &pv, const CellListView &cl, int x, int y, int z) {
+  const int c[3] = {x, y, z};
+  const int dims[3] = {lv.nx, lv.ny, lv.nz};
+  int bc[3], off[3][3], noff[3];
+  for (int k = 0; k < 3; ++k) {
+    bc[k] = (int)(((long long)c[k] * cl.nb[k]) / dims[k]);
+    noff[k] = bin_offsets(cl.nb[k], lv.per[k], bc[k], off[k]);
+  }
+  int best = INT_MAX;
+  for (int iz = 0; iz < noff[2]; ++iz)
+    for (int iy = 0; iy < noff[1]; ++iy)
+      for (int ix = 0; ix < noff[0]; ++ix) {
+        const int b = wrapi(bc[0] + off[0][ix], cl.nb[0]) +
+                      cl.nb[0] * (wrapi(bc[1] + off[1][iy], cl.nb[1]) + cl.nb[1] * wrapi(bc[2] + off[2][iz], cl.nb[2]));
+        const int e = cl.start[b + 1];
+        for (int k = cl.start[b]; k < e; ++k) {
+          const int j = cl.ids[k];
+          if (j >= best) break;
+          CellGeo g;
+          cell_geo(pv, j, g);
+          if (inside_cell(x, y, z, g.X, g.o, g.Xf, g.Xi, g.of, pv, lv)) {
+            best = j;
+            break;
           }
-        });
+        }
       }
-    }
-    int pos = warp_append(__popc(lmask), &sh_len);
-    while (lmask) {
-      const int r = __ffs(lmask) - 1;
-      lmask &= lmask - 1;
-      // the fluid node y = x + c_r bounces direction rbar into this cell
-      const int yx = xs[1 + D::cx(r)], yy = ys[1 + D::cy(r)], yz = zs[1 + D::cz(r)];
-      if (pos < pv.lk_cap) lk[pos] = pack_xyzr(yx, yy, yz, D::opp(r));
-      else atomicOr(pv.status, ST_OVERFLOW);
-      ++pos;
-    }
-  }
-  block_sum_i<6>(ci, shi);
-  if (threadIdx.x == 0) {
-    pv.lk_count[p] = min(sh_len, pv.lk_cap);
-    for (int k = 0; k < 3; ++k) {
-      pv.cK[3 * p + k] = ci[k];
-      pv.cIT[3 * p + k] = ci[3 + k];
-    }
-  }
+  return best == INT_MAX ? FLUID : best;
 }
 
 // ---------------------------------------------------------------------------
@@ -1032,8 +1101,8 @@ __device__ __forceinline__ void atomic_add3(double *a, const double v[3]) {
 }
 
 template <class S>
-__global__ void __launch_bounds__(CB) k_resolve_fill(LatticeView lv, PartView pv, int *claim, ChangeList chg,
-                                                      int par_next, int impulses) {
+__global__ void __launch_bounds__(CB) k_resolve_fill(LatticeView lv, PartView pv, CellListView cl, int *claim,
+                                                      ChangeList chg, int par_next, int impulses) {
   using D = D3Q19;
   const int p = blockIdx.x;
   const int nt = pv.touched_count[p];
@@ -1053,16 +1122,10 @@ __global__ void __launch_bounds__(CB) k_resolve_fill(LatticeView lv, PartView pv
       const int c = atomicExch(&claim[idx], CLAIM_FREE);
       if (c != CLAIM_FREE) {
         old = lv.owner[idx];
-        if (c == CLAIM_TOUCHED) {
-          nw = FLUID;
-        } else if (old >= 0) {
-          // first arrival: the old owner keeps the node while it covers it
-          CellGeo g;
-          cell_geo(pv, old, g);
-          nw = inside_cell(xyz[0], xyz[1], xyz[2], g.X, g.o, g.Xf, g.Xi, g.of, pv, lv) ? old : c;
-        } else {
-          nw = c;
-        }
+        // TOUCHED: the old owner left the node -> the lowest-index cell now
+        // covering it, else fluid; a claim: a fluid node entered by the
+        // claimants, the lowest of which takes it (reading Q5)
+        nw = c == CLAIM_TOUCHED ? lowest_cover(lv, pv, cl, xyz[0], xyz[1], xyz[2]) : c;
         changed = nw != old;
         if (changed) lv.owner[idx] = nw;
       }
@@ -1217,20 +1280,15 @@ void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const 
   *nl += 1;
 }
 
-void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg,
-                         int par_next, int impulses, cudaStream_t st, int64_t *nl) {
+void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, const CellListView &cl, int *claim,
+                         const ChangeList &chg, int par_next, int impulses, cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  if (dtype == 0) k_resolve_fill<float><<<pv.n, CB, 0, st>>>(lv, pv, claim, chg, par_next, impulses);
-  else if (dtype == 1) k_resolve_fill<__nv_bfloat16><<<pv.n, CB, 0, st>>>(lv, pv, claim, chg, par_next, impulses);
-  else k_resolve_fill<__half><<<pv.n, CB, 0, st>>>(lv, pv, claim, chg, par_next, impulses);
+  if (dtype == 0) k_resolve_fill<float><<<pv.n, CB, 0, st>>>(lv, pv, cl, claim, chg, par_next, impulses);
+  else if (dtype == 1) k_resolve_fill<__nv_bfloat16><<<pv.n, CB, 0, st>>>(lv, pv, cl, claim, chg, par_next, impulses);
+  else k_resolve_fill<__half><<<pv.n, CB, 0, st>>>(lv, pv, cl, claim, chg, par_next, impulses);
   *nl += 1;
 }
 
-void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl) {
-  if (pv.n == 0) return;
-  k_geometry<<<pv.n, CB, 0, st>>>(lv, pv);
-  *nl += 1;
-}
 
 void launch_clear_cells(int dtype, const LatticeView &lv, int par, cudaStream_t st, int64_t *nl) {
   const unsigned b = 256, g = nblk(lv.N, b);

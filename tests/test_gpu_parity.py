@@ -153,6 +153,41 @@ def test_overlap_and_wall_contacts_bitexact():
     assert rel(parts["PT"], PT_o) < 1e-6
 
 
+def test_random_resets_and_overlap_steps_bitexact():
+    """Cells set again at random jumps and turns (overlaps allowed), then
+    stepped while overlapping: every owner map bit-exact, impulses close."""
+    oracle, bl, workloads = _mods()
+    p = workloads.base_params(30, 26, 22, periodic=(1, 1, 0), R=(5.0, 2.5))
+    rng = np.random.default_rng(17)
+    n = 12
+    X = np.column_stack([rng.uniform(0, 30, n), rng.uniform(0, 26, n), rng.uniform(6.5, 15.5, n)])
+    _, q = workloads.random_axes_and_quaternions(rng, n)
+    V, L = np.zeros((n, 3)), np.zeros((n, 3))
+    orc, sim = oracle.Oracle(p), bl.Simulation(p)
+    orc.set_particles(X, q, V, L)
+    sim.set_particles(X, q, V, L)
+    np.testing.assert_array_equal(sim.owner(), orc.owner())
+    for k in range(5):
+        X = X + rng.uniform(-2.0, 2.0, (n, 3))
+        X[:, 0] %= 30.0
+        X[:, 1] %= 26.0
+        X[:, 2] = np.clip(X[:, 2], 6.5, 15.5)
+        _, q = workloads.random_axes_and_quaternions(rng, n)
+        V = rng.uniform(-0.02, 0.02, (n, 3))
+        orc.set_particles(X, q, V, L)
+        sim.set_particles(X, q, V, L)
+        np.testing.assert_array_equal(sim.owner(), orc.owner())
+        PF_o, PT_o = orc.pending()
+        parts = sim.force_parts()
+        assert rel(parts["PF"], PF_o) < 1e-6 and rel(parts["PT"], PT_o) < 1e-6
+        np.testing.assert_array_equal(sim.contact_links(), orc.contact_links())
+    for s in range(20):
+        orc.step(1)
+        sim.step(1)
+        np.testing.assert_array_equal(sim.owner(), orc.owner())
+    sim.sync()
+
+
 @pytest.mark.parametrize("mu", [0.0, 2.0])
 def test_coupled_100_steps(mu):
     oracle, bl, workloads = _mods()

@@ -1062,7 +1062,11 @@ __global__ void __launch_bounds__(CB) k_claims(LatticeView lv, PartView pv, int 
 // r_cut wide, r_cut exceeds the largest half-axis by one node, and a cell
 // moves less than half a node per step, so the cell list of the step's start
 // holds every cover of the node.  Bins list their cells in index order.
-__device__ int lowest_cover(const LatticeView &lv, const PartView &pv, const CellListView &cl, int x, int y, int z) {
+// (one warp per node: lane b < 27 scans neighbouring bin b, the lowest
+// covering index over the lanes wins; all 32 lanes call it)
+__device__ int lowest_cover(const LatticeView &lv, const PartView &pv, const CellListView &cl, int x, int y,
+                                 int z) {
+  const int lane = threadIdx.x & 31;
   const int c[3] = {x, y, z};
   const int dims[3] = {lv.nx, lv.ny, lv.nz};
   int bc[3], off[3][3], noff[3];
@@ -1071,23 +1075,22 @@ __device__ int lowest_cover(const LatticeView &lv, const PartView &pv, const Cel
     noff[k] = bin_offsets(cl.nb[k], lv.per[k], bc[k], off[k]);
   }
   int best = INT_MAX;
-  for (int iz = 0; iz < noff[2]; ++iz)
-    for (int iy = 0; iy < noff[1]; ++iy)
-      for (int ix = 0; ix < noff[0]; ++ix) {
-        const int b = wrapi(bc[0] + off[0][ix], cl.nb[0]) +
-                      cl.nb[0] * (wrapi(bc[1] + off[1][iy], cl.nb[1]) + cl.nb[1] * wrapi(bc[2] + off[2][iz], cl.nb[2]));
-        const int e = cl.start[b + 1];
-        for (int k = cl.start[b]; k < e; ++k) {
-          const int j = cl.ids[k];
-          if (j >= best) break;
-          CellGeo g;
-          cell_geo(pv, j, g);
-          if (inside_cell(x, y, z, g.X, g.o, g.Xf, g.Xi, g.of, pv, lv)) {
-            best = j;
-            break;
-          }
-        }
+  const int ix = lane % 3, iy = (lane / 3) % 3, iz = lane / 9;
+  if (lane < 27 && ix < noff[0] && iy < noff[1] && iz < noff[2]) {
+    const int b = wrapi(bc[0] + off[0][ix], cl.nb[0]) +
+                  cl.nb[0] * (wrapi(bc[1] + off[1][iy], cl.nb[1]) + cl.nb[1] * wrapi(bc[2] + off[2][iz], cl.nb[2]));
+    const int e = cl.start[b + 1];
+    for (int k = cl.start[b]; k < e; ++k) {
+      const int j = cl.ids[k];
+      CellGeo g;
+      cell_geo(pv, j, g);
+      if (inside_cell(x, y, z, g.X, g.o, g.Xf, g.Xi, g.of, pv, lv)) {
+        best = j;
+        break;
       }
+    }
+  }
+  best = __reduce_min_sync(0xffffffffu, best);
   return best == INT_MAX ? FLUID : best;
 }
 
@@ -1110,25 +1113,48 @@ __global__ void __launch_bounds__(CB) k_resolve_fill(LatticeView lv, PartView pv
   const int lane = threadIdx.x & 31;
   S *pop = reinterpret_cast<S *>(lv.pop);
   const int dims[3] = {lv.nx, lv.ny, lv.nz};
+  __shared__ int s_need[CB], s_res[CB];
+  __shared__ int s_ns;
   for (int t0 = 0; t0 < nt; t0 += CB) {
     const int t = t0 + threadIdx.x;
     int old = 0, nw = 0, xyz[3] = {0, 0, 0};
-    bool changed = false;
+    bool changed = false, act = false, need = false;
     unsigned idx = 0;
+    if (threadIdx.x == 0) s_ns = 0;
+    __syncthreads();
     if (t < nt) {
       int r_unused;
       unpack_xyzr(touched[t], xyz, r_unused);
       idx = node_of(lv, xyz[0], xyz[1], xyz[2]);
       const int c = atomicExch(&claim[idx], CLAIM_FREE);
       if (c != CLAIM_FREE) {
+        act = true;
         old = lv.owner[idx];
         // TOUCHED: the old owner left the node -> the lowest-index cell now
-        // covering it, else fluid; a claim: a fluid node entered by the
-        // claimants, the lowest of which takes it (reading Q5)
-        nw = c == CLAIM_TOUCHED ? lowest_cover(lv, pv, cl, xyz[0], xyz[1], xyz[2]) : c;
-        changed = nw != old;
-        if (changed) lv.owner[idx] = nw;
+        // covering it (searched below by a warp), else fluid; a claim: a
+        // fluid node entered by the claimants, the lowest of which takes it
+        // (reading Q5)
+        if (c == CLAIM_TOUCHED) {
+          need = true;
+          s_need[atomicAdd(&s_ns, 1)] = threadIdx.x;
+        } else {
+          nw = c;
+        }
       }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x >> 5; k < s_ns; k += CB / 32) {
+      const int tt = s_need[k];
+      int cc[3], r_unused;
+      unpack_xyzr(touched[t0 + tt], cc, r_unused);
+      const int best = lowest_cover(lv, pv, cl, cc[0], cc[1], cc[2]);
+      if (lane == 0) s_res[tt] = best;
+    }
+    __syncthreads();
+    if (act) {
+      if (need) nw = s_res[threadIdx.x];
+      changed = nw != old;
+      if (changed) lv.owner[idx] = nw;
     }
     // warp-level compaction of the changed nodes into the diagnostic list
     const unsigned bal = __ballot_sync(0xffffffffu, changed);

@@ -172,8 +172,6 @@ def run_gpu(args, ws, rank, local):
     sim.set_particles(X, q)
     sim.step(args.warmup)
     sim.sync()
-    bl.bl_timing_enable(sim.ctx, True)
-    bl.bl_timing_read(sim.ctx)  # clear
     launches0 = bl.bl_launch_count(sim.ctx)
     clocks = ClockSampler(local)
     clocks.start()
@@ -189,6 +187,18 @@ def run_gpu(args, ws, rank, local):
     ms = e0.elapsed_time(e1)
     sim.sync()
     launches = bl.bl_launch_count(sim.ctx) - launches0
+    # per-kernel times from a separate instrumented run (CUDA events around
+    # every kernel group on the stream it runs on; no graph replay there)
+    bl.bl_timing_enable(sim.ctx, True)
+    bl.bl_timing_read(sim.ctx)  # clear
+    k_inst = max(20, min(args.steps, 200))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(k_inst)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_inst = e0.elapsed_time(e1)
+    sim.sync()
     groups = bl.bl_timing_read(sim.ctx)
     bl.bl_timing_enable(sim.ctx, False)
     ms_max = allreduce_max(ms, ws)
@@ -216,6 +226,8 @@ def run_gpu(args, ws, rank, local):
                      else "fallback 6.8 TB/s", "kernel": "k_lb_step (fused collide/stream/bounce-back)",
                      "bytes_per_launch": bytes_per, "launch_ms": round(k1_ms / max(k1_n, 1), 5)},
         "kernel_time_share": group_share,
+        "instrumented": {"steps": k_inst, "ms_per_step": round(ms_inst / k_inst, 5),
+                         "note": "per-kernel CUDA events, no graph replay; roofline and shares from this run"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": e2e,

@@ -31,7 +31,18 @@ constexpr int MAX_TIMED = 1 << 16;
 struct bl_ctx {
   bl_lb_params lp;
   bl_particle_params pp;
-  cudaStream_t stream;
+  cudaStream_t stream;  // the caller's stream: every call is ordered on it
+  // the cell list and the potentials of a step run on a second stream,
+  // overlapped with the lattice sweep (they touch disjoint data)
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
+  // repeated steps replay a CUDA graph of two steps (even + odd parity) on
+  // an internal stream, forked from and joined to the caller's stream
+  cudaStream_t gstream;
+  cudaGraphExec_t gexec;
+  int g_parity;
+  const void *g_kin;
+  int64_t g_launches;
   int dtype;
   int parity;  // layout of the current populations (next step's parity)
   LatticeView lv;
@@ -59,6 +70,8 @@ struct bl_ctx {
   double t_ms[NGROUPS];
   int64_t t_cnt[NGROUPS];
 };
+
+static void drop_graph(bl_ctx *c);
 
 static int fail(bl_ctx *c, int code, const char *fmt, ...) {
   if (c && c->sticky == BL_OK) {
@@ -100,7 +113,7 @@ static int ensure_scratch(bl_ctx *c, size_t bytes) {
 // ---------------------------------------------------------------------------
 // timing
 
-static void group_begin(bl_ctx *c, int g, int *slot) {
+static void group_begin(bl_ctx *c, int g, int *slot, cudaStream_t st) {
   *slot = -1;
   if (!c->timing || c->ev_used >= MAX_TIMED) return;
   const int s = c->ev_used++;
@@ -112,12 +125,12 @@ static void group_begin(bl_ctx *c, int g, int *slot) {
     c->ev_group.push_back(g);
   }
   c->ev_group[s] = g;
-  cudaEventRecord(c->ev[2 * s], c->stream);
+  cudaEventRecord(c->ev[2 * s], st);
   *slot = s;
 }
 
-static void group_end(bl_ctx *c, int slot) {
-  if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], c->stream);
+static void group_end(bl_ctx *c, int slot, cudaStream_t st) {
+  if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], st);
 }
 
 static int harvest_timing(bl_ctx *c) {
@@ -206,6 +219,13 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
     if (cudaMalloc(&lv.owner, sizeof(int32_t) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "owner map"); break; }
     if (cudaMalloc(&c->claim, sizeof(int) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "claim map"); break; }
     if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "status"); break; }
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      rc = fail(c, BL_ECUDA, "streams");
+      break;
+    }
     if (cudaMalloc(&c->wacc.F, sizeof(double) * bl::NWALL * 3) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "wall"); break; }
     if (cudaMalloc(&c->wacc.K, sizeof(long long) * bl::NWALL * 3) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "wall"); break; }
     cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
@@ -239,6 +259,7 @@ extern "C" int bl_walls_set(bl_ctx *c, const uint8_t *mask) {
   uint8_t *d = nullptr;
   CU(cudaMalloc(&d, c->lv.N));
   CU(cudaMemcpyAsync(d, mask, c->lv.N, cudaMemcpyHostToDevice, c->stream));
+  drop_graph(c);
   launch_apply_wall_mask(c->lv, d, c->stream);
   c->launches++;
   launch_geometry(c->lv, c->pv, c->stream, &c->launches);
@@ -390,6 +411,7 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
         return fail(c, BL_EINVAL, "periodic length %d < 2 max(R) + 4", dims[k]);
   }
   const bool first = n != c->np || c->np == 0;
+  drop_graph(c);  // the cell arrays may move; the graph holds their pointers
   if (first) {
     // cells of a previous call become resting fluid
     launch_clear_cells(c->dtype, c->lv, c->parity, c->stream, &c->launches);
@@ -436,38 +458,97 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
   return BL_OK;
 }
 
-static int enqueue_step(bl_ctx *c) {
+// one step on stream st (the caller's stream, or the graph stream while a
+// graph is captured)
+static int enqueue_step(bl_ctx *c, cudaStream_t st) {
   int slot;
-  group_begin(c, 0, &slot);
-  launch_lb_step(c->dtype, c->lv, c->parity, c->wacc, c->status, c->stream);
-  group_end(c, slot);
+  if (c->np > 0) {
+    // cell list and potentials from the state at t, beside the sweep
+    cudaEventRecord(c->ev_fork, st);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    group_begin(c, 1, &slot, c->side);
+    launch_cell_list(c->lv, c->pv, c->cl, c->side, &c->launches);
+    group_end(c, slot, c->side);
+    group_begin(c, 2, &slot, c->side);
+    launch_forces(c->lv, c->pv, c->cl, c->sbits, c->side, &c->launches);
+    group_end(c, slot, c->side);
+    cudaEventRecord(c->ev_join, c->side);
+  }
+  group_begin(c, 0, &slot, st);
+  launch_lb_step(c->dtype, c->lv, c->parity, c->wacc, c->status, st);
+  group_end(c, slot, st);
   c->launches++;
   if (c->np > 0) {
-    group_begin(c, 1, &slot);
-    launch_cell_list(c->lv, c->pv, c->cl, c->stream, &c->launches);
-    group_end(c, slot);
-    group_begin(c, 2, &slot);
-    launch_forces(c->lv, c->pv, c->cl, c->sbits, c->stream, &c->launches);
-    group_end(c, slot);
-    group_begin(c, 3, &slot);
-    launch_cell_step(c->dtype, c->lv, c->pv, c->parity, c->stream, &c->launches);
-    group_end(c, slot);
-    group_begin(c, 4, &slot);
-    launch_claims(c->lv, c->pv, c->claim, c->chg, 0, c->stream, &c->launches);
-    launch_resolve_fill(c->dtype, c->lv, c->pv, c->cl, c->claim, c->chg, c->parity ^ 1, 1, c->stream, &c->launches);
-    launch_geometry(c->lv, c->pv, c->stream, &c->launches);
-    group_end(c, slot);
+    cudaStreamWaitEvent(st, c->ev_join, 0);
+    group_begin(c, 3, &slot, st);
+    launch_cell_step(c->dtype, c->lv, c->pv, c->parity, st, &c->launches);
+    group_end(c, slot, st);
+    group_begin(c, 4, &slot, st);
+    launch_claims(c->lv, c->pv, c->claim, c->chg, 0, st, &c->launches);
+    launch_resolve_fill(c->dtype, c->lv, c->pv, c->cl, c->claim, c->chg, c->parity ^ 1, 1, st, &c->launches);
+    launch_geometry(c->lv, c->pv, st, &c->launches);
+    group_end(c, slot, st);
     std::swap(c->pv.kin, c->pv.kin_next);
   }
   c->parity ^= 1;
   return check_launch(c, "step");
 }
 
+static void drop_graph(bl_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+}
+
+// the graph of two steps from the current parity and cell state
+static int capture_graph(bl_ctx *c) {
+  drop_graph(c);
+  const int64_t l0 = c->launches;
+  const int par = c->parity;
+  const void *kin = c->pv.kin;
+  cudaGraph_t g = nullptr;
+  CU(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_step(c, c->gstream);
+  if (rc == BL_OK) rc = enqueue_step(c, c->gstream);
+  cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
+  // capturing records the kernels without running them: the two steps
+  // flipped the parity and swapped the kinematics buffers twice, but an
+  // aborted capture may have stopped after one
+  c->parity = par;
+  if (c->pv.kin != (const float4 *)kin) std::swap(c->pv.kin, c->pv.kin_next);
+  c->g_launches = c->launches - l0;
+  c->launches = l0;
+  if (rc != BL_OK) return rc;
+  if (e != cudaSuccess) return fail(c, BL_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->gexec = nullptr;
+    return fail(c, BL_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  c->g_parity = par;
+  c->g_kin = kin;
+  return BL_OK;
+}
+
 extern "C" int bl_step(bl_ctx *c, int nsteps) {
   if (!c || nsteps < 0) return BL_EINVAL;
   if (c->sticky) return c->sticky;
-  for (int s = 0; s < nsteps; ++s)
-    if (enqueue_step(c)) return c->sticky;
+  int s = 0;
+  if (!c->timing && nsteps >= 2) {
+    // pairs of steps as one graph launch
+    if (!c->gexec || c->g_parity != c->parity || c->g_kin != (const void *)c->pv.kin)
+      if (capture_graph(c)) return c->sticky;
+    CU(cudaEventRecord(c->ev_fork, c->stream));
+    CU(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0));
+    for (; s + 2 <= nsteps; s += 2) {
+      CU(cudaGraphLaunch(c->gexec, c->gstream));
+      c->launches += c->g_launches;
+    }
+    CU(cudaEventRecord(c->ev_join, c->gstream));
+    CU(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  }
+  for (; s < nsteps; ++s)
+    if (enqueue_step(c, c->stream)) return c->sticky;
   return BL_OK;
 }
 
@@ -662,6 +743,11 @@ extern "C" const char *bl_last_error(const bl_ctx *c) { return c ? c->err : "nul
 extern "C" void bl_destroy(bl_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   free_particles(c);
   void *ptrs[] = {c->lv.pop, c->lv.owner, c->lv.rho_b, c->lv.nbm, c->claim, c->status, c->wacc.F, c->wacc.K,
                   c->sbits.bits, c->scratch};

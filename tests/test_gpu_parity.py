@@ -336,3 +336,27 @@ def test_full_size_shear_cell_owner_map_and_one_step():
     fl = np.flatnonzero(own == -1)
     sample = rng.choice(fl, 20000, replace=False)
     assert rel(u_g[sample], u_o[sample]) < 1e-5
+
+
+def test_graph_replay_matches_single_steps():
+    """Repeated steps replay a captured two-step graph; the result must match
+    the same steps enqueued one by one (owner maps exactly; fields and cell
+    state to FP32 round-off, since float atomics may add in another order)."""
+    oracle, bl, workloads = _mods()
+    p, X, q, V, L = _coupled(0.0, seed=1011)
+    a, b = bl.Simulation(p), bl.Simulation(p)
+    a.set_particles(X, q, V, L)
+    b.set_particles(X, q, V, L)
+    for _ in range(21):
+        a.step(1)
+    b.step(10)
+    b.step(11)  # five graph launches and one single step
+    a.sync()
+    b.sync()
+    np.testing.assert_array_equal(a.owner(), b.owner())
+    pa, pb = a.particles(), b.particles()
+    for k in ("X", "q", "V", "L", "F", "T"):
+        assert rel(pb[k], pa[k]) < 1e-6, k
+    ra, ua, _ = a.fields()
+    rb, ub, _ = b.fields()
+    assert rel(ub, ua) < 1e-6 and rel(rb - 1.0, ra - 1.0) < 1e-5

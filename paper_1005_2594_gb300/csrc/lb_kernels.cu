@@ -41,7 +41,9 @@ namespace bl {
 #define BL_LB_MINB 8
 #endif
 
-template <class S, int PAR>
+// FORCE: a body force is set (Guo forcing); TAU1: tau = 1, where the
+// relaxation gives the equilibrium itself
+template <class S, int PAR, bool FORCE, bool TAU1>
 __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, WallAcc wa, int *status) {
   using D = D3Q19;
   const int nx = lv.nx, ny = lv.ny;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, Wal
     const float rho = lv.rho0 + drho;
     const float inv = 1.0f / rho;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (lv.has_force) {
+    if constexpr (FORCE) {
       Fx = rho * lv.g[0];
       Fy = rho * lv.g[1];
       Fz = rho * lv.g[2];
@@ -114,61 +116,83 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, Wal
     if (!(rho > 0.f) || !(uu < 0.09f)) atomicOr(status, ST_UNSTABLE);
     const float om = lv.omega;
     const float src_w = 1.0f - 0.5f * om;
-    // collision in place: f[r] <- f~*_r
-    sfor<0, Q>([&](auto R) {
-      constexpr int r = decltype(R)::value;
+    const float uF = ux * Fx + uy * Fy + uz * Fz;
+    // relaxation toward the shifted equilibrium w (drho + rho t); rho t is
+    // taken as rho_bar t + drho t, which keeps the small deviation exact in
+    // FP32; the Guo source with cu = c.u, cF = c.F
+    auto relax = [&](float fr, float w, float t, float cu, float cF) {
+      const float feq = w * (drho + fmaf(drho, t, lv.rho0 * t));
+      float fs = TAU1 ? feq : fr - om * (fr - feq);
+      if constexpr (FORCE) fs += src_w * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
+      return fs;
+    };
+    // third-order equilibrium in pairs r, rbar = r + 1 (c_rbar = -c_r):
+    // t = E + O and E - O with the even part E = 4.5 cu^2 - 1.5 uu and the
+    // odd part O = cu (3 + 4.5 cu^2 - 4.5 uu)
+    const float a = 3.0f - 4.5f * uu, b = 1.5f * uu;
+    f[0] = relax(f[0], 12.0f / 36.0f, -b, 0.f, 0.f);
+    sfor<0, 9>([&](auto P) {
+      constexpr int r = 2 * decltype(P)::value + 1, rb = r + 1;
       constexpr float w = D::m(r) / 36.0f;
-      const float cu = D::cx(r) * ux + D::cy(r) * uy + D::cz(r) * uz;
-      const float t = cu * (3.0f + cu * (4.5f + 4.5f * cu)) - uu * (1.5f + 4.5f * cu);
-      // rho t = rho_bar t + drho t keeps the small deviation exact in FP32
-      const float feq = w * (drho + lv.rho0 * t + drho * t);
-      float fs = f[r] - om * (f[r] - feq);
-      if (lv.has_force) {
-        const float cF = D::cx(r) * Fx + D::cy(r) * Fy + D::cz(r) * Fz;
-        const float Sg = w * (3.0f * (cF - (ux * Fx + uy * Fy + uz * Fz)) + 9.0f * cu * cF);
-        fs += src_w * Sg;
-      }
-      f[r] = fs;
+      float cu = 0.f, cF = 0.f;
+      if constexpr (D::cx(r) != 0) cu += D::cx(r) * ux;
+      if constexpr (D::cy(r) != 0) cu += D::cy(r) * uy;
+      if constexpr (D::cz(r) != 0) cu += D::cz(r) * uz;
+      if constexpr (FORCE) cF = D::cx(r) * Fx + D::cy(r) * Fy + D::cz(r) * Fz;
+      const float q = 4.5f * cu * cu;
+      const float E = q - b, O = cu * (a + q);
+      f[r] = relax(f[r], w, E + O, cu, cF);
+      f[rb] = relax(f[rb], w, E - O, -cu, -cF);
     });
     Store<S>::st(pop + n, f[0]);
-    sfor<1, Q>([&](auto R) {
-      constexpr int r = decltype(R)::value;
-      constexpr int rb = D::opp(r);
-      const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
-      if (!(solid & (1u << r))) {
-        const unsigned dst = PAR == 0 ? (unsigned)rb * N + n : (unsigned)r * N + nb;
+    if (solid == 0u) {
+      // no solid neighbour (most nodes): plain streaming
+      sfor<1, Q>([&](auto R) {
+        constexpr int r = decltype(R)::value;
+        const unsigned dst = PAR == 0 ? (unsigned)D::opp(r) * N + n
+                                      : (unsigned)r * N + xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
         Store<S>::st(pop + dst, f[r]);
-      } else {
-        // bounce-back into the slot where the next step reads direction rbar
-        const unsigned dst = PAR == 0 ? (unsigned)r * N + nb : (unsigned)rb * N + n;
-        float v = f[r];
-        if (wall & (1u << r)) {
-          const int w = -2 - lv.owner[nb];
-          // C for the population returning along rbar: 6 alpha_rbar rho c_rbar . v_wall
-          const float C = -(D::m(r) / 6.0f) * rho *
-                          (D::cx(r) * lv.wall_vel[w][0] + D::cy(r) * lv.wall_vel[w][1] + D::cz(r) * lv.wall_vel[w][2]);
-          v += C;
-          const float dp = 2.0f * f[r] + C;
-          if (wkey != w && wkey >= 0) {
-            // a node touching two different walls: flush the first one directly
-            for (int k = 0; k < 3; ++k) {
-              atomicAdd(&wa.F[3 * wkey + k], (double)wF[k]);
-              atomicAdd((unsigned long long *)&wa.K[3 * wkey + k], (unsigned long long)(long long)wK[k]);
-              wF[k] = 0.f;
-              wK[k] = 0;
+      });
+    } else {
+      sfor<1, Q>([&](auto R) {
+        constexpr int r = decltype(R)::value;
+        constexpr int rb = D::opp(r);
+        const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
+        if (!(solid & (1u << r))) {
+          const unsigned dst = PAR == 0 ? (unsigned)rb * N + n : (unsigned)r * N + nb;
+          Store<S>::st(pop + dst, f[r]);
+        } else {
+          // bounce-back into the slot where the next step reads direction rbar
+          const unsigned dst = PAR == 0 ? (unsigned)r * N + nb : (unsigned)rb * N + n;
+          float v = f[r];
+          if (wall & (1u << r)) {
+            const int w = -2 - lv.owner[nb];
+            // C for the population returning along rbar: 6 alpha_rbar rho c_rbar . v_wall
+            const float C = -(D::m(r) / 6.0f) * rho *
+                            (D::cx(r) * lv.wall_vel[w][0] + D::cy(r) * lv.wall_vel[w][1] + D::cz(r) * lv.wall_vel[w][2]);
+            v += C;
+            const float dp = 2.0f * f[r] + C;
+            if (wkey != w && wkey >= 0) {
+              // a node touching two different walls: flush the first one directly
+              for (int k = 0; k < 3; ++k) {
+                atomicAdd(&wa.F[3 * wkey + k], (double)wF[k]);
+                atomicAdd((unsigned long long *)&wa.K[3 * wkey + k], (unsigned long long)(long long)wK[k]);
+                wF[k] = 0.f;
+                wK[k] = 0;
+              }
             }
+            wkey = w;
+            wF[0] += dp * D::cx(r);
+            wF[1] += dp * D::cy(r);
+            wF[2] += dp * D::cz(r);
+            wK[0] += D::m(r) * D::cx(r);
+            wK[1] += D::m(r) * D::cy(r);
+            wK[2] += D::m(r) * D::cz(r);
           }
-          wkey = w;
-          wF[0] += dp * D::cx(r);
-          wF[1] += dp * D::cy(r);
-          wF[2] += dp * D::cz(r);
-          wK[0] += D::m(r) * D::cx(r);
-          wK[1] += D::m(r) * D::cy(r);
-          wK[2] += D::m(r) * D::cz(r);
+          Store<S>::st(pop + dst, v);
         }
-        Store<S>::st(pop + dst, v);
-      }
-    });
+      });
+    }
     if (nbw & NB_CELL) lv.rho_b[n] = rho;
   }
   const unsigned FULL = 0xffffffffu;
@@ -496,15 +520,25 @@ __global__ void k_links(LatticeView lv, int contact, int pass, int *block_count,
 // ---------------------------------------------------------------------------
 // host-side launchers
 
+template <class S, int PAR, bool FORCE>
+static void launch_lb_tau(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
+                          cudaStream_t st) {
+  if (lv.omega == 1.0f) k_lb_step<S, PAR, FORCE, true><<<grid, block, 0, st>>>(lv, wa, status);
+  else k_lb_step<S, PAR, FORCE, false><<<grid, block, 0, st>>>(lv, wa, status);
+}
+
 template <class S>
 static void launch_lb_typed(const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st) {
   const int bx = lv.nx >= 128 ? 128 : ((lv.nx + 31) / 32) * 32;
   dim3 block(bx, 1, 1);
   dim3 grid((lv.nx + bx - 1) / bx, lv.ny, lv.nz);
-  if (par == 0)
-    k_lb_step<S, 0><<<grid, block, 0, st>>>(lv, wa, status);
-  else
-    k_lb_step<S, 1><<<grid, block, 0, st>>>(lv, wa, status);
+  if (par == 0) {
+    if (lv.has_force) launch_lb_tau<S, 0, true>(lv, grid, block, wa, status, st);
+    else launch_lb_tau<S, 0, false>(lv, grid, block, wa, status, st);
+  } else {
+    if (lv.has_force) launch_lb_tau<S, 1, true>(lv, grid, block, wa, status, st);
+    else launch_lb_tau<S, 1, false>(lv, grid, block, wa, status, st);
+  }
 }
 
 void launch_lb_step(int dtype, const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st) {

@@ -17,9 +17,13 @@
  * Ownership: the library owns all of its device memory (allocated in
  *   bl_lb_init / bl_particles_set, released by bl_destroy).  Caller pointers
  *   are borrowed for the duration of the call only.
- * Streams: every kernel of a context runs on the CUDA stream given to
- *   bl_lb_init (NULL = the legacy default stream).  A context is not
- *   thread-safe; use one context per stream.
+ * Streams: every call of a context is ordered on the CUDA stream given to
+ *   bl_lb_init (NULL = the legacy default stream).  Inside a step the cell
+ *   list and the potentials run on a second stream of the context beside
+ *   the lattice sweep, and repeated steps replay a captured graph on a
+ *   third; both are forked from and joined back to the caller's stream with
+ *   events, so work the caller enqueues later still follows the step.  A
+ *   context is not thread-safe; use one context per stream.
  * Lattice: nodes are numbered n = x + nx (y + ny z), x fastest.  A
  *   non-periodic axis carries solid wall layers at index 0 and N-1; faces
  *   are numbered x-,x+,y-,y+,z-,z+ = wall ids 0..5.  Owner codes: -1 fluid,
@@ -45,7 +49,8 @@ extern "C" {
 #define BL_OK 0
 #define BL_EINVAL (-1)     /* bad argument, size or parameter */
 #define BL_ENOMEM (-2)     /* device allocation failed */
-#define BL_EUNSTABLE (-3)  /* rho <= 0, NaN, or |u| above the Mach guard in a fluid node */
+#define BL_EUNSTABLE (-3)  /* rho <= 0, NaN, |u| above the Mach guard in a fluid node, or a cell
+                              faster than half a node per step */
 #define BL_EOVERFLOW (-4)  /* an internal list exceeded its capacity */
 #define BL_EBARRIER (-5)   /* a bounded device-side wait timed out */
 #define BL_ECUDA (-6)      /* a CUDA runtime call failed */
@@ -104,14 +109,20 @@ int bl_walls_set(bl_ctx *c, const uint8_t *mask);
    (lowest index wins on overlap), deletes the fluid of covered nodes and
    gives no impulses.  A later call with the same n re-discretises against
    the current owner map with the first-arrival rule and fill/drain
-   impulses, exactly as a time step does (Sec. II).  n may be 0. */
+   impulses, exactly as a time step does (Sec. II).  n may be 0.
+   Requirements (BL_EINVAL otherwise): r_cut >= max(R_par, R_perp) + 1, so
+   that the cells covering a node lie in the cell-list bins around it; every
+   periodic length >= 2 max(R_par, R_perp) + 4, so that a cell does not
+   reach its own periodic image. */
 int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, const double *X, const double *q,
                      const double *V, const double *L);
 
 /* Enqueues nsteps coupled time steps on the context stream (no host sync):
    collide + stream + bounce-back + momentum exchange + contact links, cell
    list, pair and wall potentials, leap-frog, re-discretisation with
-   fill/drain.  Returns the sticky status known so far (device errors of
+   fill/drain.  With timing off, pairs of steps are launched as one CUDA
+   graph (captured on first use and again after bl_particles_set or
+   bl_walls_set).  Returns the sticky status known so far (device errors of
    this call surface at the next bl_sync). */
 int bl_step(bl_ctx *c, int nsteps);
 
@@ -177,12 +188,15 @@ int bl_cell_list_get(bl_ctx *c, int32_t nb[3], int32_t *start, int32_t *ids);
 int bl_cell_list_build_static(const double *X, int n, const int32_t dims[3], double r_cut, int32_t nb[3],
                               int32_t *start, int32_t *ids, void *cuda_stream);
 
-/* Kernel timing with CUDA events on the context stream.  While enabled,
-   each kernel group of a step is bracketed by an event pair.  Groups:
-   0 fused collide/stream/bounce-back (the lattice sweep), 1 cell list,
-   2 pair + wall potentials, 3 leap-frog + claims, 4 resolve + fill/drain.
-   bl_timing_read waits, then writes per group the summed milliseconds and
-   the number of timed launches (arrays of ngroups), and clears the sums. */
+/* Kernel timing with CUDA events.  While enabled, steps are enqueued one
+   kernel group at a time (no graph), each group bracketed by an event pair
+   on the stream it runs on.  Groups: 0 fused collide/stream/bounce-back
+   (the lattice sweep), 1 cell list, 2 pair + wall potentials (1 and 2 on
+   the second stream, beside the sweep), 3 link sums + half-step solve +
+   leap-frog + moving-boundary correction, 4 claims + resolve with
+   fill/drain + geometry pass.  bl_timing_read waits, then writes per group
+   the summed milliseconds and the number of timed launches (arrays of
+   ngroups), and clears the sums. */
 int bl_timing_enable(bl_ctx *c, int enable);
 int bl_timing_read(bl_ctx *c, double *ms, int64_t *count, int ngroups);
 

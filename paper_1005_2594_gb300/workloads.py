@@ -136,14 +136,16 @@ def _contact_scale2(Rp, Ra, o, O, d):
     return F.max(axis=1)
 
 
-def pack_cells(params, n, seed, lumen=None, clearance=1.0, max_fail=1500):
+def pack_cells(params, n, seed, lumen=None, clearance=1.0, max_fail=1500, refresh_every=1):
     """Seeded cell states (X n x 3, q n x 4) by random sequential addition.
     ``lumen`` is an optional callable (X, half_widths_xyz, radius) -> bool
     telling whether a cell fits inside the fluid region; walled axes keep the
     cell between the wall layers.  A candidate is accepted when every
     neighbour is disjoint from it after scaling both by ``clearance``.  After
     ``max_fail`` rejections in a row the addition stops and the remaining
-    cells go on a jittered lattice.  Returns X, q and the number placed
+    cells go on a jittered lattice.  The pool of free voxels is listed anew
+    after every ``refresh_every`` placements (and every 64 rejections); large
+    lattices use a coarser interval.  Returns X, q and the number placed
     without overlap."""
     rng = np.random.default_rng(seed)
     L = np.array([params["nx"], params["ny"], params["nz"]], dtype=np.float64)
@@ -178,9 +180,11 @@ def pack_cells(params, n, seed, lumen=None, clearance=1.0, max_fail=1500):
     free = None
     placed = 0
     fails = 0
+    since = 0  # placements since the pool was listed
     while placed < n and fails < max_fail:
         fails += 1
-        if free is None or fails % 64 == 1:
+        if free is None or (fails % 64 == 1 and (fails > 1 or since >= refresh_every)):
+            since = 0
             free = np.flatnonzero(~blocked.reshape(-1))
             if free.size == 0:
                 break
@@ -233,6 +237,7 @@ def pack_cells(params, n, seed, lumen=None, clearance=1.0, max_fail=1500):
             gx, gy, gz = gx[hit] % shape[0], gy[hit] % shape[1], gz[hit] % shape[2]
             blocked[gx, gy, gz] = True
             placed += 1
+            since += 1
             fails = 0
     n_free = placed
     if placed < n:
@@ -289,7 +294,7 @@ def duct(n=256, n_cells=8192, g=1e-6, seed=1003, R=(7.0, 3.0)):
     """n^3 duct: periodic x, walls y and z at rest, body force g along x on
     plasma and cells."""
     p = base_params(n, n, n, periodic=(1, 0, 0), R=R, eps=1.0, g=(g, 0.0, 0.0), body_force_on_cells=1)
-    X, q, _ = pack_cells(p, n_cells, seed)
+    X, q, _ = pack_cells(p, n_cells, seed, refresh_every=64)
     return p, X, q
 
 

@@ -151,6 +151,24 @@ def make_workload(name):
     raise ValueError(name)
 
 
+# DRAM traffic of one lattice sweep (dram__bytes_read.sum + dram__bytes_write.sum,
+# mean of the even and odd launch) from the ncu capture summarised in
+# profiles/lattice_sweep_shear128_dram.md, valid for the kernel source it was
+# taken on (first 16 hex digits of its SHA-256) and that workload only
+SWEEP_TRAFFIC = {"sha": "e3b89d5a8bce7701", "config": "shear128", "store": 0, "bytes": 278206976}
+
+
+def sweep_traffic(config, store):
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_1005_2594_gb300", "csrc", "lb_kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    t = SWEEP_TRAFFIC
+    if sha == t["sha"] and config == t["config"] and store == t["store"]:
+        return t["bytes"]
+    return None
+
+
 def job_value(ws, N, steps, ms_max):
     """whole-job MLUPS: every rank steps its own replica of N sites; the
     slowest rank's time counts"""
@@ -231,7 +249,7 @@ def run_gpu(args, ws, rank, local):
                    "l2": "populations %.0f MB > 129 MB L2, no flush" % (N * 19 * dsize / 1e6)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
-                     "traffic": None, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
+                     "traffic": sweep_traffic(args.config, args.store), "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
                      else "fallback 6.8 TB/s", "kernel": "k_lb_step (fused collide/stream/bounce-back)",
                      "bytes_per_launch": bytes_per, "launch_ms": round(k1_ms / max(k1_n, 1), 5)},
         "kernel_time_share": group_share,

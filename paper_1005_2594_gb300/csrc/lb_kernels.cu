@@ -41,33 +41,53 @@ namespace bl {
 #define BL_LB_MINB 8
 #endif
 
+// warp-level sum of the wall momenta, one atomic per wall and component
+// (all lanes of the warp call it)
+__device__ __forceinline__ void flush_wall_momentum(const WallAcc &wa, int &wkey, float (&wF)[3], int (&wK)[3]) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  unsigned pending = __ballot_sync(FULL, wkey >= 0);
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    const int lk = __shfl_sync(FULL, wkey, leader);
+    const bool mine = wkey == lk;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float vs = warp_sum(mine ? wF[k] : 0.f);
+      const int is = __reduce_add_sync(FULL, mine ? wK[k] : 0);
+      if (lane == leader) {
+        atomicAdd(&wa.F[3 * lk + k], (double)vs);
+        atomicAdd((unsigned long long *)&wa.K[3 * lk + k], (unsigned long long)(long long)is);
+      }
+    }
+    pending &= ~__ballot_sync(FULL, mine);
+    if (mine) wkey = -1;
+  }
+}
+
+// index of the slot from which node n reads direction r in a step of parity
+// PAR (xo, yo, zo: coordinates of its 3 x 3 x 3 neighbourhood, y and z
+// pre-multiplied by their strides)
+template <int PAR>
+__device__ __forceinline__ unsigned src_slot(int r, unsigned N, unsigned n, const unsigned xo[3], const unsigned yo[3],
+                                             const unsigned zo[3]) {
+  using D = D3Q19;
+  if (PAR == 0 || r == 0) return (unsigned)r * N + n;
+  return (unsigned)D::opp(r) * N + xo[1 - D::cx(r)] + yo[1 - D::cy(r)] + zo[1 - D::cz(r)];
+}
+
+// One fluid node of the sweep: moments, collision, streaming with
+// bounce-back and the wall momentum.  load(r, slot) gives the incoming
+// population of direction r (from the slot src_slot names).
 // FORCE: a body force is set (Guo forcing); TAU1: tau = 1, where the
 // relaxation gives the equilibrium itself
-template <class S, int PAR, bool FORCE, bool TAU1>
-__global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, WallAcc wa, int *status) {
+template <class S, int PAR, bool FORCE, bool TAU1, class Load>
+__device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc &wa, int *status, unsigned n,
+                                            const unsigned xo[3], const unsigned yo[3], const unsigned zo[3],
+                                            uint32_t nbw, Load load, int &wkey, float (&wF)[3], int (&wK)[3]) {
   using D = D3Q19;
-  const int nx = lv.nx, ny = lv.ny;
-  const int x0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  const bool valid = x0 < nx;
-  const int x = valid ? x0 : nx - 1;
   const unsigned N = lv.N;
-  const unsigned nxy = (unsigned)nx * (unsigned)ny;
-  const unsigned n = (unsigned)x + (unsigned)nx * (unsigned)y + nxy * (unsigned)z;
-  // coordinates of the 3 x 3 x 3 neighbourhood, periodic wrap on every axis
-  // (a walled axis has wall layers at both ends, never crossed by a link)
-  const unsigned xo[3] = {(unsigned)(x == 0 ? nx - 1 : x - 1), (unsigned)x, (unsigned)(x == nx - 1 ? 0 : x + 1)};
-  const unsigned yo[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1) * nx, (unsigned)y * nx,
-                          (unsigned)(y == ny - 1 ? 0 : y + 1) * nx};
-  const unsigned zo[3] = {(unsigned)(z == 0 ? lv.nz - 1 : z - 1) * nxy, (unsigned)z * nxy,
-                          (unsigned)(z == lv.nz - 1 ? 0 : z + 1) * nxy};
   S *pop = reinterpret_cast<S *>(lv.pop);
-  const uint32_t nbw = valid ? lv.nbm[n] : 0u;
-  // wall momentum of this thread: wall id, variable part, constant-part integers
-  int wkey = -1;
-  float wF[3] = {0.f, 0.f, 0.f};
-  int wK[3] = {0, 0, 0};
-
   if (nbw & NB_FLUID) {
     // neighbour classes from the geometry pass: solid = any non-fluid node;
     // the wall subset is looked up only next to a wall
@@ -92,7 +112,7 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, Wal
       } else {
         src = (unsigned)D::opp(r) * N + xo[1 - D::cx(r)] + yo[1 - D::cy(r)] + zo[1 - D::cz(r)];
       }
-      f[r] = Store<S>::ld(pop + src);
+      f[r] = load(r, src);
     });
     // moments (shifted: rho = rho_bar + sum f~, j = sum f~ c)
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
@@ -195,26 +215,122 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, Wal
     }
     if (nbw & NB_CELL) lv.rho_b[n] = rho;
   }
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  // warp-level sum of the wall momenta, one atomic per wall and component
-  unsigned pending = __ballot_sync(FULL, wkey >= 0);
-  while (pending) {
-    const int leader = __ffs(pending) - 1;
-    const int lk = __shfl_sync(FULL, wkey, leader);
-    const bool mine = wkey == lk;
+}
+
+template <class S, int PAR, bool FORCE, bool TAU1>
+__global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, WallAcc wa, int *status) {
+  const int nx = lv.nx, ny = lv.ny;
+  const int x0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const bool valid = x0 < nx;
+  const int x = valid ? x0 : nx - 1;
+  const unsigned nxy = (unsigned)nx * (unsigned)ny;
+  const unsigned n = (unsigned)x + (unsigned)nx * (unsigned)y + nxy * (unsigned)z;
+  // coordinates of the 3 x 3 x 3 neighbourhood, periodic wrap on every axis
+  // (a walled axis has wall layers at both ends, never crossed by a link)
+  const unsigned xo[3] = {(unsigned)(x == 0 ? nx - 1 : x - 1), (unsigned)x, (unsigned)(x == nx - 1 ? 0 : x + 1)};
+  const unsigned yo[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1) * nx, (unsigned)y * nx,
+                          (unsigned)(y == ny - 1 ? 0 : y + 1) * nx};
+  const unsigned zo[3] = {(unsigned)(z == 0 ? lv.nz - 1 : z - 1) * nxy, (unsigned)z * nxy,
+                          (unsigned)(z == lv.nz - 1 ? 0 : z + 1) * nxy};
+  const S *pop = reinterpret_cast<const S *>(lv.pop);
+  const uint32_t nbw = valid ? lv.nbm[n] : 0u;
+  // wall momentum of this thread: wall id, variable part, constant-part integers
+  int wkey = -1;
+  float wF[3] = {0.f, 0.f, 0.f};
+  int wK[3] = {0, 0, 0};
+  if (nbw & NB_FLUID)
+    node_update<S, PAR, FORCE, TAU1>(lv, wa, status, n, xo, yo, zo, nbw,
+                                     [&](int, unsigned slot) { return Store<S>::ld(pop + slot); }, wkey, wF, wK);
+  flush_wall_momentum(wa, wkey, wF, wK);
+}
+
+// The FP32 sweep as a software pipeline along z: a block of 128 threads takes
+// a row segment and PIPE_ZC consecutive z planes; while a node is collided,
+// the populations of the next PIPE_ST - 1 nodes above it are on their way
+// into shared memory (asynchronous 4-byte copies, one group per node).  The
+// neighbour word of a node is loaded just before its copies are issued;
+// solid nodes copy nothing.
+#ifndef BL_PIPE_ZC
+#define BL_PIPE_ZC 4
+#endif
+#ifndef BL_PIPE_ST
+#define BL_PIPE_ST 2
+#endif
+constexpr int PIPE_ZC = BL_PIPE_ZC, PIPE_ST = BL_PIPE_ST;
+
+__device__ __forceinline__ void cp_async4(void *dst_smem, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int G>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(G) : "memory");
+}
+
+template <int PAR, bool FORCE, bool TAU1>
+__global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv, WallAcc wa, int *status) {
+  __shared__ float stage[PIPE_ST][Q][128];
+  const int nx = lv.nx, ny = lv.ny, nz = lv.nz;
+  const int tx = threadIdx.x;
+  const int x0 = blockIdx.x * blockDim.x + tx;
+  const int y = blockIdx.y;
+  const int zb = blockIdx.z * PIPE_ZC, ze = min(zb + PIPE_ZC, nz);
+  const bool valid = x0 < nx;
+  const int x = valid ? x0 : nx - 1;
+  const unsigned N = lv.N;
+  const unsigned nxy = (unsigned)nx * (unsigned)ny;
+  const unsigned xo[3] = {(unsigned)(x == 0 ? nx - 1 : x - 1), (unsigned)x, (unsigned)(x == nx - 1 ? 0 : x + 1)};
+  const unsigned yo[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1) * nx, (unsigned)y * nx,
+                          (unsigned)(y == ny - 1 ? 0 : y + 1) * nx};
+  const unsigned rowb = (unsigned)x + (unsigned)nx * (unsigned)y;
+  const float *pop = reinterpret_cast<const float *>(lv.pop);
+  auto zoff = [&](int z, unsigned zo[3]) {
+    zo[0] = (unsigned)(z == 0 ? nz - 1 : z - 1) * nxy;
+    zo[1] = (unsigned)z * nxy;
+    zo[2] = (unsigned)(z == nz - 1 ? 0 : z + 1) * nxy;
+  };
+  // neighbour word of node z, and its copies into stage buffer b when fluid
+  auto issue = [&](int z, int b) -> uint32_t {
+    if (!valid || z >= ze) return 0u;
+    unsigned zo[3];
+    zoff(z, zo);
+    const unsigned n = rowb + zo[1];
+    const uint32_t w = lv.nbm[n];
+    if (w & NB_FLUID)
+      sfor<0, Q>([&](auto R) {
+        constexpr int r = decltype(R)::value;
+        cp_async4(&stage[b][r][tx], pop + src_slot<PAR>(r, N, n, xo, yo, zo));
+      });
+    return w;
+  };
+  int wkey = -1;
+  float wF[3] = {0.f, 0.f, 0.f};
+  int wK[3] = {0, 0, 0};
+  uint32_t w[PIPE_ST];  // neighbour words of the nodes in flight, oldest first
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float vs = warp_sum(mine ? wF[k] : 0.f);
-      const int is = __reduce_add_sync(FULL, mine ? wK[k] : 0);
-      if (lane == leader) {
-        atomicAdd(&wa.F[3 * lk + k], (double)vs);
-        atomicAdd((unsigned long long *)&wa.K[3 * lk + k], (unsigned long long)(long long)is);
-      }
-    }
-    pending &= ~__ballot_sync(FULL, mine);
-    if (mine) wkey = -1;
+  for (int k = 0; k < PIPE_ST - 1; ++k) {
+    w[k] = issue(zb + k, k);
+    cp_async_commit();
   }
+  for (int z = zb; z < ze; ++z) {
+    const int i = z - zb;
+    w[PIPE_ST - 1] = issue(z + PIPE_ST - 1, (i + PIPE_ST - 1) % PIPE_ST);
+    cp_async_commit();
+    cp_async_wait<PIPE_ST - 1>();  // the copies of node z have landed
+    const int b = i % PIPE_ST;
+    if (w[0] & NB_FLUID) {
+      unsigned zo[3];
+      zoff(z, zo);
+      node_update<float, PAR, FORCE, TAU1>(lv, wa, status, rowb + zo[1], xo, yo, zo, w[0],
+                                           [&](int r, unsigned) { return stage[b][r][tx]; }, wkey, wF, wK);
+    }
+#pragma unroll
+    for (int k = 0; k < PIPE_ST - 1; ++k) w[k] = w[k + 1];
+  }
+  cp_async_wait<0>();
+  flush_wall_momentum(wa, wkey, wF, wK);
 }
 
 // ---------------------------------------------------------------------------
@@ -523,8 +639,15 @@ __global__ void k_links(LatticeView lv, int contact, int pass, int *block_count,
 template <class S, int PAR, bool FORCE>
 static void launch_lb_tau(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
                           cudaStream_t st) {
-  if (lv.omega == 1.0f) k_lb_step<S, PAR, FORCE, true><<<grid, block, 0, st>>>(lv, wa, status);
-  else k_lb_step<S, PAR, FORCE, false><<<grid, block, 0, st>>>(lv, wa, status);
+  if constexpr (std::is_same<S, float>::value) {
+    // FP32: the pipelined sweep, PIPE_ZC planes per block
+    const dim3 gp(grid.x, grid.y, (grid.z + PIPE_ZC - 1) / PIPE_ZC);
+    if (lv.omega == 1.0f) k_lb_step_pipe<PAR, FORCE, true><<<gp, block, 0, st>>>(lv, wa, status);
+    else k_lb_step_pipe<PAR, FORCE, false><<<gp, block, 0, st>>>(lv, wa, status);
+  } else {
+    if (lv.omega == 1.0f) k_lb_step<S, PAR, FORCE, true><<<grid, block, 0, st>>>(lv, wa, status);
+    else k_lb_step<S, PAR, FORCE, false><<<grid, block, 0, st>>>(lv, wa, status);
+  }
 }
 
 template <class S>

@@ -188,6 +188,37 @@ int bl_cell_list_get(bl_ctx *c, int32_t nb[3], int32_t *start, int32_t *ids);
 int bl_cell_list_build_static(const double *X, int n, const int32_t dims[3], double r_cut, int32_t nb[3],
                               int32_t *start, int32_t *ids, void *cuda_stream);
 
+/* Sweep variants of the lattice sweep (the same arithmetic, other thread
+   mappings): 0 one node per thread; 1, 2 (FP32 storage only) a software
+   pipeline that walks 4 or 8 z planes per thread block and copies the next
+   node's populations into shared memory while the current one is collided.
+   FP32 contexts start with 1.  bl_sweep_variant sets one (BL_EINVAL for an
+   unknown variant or a pipelined variant with 16-bit storage).
+   bl_autotune times every variant the storage type allows over trial_steps
+   steps (>= 2; the context advances by those steps, so call it before the
+   steps that count), keeps the fastest and writes its number to *choice
+   (may be NULL).  The paper has no counterpart: these are interfaces of
+   this library. */
+int bl_sweep_variant(bl_ctx *c, int variant);
+int bl_autotune(bl_ctx *c, int trial_steps, int *choice);
+
+/* Ensembles: n independent contexts (different lattices, cells, parameters;
+   one device) advanced together.  bl_ensemble_step(e, k) advances every
+   member by k steps; pairs of steps of all members run as one CUDA graph
+   whose branches are the members' steps, so that small lattices fill the
+   GPU together; it is ordered after the work already enqueued on each
+   member's stream and on cuda_stream, and each member's later work follows
+   it.  The ensemble borrows the contexts: they must outlive it, and a
+   member with timing enabled makes the step return BL_ESTATE.  Errors of a
+   member are reported by bl_ensemble_step / bl_ensemble_sync (the first
+   one).  The paper has no counterpart (a batching interface of this
+   library). */
+typedef struct bl_ens bl_ens;
+int bl_ensemble_create(bl_ens **out, bl_ctx *const *ctxs, int n, void *cuda_stream);
+int bl_ensemble_step(bl_ens *e, int nsteps);
+int bl_ensemble_sync(bl_ens *e);
+void bl_ensemble_destroy(bl_ens *e);
+
 /* Kernel timing with CUDA events.  While enabled, steps are enqueued one
    kernel group at a time (no graph), each group bracketed by an event pair
    on the stream it runs on.  Groups: 0 fused collide/stream/bounce-back

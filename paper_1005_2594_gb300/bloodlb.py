@@ -34,7 +34,8 @@ ABI_FUNCTIONS = (
     "bl_lb_init", "bl_walls_set", "bl_particles_set", "bl_step", "bl_fields_get", "bl_forces_get",
     "bl_force_parts_get", "bl_wall_momentum_get", "bl_populations_get", "bl_populations_set",
     "bl_boundary_links_get", "bl_contact_links_get", "bl_cell_list_get", "bl_cell_list_build_static",
-    "bl_timing_enable",
+    "bl_sweep_variant", "bl_autotune", "bl_ensemble_create", "bl_ensemble_step", "bl_ensemble_sync",
+    "bl_ensemble_destroy", "bl_timing_enable",
     "bl_timing_read", "bl_launch_count", "bl_sync", "bl_last_error", "bl_destroy",
 )
 
@@ -96,6 +97,12 @@ def lib():
         "bl_contact_links_get": (ctypes.c_int, [vp, I, i64, ctypes.POINTER(i64)]),
         "bl_cell_list_get": (ctypes.c_int, [vp, I, I, I]),
         "bl_cell_list_build_static": (ctypes.c_int, [vp, ctypes.c_int, I, ctypes.c_double, I, vp, vp, vp]),
+        "bl_sweep_variant": (ctypes.c_int, [vp, ctypes.c_int]),
+        "bl_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "bl_ensemble_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, vp]),
+        "bl_ensemble_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "bl_ensemble_sync": (ctypes.c_int, [vp]),
+        "bl_ensemble_destroy": (None, [vp]),
         "bl_timing_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "bl_timing_read": (ctypes.c_int, [vp, D, ctypes.POINTER(i64), ctypes.c_int]),
         "bl_launch_count": (i64, [vp]),
@@ -187,6 +194,46 @@ def bl_step(ctx, nsteps=1):
 
 def bl_sync(ctx):
     return _check(ctx, lib().bl_sync(ctx))
+
+
+def bl_sweep_variant(ctx, variant):
+    return _check(ctx, lib().bl_sweep_variant(ctx, int(variant)))
+
+
+def bl_autotune(ctx, trial_steps=20):
+    """Times the sweep variants on this context (it advances by the trial
+    steps), keeps the fastest and returns its number."""
+    choice = ctypes.c_int(-1)
+    _check(ctx, lib().bl_autotune(ctx, int(trial_steps), ctypes.byref(choice)))
+    return choice.value
+
+
+def bl_ensemble_create(ctxs, stream=None):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    ens = ctypes.c_void_p()
+    rc = lib().bl_ensemble_create(ctypes.byref(ens), arr, len(ctxs), ctypes.c_void_p(stream or 0))
+    if rc != BL_OK:
+        raise BloodLBError(rc, "bl_ensemble_create")
+    return ens
+
+
+def bl_ensemble_step(ens, nsteps=1):
+    rc = lib().bl_ensemble_step(ens, int(nsteps))
+    if rc != BL_OK:
+        raise BloodLBError(rc, "bl_ensemble_step")
+    return rc
+
+
+def bl_ensemble_sync(ens):
+    rc = lib().bl_ensemble_sync(ens)
+    if rc != BL_OK:
+        raise BloodLBError(rc, "bl_ensemble_sync")
+    return rc
+
+
+def bl_ensemble_destroy(ens):
+    if ens:
+        lib().bl_ensemble_destroy(ens)
 
 
 def bl_fields_get(ctx, N, rho=None, u=None, owner=None, on_device=False):
@@ -364,3 +411,35 @@ class Simulation:
 
     def wall_momentum(self):
         return bl_wall_momentum_get(self.ctx)
+
+    def autotune(self, trial_steps=20):
+        return bl_autotune(self.ctx, trial_steps)
+
+    def sweep_variant(self, variant):
+        bl_sweep_variant(self.ctx, variant)
+
+
+class Ensemble:
+    """Independent simulations advanced together (bl_ensemble_*); the
+    members must outlive the ensemble."""
+
+    def __init__(self, sims, stream=None):
+        self.sims = list(sims)
+        self.ens = bl_ensemble_create([s.ctx for s in self.sims], stream)
+
+    def step(self, n=1):
+        bl_ensemble_step(self.ens, n)
+
+    def sync(self):
+        bl_ensemble_sync(self.ens)
+
+    def close(self):
+        if getattr(self, "ens", None):
+            bl_ensemble_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

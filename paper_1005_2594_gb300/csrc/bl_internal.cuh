@@ -72,6 +72,7 @@ struct LatticeView {
   float rho0;
   float g[3];
   int has_force;
+  int sweep;  // sweep variant (0 one node per thread, 1 / 2 FP32 pipeline over 4 / 8 planes)
   void *pop;       // 19 x N storage elements, slot r of node n at r * N + n
   int32_t *owner;  // N
   float *rho_b;    // N: density of each fluid node with a cell link, written by the sweep

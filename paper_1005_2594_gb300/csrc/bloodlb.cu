@@ -43,6 +43,7 @@ struct bl_ctx {
   int g_parity;
   const void *g_kin;
   int64_t g_launches;
+  int epoch;  // counts graph invalidations (cell arrays moved, walls or sweep variant changed)
   int dtype;
   int parity;  // layout of the current populations (next step's parity)
   LatticeView lv;
@@ -209,6 +210,7 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
   lv.omega = (float)(1.0 / p->tau);
   lv.rho0 = (float)p->rho0;
   lv.has_force = 0;
+  lv.sweep = p->store_dtype == BL_STORE_F32 ? 1 : 0;  // FP32: the pipelined sweep over 4 planes
   for (int k = 0; k < 3; ++k) {
     lv.g[k] = (float)p->g[k];
     if (p->g[k] != 0.0) lv.has_force = 1;
@@ -497,6 +499,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
 static void drop_graph(bl_ctx *c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   c->gexec = nullptr;
+  c->epoch++;
 }
 
 // the graph of two steps from the current parity and cell state
@@ -739,6 +742,221 @@ extern "C" int bl_timing_read(bl_ctx *c, double *ms, int64_t *count, int ngroups
 extern "C" int64_t bl_launch_count(const bl_ctx *c) { return c ? c->launches : 0; }
 
 extern "C" const char *bl_last_error(const bl_ctx *c) { return c ? c->err : "null context"; }
+
+// ---------------------------------------------------------------------------
+// autotuning of the sweep variant
+
+extern "C" int bl_autotune(bl_ctx *c, int trial_steps, int *choice) {
+  if (!c || trial_steps < 2) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (c->timing) return fail(c, BL_ESTATE, "bl_autotune with timing enabled");
+  const int nvar = c->dtype == BL_STORE_F32 ? 3 : 1;
+  int best = 0;
+  float best_ms = 0.f;
+  cudaEvent_t a, b;
+  CU(cudaEventCreate(&a));
+  CU(cudaEventCreate(&b));
+  int rc = BL_OK;
+  for (int v = 0; v < nvar && rc == BL_OK; ++v) {
+    drop_graph(c);  // the graph holds the lattice view, variant included
+    c->lv.sweep = v;
+    if ((rc = bl_step(c, 2)) != BL_OK) break;  // capture + warm-up
+    cudaEventRecord(a, c->stream);
+    if ((rc = bl_step(c, trial_steps & ~1)) != BL_OK) break;
+    cudaEventRecord(b, c->stream);
+    if (cudaEventSynchronize(b) != cudaSuccess) {
+      rc = fail(c, BL_ECUDA, "autotune timing");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (v == 0 || ms < best_ms) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  drop_graph(c);
+  c->lv.sweep = best;
+  if (choice) *choice = best;
+  if (rc != BL_OK) return rc;
+  return read_status(c);
+}
+
+extern "C" int bl_sweep_variant(bl_ctx *c, int variant) {
+  if (!c || variant < 0 || variant > 2) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (variant != 0 && c->dtype != BL_STORE_F32) return BL_EINVAL;
+  drop_graph(c);
+  c->lv.sweep = variant;
+  return BL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ensembles: independent contexts advanced together by one graph whose
+// branches are the members' steps
+
+struct bl_ens {
+  std::vector<bl_ctx *> m;
+  cudaStream_t stream;  // the caller's stream of the ensemble
+  cudaStream_t cap;     // internal stream the graph is captured and replayed on
+  cudaEvent_t ev_fork, ev_join;
+  std::vector<cudaEvent_t> ev_m;
+  cudaGraphExec_t gexec;
+  std::vector<int> g_parity, g_epoch;
+  std::vector<const void *> g_kin;
+  std::vector<int64_t> g_launches;
+  int sticky;
+};
+
+static void ens_drop(bl_ens *e) {
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
+  e->gexec = nullptr;
+}
+
+static bool ens_valid(const bl_ens *e) {
+  if (!e->gexec) return false;
+  for (size_t i = 0; i < e->m.size(); ++i) {
+    const bl_ctx *c = e->m[i];
+    if (c->parity != e->g_parity[i] || (const void *)c->pv.kin != e->g_kin[i] || c->epoch != e->g_epoch[i])
+      return false;
+  }
+  return true;
+}
+
+static int ens_capture(bl_ens *e) {
+  ens_drop(e);
+  const size_t n = e->m.size();
+  std::vector<int64_t> l0(n);
+  for (size_t i = 0; i < n; ++i) {
+    bl_ctx *c = e->m[i];
+    e->g_parity[i] = c->parity;
+    e->g_kin[i] = c->pv.kin;
+    e->g_epoch[i] = c->epoch;
+    l0[i] = c->launches;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BL_ECUDA;
+  int rc = BL_OK;
+  cudaEventRecord(e->ev_fork, e->cap);
+  for (size_t i = 0; i < n && rc == BL_OK; ++i) {
+    bl_ctx *c = e->m[i];
+    cudaStreamWaitEvent(c->gstream, e->ev_fork, 0);
+    rc = enqueue_step(c, c->gstream);
+    if (rc == BL_OK) rc = enqueue_step(c, c->gstream);
+    cudaEventRecord(e->ev_m[i], c->gstream);
+    cudaStreamWaitEvent(e->cap, e->ev_m[i], 0);
+  }
+  const cudaError_t err = cudaStreamEndCapture(e->cap, &g);
+  for (size_t i = 0; i < n; ++i) {  // capturing ran nothing: restore the members' step state
+    bl_ctx *c = e->m[i];
+    c->parity = e->g_parity[i];
+    if ((const void *)c->pv.kin != e->g_kin[i]) std::swap(c->pv.kin, c->pv.kin_next);
+    e->g_launches[i] = c->launches - l0[i];
+    c->launches = l0[i];
+  }
+  if (rc != BL_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (err != cudaSuccess) return BL_ECUDA;
+  const cudaError_t ie = cudaGraphInstantiate(&e->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    e->gexec = nullptr;
+    return BL_ECUDA;
+  }
+  return BL_OK;
+}
+
+extern "C" int bl_ensemble_create(bl_ens **out, bl_ctx *const *ctxs, int n, void *cuda_stream) {
+  if (!out) return BL_EINVAL;
+  *out = nullptr;
+  if (!ctxs || n < 1) return BL_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return BL_EINVAL;
+    if (ctxs[i]->sticky) return ctxs[i]->sticky;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return BL_EINVAL;
+  }
+  bl_ens *e = new bl_ens();
+  e->m.assign(ctxs, ctxs + n);
+  e->stream = (cudaStream_t)cuda_stream;
+  e->g_parity.assign(n, 0);
+  e->g_epoch.assign(n, 0);
+  e->g_kin.assign(n, nullptr);
+  e->g_launches.assign(n, 0);
+  e->ev_m.assign(n, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < n && ok; ++i) ok = cudaEventCreateWithFlags(&e->ev_m[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    bl_ensemble_destroy(e);
+    return BL_ECUDA;
+  }
+  *out = e;
+  return BL_OK;
+}
+
+extern "C" int bl_ensemble_step(bl_ens *e, int nsteps) {
+  if (!e || nsteps < 0) return BL_EINVAL;
+  if (e->sticky) return e->sticky;
+  for (bl_ctx *c : e->m) {
+    if (c->sticky) return e->sticky = c->sticky;
+    if (c->timing) return e->sticky = BL_ESTATE;
+  }
+  int s = 0;
+  if (nsteps >= 2) {
+    if (!ens_valid(e)) {
+      const int rc = ens_capture(e);
+      if (rc != BL_OK) return e->sticky = rc;
+    }
+    // every member's prior work, then the graph, then every member's stream
+    for (size_t i = 0; i < e->m.size(); ++i) {
+      cudaEventRecord(e->ev_m[i], e->m[i]->stream);
+      cudaStreamWaitEvent(e->cap, e->ev_m[i], 0);
+    }
+    cudaEventRecord(e->ev_fork, e->stream);
+    cudaStreamWaitEvent(e->cap, e->ev_fork, 0);
+    for (; s + 2 <= nsteps; s += 2) {
+      if (cudaGraphLaunch(e->gexec, e->cap) != cudaSuccess) return e->sticky = BL_ECUDA;
+      for (size_t i = 0; i < e->m.size(); ++i) e->m[i]->launches += e->g_launches[i];
+    }
+    cudaEventRecord(e->ev_join, e->cap);
+    cudaStreamWaitEvent(e->stream, e->ev_join, 0);
+    for (bl_ctx *c : e->m) cudaStreamWaitEvent(c->stream, e->ev_join, 0);
+  }
+  for (; s < nsteps; ++s)
+    for (bl_ctx *c : e->m) {
+      const int rc = bl_step(c, 1);
+      if (rc != BL_OK) return e->sticky = rc;
+    }
+  return BL_OK;
+}
+
+extern "C" int bl_ensemble_sync(bl_ens *e) {
+  if (!e) return BL_EINVAL;
+  int rc = e->sticky;
+  for (bl_ctx *c : e->m) {
+    const int r = bl_sync(c);
+    if (rc == BL_OK) rc = r;
+  }
+  return rc;
+}
+
+extern "C" void bl_ensemble_destroy(bl_ens *e) {
+  if (!e) return;
+  if (e->cap) cudaStreamSynchronize(e->cap);
+  ens_drop(e);
+  if (e->cap) cudaStreamDestroy(e->cap);
+  if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+  if (e->ev_join) cudaEventDestroy(e->ev_join);
+  for (cudaEvent_t ev : e->ev_m)
+    if (ev) cudaEventDestroy(ev);
+  delete e;
+}
 
 extern "C" void bl_destroy(bl_ctx *c) {
   if (!c) return;

@@ -246,18 +246,15 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, Wal
 }
 
 // The FP32 sweep as a software pipeline along z: a block of 128 threads takes
-// a row segment and PIPE_ZC consecutive z planes; while a node is collided,
+// a row segment and ZC consecutive z planes; while a node is collided,
 // the populations of the next PIPE_ST - 1 nodes above it are on their way
 // into shared memory (asynchronous 4-byte copies, one group per node).  The
 // neighbour word of a node is loaded just before its copies are issued;
 // solid nodes copy nothing.
-#ifndef BL_PIPE_ZC
-#define BL_PIPE_ZC 4
-#endif
 #ifndef BL_PIPE_ST
 #define BL_PIPE_ST 2
 #endif
-constexpr int PIPE_ZC = BL_PIPE_ZC, PIPE_ST = BL_PIPE_ST;
+constexpr int PIPE_ST = BL_PIPE_ST;
 
 __device__ __forceinline__ void cp_async4(void *dst_smem, const void *src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
@@ -269,14 +266,14 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(G) : "memory");
 }
 
-template <int PAR, bool FORCE, bool TAU1>
+template <int PAR, bool FORCE, bool TAU1, int ZC>
 __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv, WallAcc wa, int *status) {
   __shared__ float stage[PIPE_ST][Q][128];
   const int nx = lv.nx, ny = lv.ny, nz = lv.nz;
   const int tx = threadIdx.x;
   const int x0 = blockIdx.x * blockDim.x + tx;
   const int y = blockIdx.y;
-  const int zb = blockIdx.z * PIPE_ZC, ze = min(zb + PIPE_ZC, nz);
+  const int zb = blockIdx.z * ZC, ze = min(zb + ZC, nz);
   const bool valid = x0 < nx;
   const int x = valid ? x0 : nx - 1;
   const unsigned N = lv.N;
@@ -636,18 +633,30 @@ __global__ void k_links(LatticeView lv, int contact, int pass, int *block_count,
 // ---------------------------------------------------------------------------
 // host-side launchers
 
+template <int PAR, bool FORCE, bool TAU1, int ZC>
+static void launch_pipe(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
+                        cudaStream_t st) {
+  const dim3 gp(grid.x, grid.y, (grid.z + ZC - 1) / ZC);
+  k_lb_step_pipe<PAR, FORCE, TAU1, ZC><<<gp, block, 0, st>>>(lv, wa, status);
+}
+
+// sweep variants (LatticeView::sweep): 0 one node per thread; 1, 2 the FP32
+// pipeline over 4 or 8 planes (BF16 / FP16 storage always take variant 0)
+template <class S, int PAR, bool FORCE, bool TAU1>
+static void launch_lb_variant(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
+                              cudaStream_t st) {
+  if constexpr (std::is_same<S, float>::value) {
+    if (lv.sweep == 1) return launch_pipe<PAR, FORCE, TAU1, 4>(lv, grid, block, wa, status, st);
+    if (lv.sweep == 2) return launch_pipe<PAR, FORCE, TAU1, 8>(lv, grid, block, wa, status, st);
+  }
+  k_lb_step<S, PAR, FORCE, TAU1><<<grid, block, 0, st>>>(lv, wa, status);
+}
+
 template <class S, int PAR, bool FORCE>
 static void launch_lb_tau(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
                           cudaStream_t st) {
-  if constexpr (std::is_same<S, float>::value) {
-    // FP32: the pipelined sweep, PIPE_ZC planes per block
-    const dim3 gp(grid.x, grid.y, (grid.z + PIPE_ZC - 1) / PIPE_ZC);
-    if (lv.omega == 1.0f) k_lb_step_pipe<PAR, FORCE, true><<<gp, block, 0, st>>>(lv, wa, status);
-    else k_lb_step_pipe<PAR, FORCE, false><<<gp, block, 0, st>>>(lv, wa, status);
-  } else {
-    if (lv.omega == 1.0f) k_lb_step<S, PAR, FORCE, true><<<grid, block, 0, st>>>(lv, wa, status);
-    else k_lb_step<S, PAR, FORCE, false><<<grid, block, 0, st>>>(lv, wa, status);
-  }
+  if (lv.omega == 1.0f) launch_lb_variant<S, PAR, FORCE, true>(lv, grid, block, wa, status, st);
+  else launch_lb_variant<S, PAR, FORCE, false>(lv, grid, block, wa, status, st);
 }
 
 template <class S>

@@ -298,6 +298,26 @@ def duct(n=256, n_cells=8192, g=1e-6, seed=1003, R=(7.0, 3.0)):
     return p, X, q
 
 
+def ensemble(n_boxes=64, seed=1004, R=(7.0, 3.0), sizes=(48, 64, 80, 96), hct=(0.10, 0.20, 0.30, 0.40, 0.45),
+             U=(0.005, 0.05), max_fail=300):
+    """Uneven shear cells for rheology sweeps: cube edges drawn from
+    ``sizes``, volume fractions from ``hct``, wall speeds uniform in ``U``
+    (walls at z moving -/+U along x); (7,7,3) cells.  Returns a list of
+    (params, X, q, description)."""
+    rng = np.random.default_rng(seed)
+    vol = 4.0 / 3.0 * math.pi * R[0] * R[0] * R[1]
+    out = []
+    for b in range(n_boxes):
+        n = int(rng.choice(sizes))
+        phi = float(rng.choice(hct))
+        u = float(rng.uniform(U[0], U[1]))
+        p = base_params(n, n, n, periodic=(1, 1, 0), R=R, eps=1.0, wall_vel={4: (-u, 0.0, 0.0), 5: (u, 0.0, 0.0)})
+        m = max(1, int(round(phi * n ** 3 / vol)))
+        X, q, _ = pack_cells(p, m, seed * 1000 + b, refresh_every=16, max_fail=max_fail)
+        out.append((p, X, q, "%d^3, %d cells (%.0f %%), U = %.4f" % (n, m, 100 * phi, u)))
+    return out
+
+
 def tube_mask(params, radius, axis=0):
     """uint8 wall mask of a tube of the given radius about the axis through
     the box centre (mask value 7 -> wall id 6, at rest)."""

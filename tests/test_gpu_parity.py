@@ -360,3 +360,61 @@ def test_graph_replay_matches_single_steps():
     ra, ua, _ = a.fields()
     rb, ub, _ = b.fields()
     assert rel(ub, ua) < 1e-6 and rel(rb - 1.0, ra - 1.0) < 1e-5
+
+
+def test_sweep_variants_agree():
+    """The three thread mappings of the FP32 sweep compute the same step."""
+    oracle, bl, workloads = _mods()
+    p, X, q, V, L = _coupled(0.0, seed=1021)
+    sims = []
+    for v in (0, 1, 2):
+        s = bl.Simulation(p)
+        s.sweep_variant(v)
+        s.set_particles(X, q, V, L)
+        s.step(15)
+        s.sync()
+        sims.append(s)
+    ref = sims[1]
+    for s in (sims[0], sims[2]):
+        np.testing.assert_array_equal(s.owner(), ref.owner())
+        assert rel(s.particles()["X"], ref.particles()["X"]) < 1e-6
+        assert rel(s.fields()[1], ref.fields()[1]) < 1e-6
+    with pytest.raises(bl.BloodLBError):
+        bl.Simulation(p, store_dtype=1).sweep_variant(1)  # the pipeline is FP32 only
+
+
+def test_ensemble_matches_members_stepped_alone():
+    """An ensemble of uneven lattices advanced by one graph equals its
+    members advanced one by one."""
+    oracle, bl, workloads = _mods()
+    boxes = workloads.ensemble(n_boxes=3, seed=77, R=(3.5, 1.5), sizes=(24, 32), hct=(0.1, 0.2))
+    alone, grouped = [], []
+    for p, X, q, _ in boxes:
+        for group in (alone, grouped):
+            s = bl.Simulation(p)
+            s.set_particles(X, q)
+            group.append(s)
+    for s in alone:
+        for _ in range(9):
+            s.step(1)
+        s.sync()
+    ens = bl.Ensemble(grouped)
+    ens.step(8)
+    ens.step(1)
+    ens.sync()
+    for a, b in zip(alone, grouped):
+        np.testing.assert_array_equal(a.owner(), b.owner())
+        assert rel(b.particles()["X"], a.particles()["X"]) < 1e-6
+        assert rel(b.fields()[1], a.fields()[1]) < 1e-6
+    ens.close()
+
+
+def test_autotune_keeps_a_valid_variant():
+    oracle, bl, workloads = _mods()
+    p, X, q, V, L = _coupled(0.0)
+    s = bl.Simulation(p)
+    s.set_particles(X, q, V, L)
+    choice = s.autotune(6)
+    assert choice in (0, 1, 2)
+    s.step(4)
+    s.sync()

@@ -219,6 +219,38 @@ int bl_ensemble_step(bl_ens *e, int nsteps);
 int bl_ensemble_sync(bl_ens *e);
 void bl_ensemble_destroy(bl_ens *e);
 
+/* Learned near-contact correction (the paper motivates it and leaves it open:
+   two cells closer than the lattice resolves have no fluid node between them
+   and no lubrication force, Sec. II).  A network 14 -> 64 -> 64 -> 6 with tanh
+   hidden layers, BF16 weights and activations on the tensor cores, FP32
+   accumulation and FP32 master parameters.
+   Features of the ordered pair (i, j), in the body frame of i: R_i^T r
+   (r = X_j - X_i, minimum image), q_i^* q_j with w >= 0, the gap
+   |r| - sigma_R (the contact distance of Eq. sigma built from R_par, R_perp),
+   R_i^T (V_j - V_i), R_i^T (W_j - W_i).  Outputs: the force and torque
+   correction on i in the body frame of i.
+   Parameters (host arrays of float): theta = W1 (64 x 14), b1 (64),
+   W2 (64 x 64), b2 (64), W3 (6 x 64), b3 (6), row-major, 5510 values;
+   norm = input means (14), input scales (14), output means (6), output
+   scales (6): the network sees (x - mean) / scale and its output is
+   y~ scale + mean.  Scales must be > 0.
+   bl_mlp_forward: x (B x 14) and y (B x 6) are device arrays (FP32) on the
+   model's stream.  bl_mlp_grad: loss (mean over the B samples of the squared
+   error of the scaled outputs summed over the six) and its gradient with
+   respect to theta for targets y (device); loss and grad (5510) are host
+   pointers, may be NULL (then the call does not wait); the gradient stays on
+   the device for bl_mlp_adam, which takes one Adam step with it.
+   bl_mlp_params_set resets the Adam moments. */
+typedef struct bl_mlp bl_mlp;
+int bl_mlp_create(bl_mlp **out, void *cuda_stream);
+int bl_mlp_params_set(bl_mlp *m, const float *theta, const float *norm);
+int bl_mlp_params_get(bl_mlp *m, float *theta, float *norm);
+int bl_mlp_forward(bl_mlp *m, const float *x, int B, float *y);
+int bl_mlp_grad(bl_mlp *m, const float *x, const float *y, int B, float *loss, float *grad);
+int bl_mlp_adam(bl_mlp *m, float lr, float beta1, float beta2, float eps);
+int bl_mlp_sync(bl_mlp *m);
+void bl_mlp_destroy(bl_mlp *m);
+
 /* Kernel timing with CUDA events.  While enabled, steps are enqueued one
    kernel group at a time (no graph), each group bracketed by an event pair
    on the stream it runs on.  Groups: 0 fused collide/stream/bounce-back

@@ -35,7 +35,8 @@ ABI_FUNCTIONS = (
     "bl_force_parts_get", "bl_wall_momentum_get", "bl_populations_get", "bl_populations_set",
     "bl_boundary_links_get", "bl_contact_links_get", "bl_cell_list_get", "bl_cell_list_build_static",
     "bl_sweep_variant", "bl_autotune", "bl_ensemble_create", "bl_ensemble_step", "bl_ensemble_sync",
-    "bl_ensemble_destroy", "bl_timing_enable",
+    "bl_ensemble_destroy", "bl_mlp_create", "bl_mlp_params_set", "bl_mlp_params_get", "bl_mlp_forward",
+    "bl_mlp_grad", "bl_mlp_adam", "bl_mlp_sync", "bl_mlp_destroy", "bl_timing_enable",
     "bl_timing_read", "bl_launch_count", "bl_sync", "bl_last_error", "bl_destroy",
 )
 
@@ -81,6 +82,7 @@ def lib():
         raise RuntimeError("CUDA library %s is not built; run __graft_entry__.build()" % LIB_PATH)
     L = ctypes.CDLL(LIB_PATH)
     vp, D, I = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    F = ctypes.POINTER(ctypes.c_float)
     i64 = ctypes.c_int64
     sig = {
         "bl_lb_init": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(bl_lb_params), vp]),
@@ -103,6 +105,14 @@ def lib():
         "bl_ensemble_step": (ctypes.c_int, [vp, ctypes.c_int]),
         "bl_ensemble_sync": (ctypes.c_int, [vp]),
         "bl_ensemble_destroy": (None, [vp]),
+        "bl_mlp_create": (ctypes.c_int, [ctypes.POINTER(vp), vp]),
+        "bl_mlp_params_set": (ctypes.c_int, [vp, F, F]),
+        "bl_mlp_params_get": (ctypes.c_int, [vp, F, F]),
+        "bl_mlp_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
+        "bl_mlp_grad": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, F, F]),
+        "bl_mlp_adam": (ctypes.c_int, [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+        "bl_mlp_sync": (ctypes.c_int, [vp]),
+        "bl_mlp_destroy": (None, [vp]),
         "bl_timing_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "bl_timing_read": (ctypes.c_int, [vp, D, ctypes.POINTER(i64), ctypes.c_int]),
         "bl_launch_count": (i64, [vp]),
@@ -234,6 +244,65 @@ def bl_ensemble_sync(ens):
 def bl_ensemble_destroy(ens):
     if ens:
         lib().bl_ensemble_destroy(ens)
+
+
+MLP_NPAR = 5510
+
+
+def _fp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _mcheck(rc, what):
+    if rc != BL_OK:
+        raise BloodLBError(rc, what)
+    return rc
+
+
+def bl_mlp_create(stream=None):
+    m = ctypes.c_void_p()
+    _mcheck(lib().bl_mlp_create(ctypes.byref(m), ctypes.c_void_p(stream or 0)), "bl_mlp_create")
+    return m
+
+
+def bl_mlp_params_set(m, theta=None, norm=None):
+    t = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32).reshape(MLP_NPAR)
+    n = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32).reshape(40)
+    return _mcheck(lib().bl_mlp_params_set(m, _fp(t), _fp(n)), "bl_mlp_params_set")
+
+
+def bl_mlp_params_get(m):
+    t, n = np.zeros(MLP_NPAR, dtype=np.float32), np.zeros(40, dtype=np.float32)
+    _mcheck(lib().bl_mlp_params_get(m, _fp(t), _fp(n)), "bl_mlp_params_get")
+    return t, n
+
+
+def bl_mlp_forward(m, x, y):
+    """x, y: CUDA float32 tensors (B x 14, B x 6)"""
+    return _mcheck(lib().bl_mlp_forward(m, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                        ctypes.c_void_p(y.data_ptr())), "bl_mlp_forward")
+
+
+def bl_mlp_grad(m, x, y, want_grad=False):
+    """x, y: CUDA float32 tensors; returns (loss, grad or None)"""
+    loss = np.zeros(1, dtype=np.float32)
+    g = np.zeros(MLP_NPAR, dtype=np.float32) if want_grad else None
+    _mcheck(lib().bl_mlp_grad(m, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), int(x.shape[0]),
+                              _fp(loss), _fp(g)), "bl_mlp_grad")
+    return float(loss[0]), g
+
+
+def bl_mlp_adam(m, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    return _mcheck(lib().bl_mlp_adam(m, float(lr), float(beta1), float(beta2), float(eps)), "bl_mlp_adam")
+
+
+def bl_mlp_sync(m):
+    return _mcheck(lib().bl_mlp_sync(m), "bl_mlp_sync")
+
+
+def bl_mlp_destroy(m):
+    if m:
+        lib().bl_mlp_destroy(m)
 
 
 def bl_fields_get(ctx, N, rho=None, u=None, owner=None, on_device=False):

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libbloodlb.so")
-SOURCES = ["bloodlb.cu", "lb_kernels.cu", "particle_kernels.cu", "cell_list_static.cu"]
+SOURCES = ["bloodlb.cu", "lb_kernels.cu", "particle_kernels.cu", "cell_list_static.cu", "mlp_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-Xptxas", "-O3"]

@@ -87,7 +87,9 @@ typedef struct {
   double mu, nu, chi_prime; /* Gay-Berne exponents of the strength */
   double r_cut;             /* neighbour-list radius (the potential is compact) */
   double rho_p;             /* cell density; mass rho_p 4/3 pi R_perp^2 R_par */
-  int move_particles;       /* 0: cells held fixed (forces still computed) */
+  int move_particles;       /* 0: cells held fixed (forces still computed); 1: free cells; 2: prescribed
+                               motion, the cells keep the V and Omega = I_lab^-1 L of their last set
+                               (forces computed and reported, not applied) */
   int reserved;
 } bl_particle_params;
 
@@ -250,6 +252,19 @@ int bl_mlp_grad(bl_mlp *m, const float *x, const float *y, int B, float *loss, f
 int bl_mlp_adam(bl_mlp *m, float lr, float beta1, float beta2, float eps);
 int bl_mlp_sync(bl_mlp *m);
 void bl_mlp_destroy(bl_mlp *m);
+
+/* Uses model m (NULL: none) in every later step of context c: after the
+   potentials, every ordered pair of cells with gap < gap_cut (lattice units)
+   gets the network's force and torque correction, rotated to the lab frame
+   and added to the potential part of the step's force (bl_force_parts_get
+   Fp / Tp).  The model must outlive its use; the step runs it on the
+   context's streams. */
+int bl_mlp_attach(bl_ctx *c, bl_mlp *m, double gap_cut);
+
+/* Features of n ordered pairs (device array of n x 2 int32 cell indices) from
+   the current cell state, into the device array out (n x 14 float), on the
+   context stream; invalid pairs (an index out of range, i == j) give zeros. */
+int bl_pair_features(bl_ctx *c, const int32_t *pairs, int n, float *out);
 
 /* Kernel timing with CUDA events.  While enabled, steps are enqueued one
    kernel group at a time (no graph), each group bracketed by an event pair

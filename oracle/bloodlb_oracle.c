@@ -91,7 +91,7 @@ typedef struct {
   double mu, nu, chi_prime;
   double r_cut;
   double rho_p;
-  int move_particles;
+  int move_particles; /* 0 held fixed, 1 free (implicit coupling), 2 prescribed V, Omega */
 } orc_params;
 
 typedef struct {
@@ -708,7 +708,9 @@ static void step_once(orc_state *s) {
        Ztf V + (I_lab + Ztt) Omega = L(t-1/2) + T0 + T_other,
      with F_other, T_other the contact, potential, fill/drain and body forces. */
   double m = cell_mass(p);
-  if (s->np > 0 && p->move_particles) {
+  /* move_particles 2: prescribed motion, the cells keep the V and Omega of
+     their last set; the forces are measured, not applied */
+  if (s->np > 0 && p->move_particles == 1) {
     double *F0 = (double *)xcalloc(3 * (long)s->np, sizeof(double));
     double *T0 = (double *)xcalloc(3 * (long)s->np, sizeof(double));
     double *Z = (double *)xcalloc(36 * (long)s->np, sizeof(double)); /* 6 x 6 per cell */

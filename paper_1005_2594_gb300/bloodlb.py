@@ -36,7 +36,8 @@ ABI_FUNCTIONS = (
     "bl_boundary_links_get", "bl_contact_links_get", "bl_cell_list_get", "bl_cell_list_build_static",
     "bl_sweep_variant", "bl_autotune", "bl_ensemble_create", "bl_ensemble_step", "bl_ensemble_sync",
     "bl_ensemble_destroy", "bl_mlp_create", "bl_mlp_params_set", "bl_mlp_params_get", "bl_mlp_forward",
-    "bl_mlp_grad", "bl_mlp_adam", "bl_mlp_sync", "bl_mlp_destroy", "bl_timing_enable",
+    "bl_mlp_grad", "bl_mlp_adam", "bl_mlp_sync", "bl_mlp_destroy", "bl_mlp_attach", "bl_pair_features",
+    "bl_timing_enable",
     "bl_timing_read", "bl_launch_count", "bl_sync", "bl_last_error", "bl_destroy",
 )
 
@@ -113,6 +114,8 @@ def lib():
         "bl_mlp_adam": (ctypes.c_int, [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
         "bl_mlp_sync": (ctypes.c_int, [vp]),
         "bl_mlp_destroy": (None, [vp]),
+        "bl_mlp_attach": (ctypes.c_int, [vp, vp, ctypes.c_double]),
+        "bl_pair_features": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         "bl_timing_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "bl_timing_read": (ctypes.c_int, [vp, D, ctypes.POINTER(i64), ctypes.c_int]),
         "bl_launch_count": (i64, [vp]),
@@ -303,6 +306,16 @@ def bl_mlp_sync(m):
 def bl_mlp_destroy(m):
     if m:
         lib().bl_mlp_destroy(m)
+
+
+def bl_mlp_attach(ctx, m, gap_cut):
+    return _check(ctx, lib().bl_mlp_attach(ctx, m, float(gap_cut)))
+
+
+def bl_pair_features(ctx, pairs, out):
+    """pairs: CUDA int32 tensor (n x 2); out: CUDA float32 tensor (n x 14)"""
+    return _check(ctx, lib().bl_pair_features(ctx, ctypes.c_void_p(pairs.data_ptr()), int(pairs.shape[0]),
+                                              ctypes.c_void_p(out.data_ptr())))
 
 
 def bl_fields_get(ctx, N, rho=None, u=None, owner=None, on_device=False):

@@ -143,6 +143,15 @@ struct SurfBits {
   int nxw;
 };
 
+// close pairs of the learned correction: pairs (i, j), their features
+// (14 floats) and the network's outputs (6 floats)
+struct PairBuf {
+  int2 *pairs;
+  float *feat, *out;
+  int *count;
+  int cap;
+};
+
 struct ChangeList {
   int *count;
   int32_t *items;  // triples (node, old, new)
@@ -174,6 +183,13 @@ void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st,
 void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, const CellListView &cl, int *claim,
                          const ChangeList &chg, int par_next, int impulses, cudaStream_t st, int64_t *nl);
 void launch_clear_cells(int dtype, const LatticeView &lv, int par, cudaStream_t st, int64_t *nl);
+
+void launch_pair_features(const LatticeView &lv, const PartView &pv, const int2 *pairs, int n, float *out,
+                          cudaStream_t st);
+void launch_mlp_correction(const LatticeView &lv, const PartView &pv, const CellListView &cl, const PairBuf &pb,
+                           float gap_cut, const void *mlp, cudaStream_t st, int64_t *nl);
+// forward pass of a bl_mlp over *count rows of x (at most cap), raw units
+void launch_mlp_forward_dev(const void *mlp, const float *x, const int *count, int cap, float *y, cudaStream_t st);
 
 // bit flags of the device status word
 constexpr int ST_UNSTABLE = 1;

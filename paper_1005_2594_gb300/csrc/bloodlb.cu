@@ -44,6 +44,11 @@ struct bl_ctx {
   const void *g_kin;
   int64_t g_launches;
   int epoch;  // counts graph invalidations (cell arrays moved, walls or sweep variant changed)
+  // learned near-contact correction (bl_mlp_attach): the model, its gap
+  // cut-off and the close-pair buffers (32 pairs per cell)
+  const void *mlp;
+  float gap_cut;
+  PairBuf pb;
   int dtype;
   int parity;  // layout of the current populations (next step's parity)
   LatticeView lv;
@@ -280,6 +285,12 @@ static void free_particles(bl_ctx *c) {
                   c->chg.count, c->chg.items};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  {
+    void *pp[] = {c->pb.pairs, c->pb.feat, c->pb.out, c->pb.count};
+    for (void *p : pp)
+      if (p) cudaFree(p);
+    c->pb = PairBuf{};
+  }
   memset(&c->pv, 0, sizeof(c->pv));
   memset(&c->cl, 0, sizeof(c->cl));
   memset(&c->chg, 0, sizeof(c->chg));
@@ -359,6 +370,18 @@ static int alloc_particles(bl_ctx *c, int n) {
   return BL_OK;
 }
 
+static int alloc_pairbuf(bl_ctx *c) {
+  if (c->pb.pairs || c->np == 0) return BL_OK;
+  PairBuf &pb = c->pb;
+  pb.cap = 32 * c->np;
+  CU(cudaMalloc(&pb.pairs, sizeof(int2) * (size_t)pb.cap));
+  CU(cudaMalloc(&pb.feat, sizeof(float) * 14 * (size_t)pb.cap));
+  CU(cudaMalloc(&pb.out, sizeof(float) * 6 * (size_t)pb.cap));
+  CU(cudaMalloc(&pb.count, sizeof(int)));
+  CU(cudaMemsetAsync(pb.count, 0, sizeof(int), c->stream));
+  return BL_OK;
+}
+
 static void fill_particle_constants(bl_ctx *c) {
   const bl_particle_params &pp = c->pp;
   PartView &pv = c->pv;
@@ -370,7 +393,7 @@ static void fill_particle_constants(bl_ctx *c) {
   for (int k = 0; k < 3; ++k) pv.g[k] = c->lp.g[k];
   pv.status = c->status;
   pv.bfc = c->lp.body_force_on_cells ? 1 : 0;
-  pv.move = pp.move_particles ? 1 : 0;
+  pv.move = pp.move_particles;
   pv.inv_rpar2 = 1.0 / (pp.R_par * pp.R_par);
   pv.inv_rperp2 = 1.0 / (pp.R_perp * pp.R_perp);
   pv.R_par = pp.R_par;
@@ -402,6 +425,7 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
                 !(pp->sig_par > 0) || !(pp->sig_perp > 0) || !(pp->R_par < 1e4) || !(pp->R_perp < 1e4) ||
                 !(pp->sig_w >= 0) || !(pp->eps >= 0) || !(pp->eps_w >= 0)))
     return fail(c, BL_EINVAL, "bad cell parameters");
+  if (pp->move_particles < 0 || pp->move_particles > 2) return fail(c, BL_EINVAL, "move_particles not in 0..2");
   if (n > 0) {
     // the owner search covers one cell-list bin around a node (bins are at
     // least r_cut wide), and a cell must not reach half a periodic length
@@ -428,6 +452,7 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
       return BL_OK;
     }
     if (alloc_particles(c, n)) return c->sticky;
+    if (c->mlp && alloc_pairbuf(c)) return c->sticky;
   } else {
     c->pp = *pp;
   }
@@ -473,6 +498,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     group_end(c, slot, c->side);
     group_begin(c, 2, &slot, c->side);
     launch_forces(c->lv, c->pv, c->cl, c->sbits, c->side, &c->launches);
+    if (c->mlp) launch_mlp_correction(c->lv, c->pv, c->cl, c->pb, c->gap_cut, c->mlp, c->side, &c->launches);
     group_end(c, slot, c->side);
     cudaEventRecord(c->ev_join, c->side);
   }
@@ -742,6 +768,28 @@ extern "C" int bl_timing_read(bl_ctx *c, double *ms, int64_t *count, int ngroups
 extern "C" int64_t bl_launch_count(const bl_ctx *c) { return c ? c->launches : 0; }
 
 extern "C" const char *bl_last_error(const bl_ctx *c) { return c ? c->err : "null context"; }
+
+// ---------------------------------------------------------------------------
+// learned near-contact correction
+
+extern "C" int bl_mlp_attach(bl_ctx *c, bl_mlp *m, double gap_cut) {
+  if (!c) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (m && !(gap_cut > -1e3 && gap_cut < 1e3)) return fail(c, BL_EINVAL, "gap cut-off");
+  drop_graph(c);
+  c->mlp = m;
+  c->gap_cut = (float)gap_cut;
+  if (m && alloc_pairbuf(c)) return c->sticky;
+  return BL_OK;
+}
+
+extern "C" int bl_pair_features(bl_ctx *c, const int32_t *pairs, int n, float *out) {
+  if (!c || n < 0 || (n > 0 && (!pairs || !out))) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  launch_pair_features(c->lv, c->pv, reinterpret_cast<const int2 *>(pairs), n, out, c->stream);
+  c->launches += n > 0;
+  return check_launch(c, "pair features");
+}
 
 // ---------------------------------------------------------------------------
 // autotuning of the sweep variant

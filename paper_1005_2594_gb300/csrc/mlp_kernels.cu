@@ -162,9 +162,11 @@ __device__ __forceinline__ void load_x(const float *x, int B, int r0, const floa
   }
 }
 
-// inference on raw features: y = network(x) in raw output units (B x 6)
-__global__ void __launch_bounds__(128) k_mlp_forward(MlpDev m, const float *x, int B, float *y) {
+// inference on raw features: y = network(x) in raw output units (B x 6);
+// with Bdev the row count is min(*Bdev, B), read on the device
+__global__ void __launch_bounds__(128) k_mlp_forward(MlpDev m, const float *x, int B, const int *Bdev, float *y) {
   __shared__ __align__(16) __nv_bfloat16 wp[P_TOTAL];
+  if (Bdev) B = min(*Bdev, B);
   for (int i = threadIdx.x; i < P_W2T; i += blockDim.x) wp[i] = m.wp[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -478,7 +480,7 @@ extern "C" int bl_mlp_forward(bl_mlp *m, const float *x, int B, float *y) {
   if (!m || B < 0 || (B > 0 && (!x || !y))) return BL_EINVAL;
   if (B == 0) return BL_OK;
   const int blocks = min((B + 63) / 64, 4 * MLP_BLOCKS);
-  k_mlp_forward<<<blocks, 128, 0, m->stream>>>(mlp_dev(m), x, B, y);
+  k_mlp_forward<<<blocks, 128, 0, m->stream>>>(mlp_dev(m), x, B, nullptr, y);
   return cudaGetLastError() == cudaSuccess ? BL_OK : BL_ECUDA;
 }
 
@@ -503,6 +505,14 @@ extern "C" int bl_mlp_adam(bl_mlp *m, float lr, float beta1, float beta2, float 
   if (cudaGetLastError() != cudaSuccess) return BL_ECUDA;
   return mlp_pack(m);
 }
+
+namespace bl {
+void launch_mlp_forward_dev(const void *mlp, const float *x, const int *count, int cap, float *y, cudaStream_t st) {
+  const bl_mlp *m = static_cast<const bl_mlp *>(mlp);
+  const int blocks = min((cap + 63) / 64, 4 * MLP_BLOCKS);
+  if (blocks > 0) k_mlp_forward<<<blocks, 128, 0, st>>>(mlp_dev(m), x, cap, count, y);
+}
+}  // namespace bl
 
 extern "C" int bl_mlp_sync(bl_mlp *m) {
   if (!m) return BL_EINVAL;

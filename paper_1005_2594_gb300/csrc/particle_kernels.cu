@@ -711,7 +711,7 @@ __global__ void k_solve(LatticeView lv, PartView pv) {
   }
   const double Vp[3] = {k1.x, k1.y, k1.z}, Wp[3] = {k2.x, k2.y, k2.z};
   const bool move = pv.move != 0;
-  if (move) {
+  if (pv.move == 1) {  // free cells; 2: prescribed, V and W stay as set
     float Z[6][6];
     {
       int k = 6;
@@ -1254,6 +1254,107 @@ __global__ void k_clear_cells(LatticeView lv, int par) {
 }
 
 // ---------------------------------------------------------------------------
+// learned near-contact correction: pair features, close pairs, application
+
+// features of the ordered pair (i, j) in the body frame of i (R the rotation
+// of i): R^T r, q_i^* q_j with w >= 0, the gap |r| - sigma_R (Eq. sigma with
+// the fluid-coupling half-axes), R^T (V_j - V_i), R^T (W_j - W_i); velocities
+// of the current kinematics
+__device__ void pair_features(const LatticeView &lv, const PartView &pv, int i, int j, float f[14], float R[3][3]) {
+  const float4 a0 = pv.kin[3 * i], a1 = pv.kin[3 * i + 1], a2 = pv.kin[3 * i + 2];
+  const float4 b0 = pv.kin[3 * j], b1 = pv.kin[3 * j + 1], b2 = pv.kin[3 * j + 2];
+  const int dims[3] = {lv.nx, lv.ny, lv.nz};
+  const int ai[3] = {(int)a0.w, (int)a1.w, (int)a2.w}, bi[3] = {(int)b0.w, (int)b1.w, (int)b2.w};
+  const float af[3] = {a0.x, a0.y, a0.z}, bf[3] = {b0.x, b0.y, b0.z};
+  float r[3];
+  for (int k = 0; k < 3; ++k) r[k] = (float)imin_image(bi[k] - ai[k], dims[k], lv.per[k]) + (bf[k] - af[k]);
+  const double *qi = pv.q + 4 * i, *qj = pv.q + 4 * j;
+  rotmat_f(qi, R);
+  float Rj[3][3];
+  rotmat_f(qj, Rj);
+  const float oi[3] = {R[0][2], R[1][2], R[2][2]}, oj[3] = {Rj[0][2], Rj[1][2], Rj[2][2]};
+  const float rl = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), ir = 1.0f / rl;
+  const float a = (r[0] * oi[0] + r[1] * oi[1] + r[2] * oi[2]) * ir, b = (r[0] * oj[0] + r[1] * oj[1] + r[2] * oj[2]) * ir;
+  const float c = oi[0] * oj[0] + oi[1] * oj[1] + oi[2] * oj[2];
+  const float Rp2 = (float)(pv.R_par * pv.R_par), Rq2 = (float)(pv.R_perp * pv.R_perp);
+  const float chi = (Rp2 - Rq2) / (Rp2 + Rq2);
+  const float S = 1.0f - 0.5f * chi * ((a + b) * (a + b) / (1.0f + chi * c) + (a - b) * (a - b) / (1.0f - chi * c));
+  const float gap = rl - 2.0f * (float)pv.R_perp * rsqrtf(S);
+  const float dv[3] = {b1.x - a1.x, b1.y - a1.y, b1.z - a1.z}, dw[3] = {b2.x - a2.x, b2.y - a2.y, b2.z - a2.z};
+  for (int k = 0; k < 3; ++k) {
+    f[k] = R[0][k] * r[0] + R[1][k] * r[1] + R[2][k] * r[2];
+    f[8 + k] = R[0][k] * dv[0] + R[1][k] * dv[1] + R[2][k] * dv[2];
+    f[11 + k] = R[0][k] * dw[0] + R[1][k] * dw[1] + R[2][k] * dw[2];
+  }
+  const float w1 = (float)qi[0], x1 = -(float)qi[1], y1 = -(float)qi[2], z1 = -(float)qi[3];
+  const float w2 = (float)qj[0], x2 = (float)qj[1], y2 = (float)qj[2], z2 = (float)qj[3];
+  float qr[4] = {w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                 w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2};
+  const float sgn = qr[0] < 0.f ? -1.f : 1.f;
+  for (int k = 0; k < 4; ++k) f[3 + k] = sgn * qr[k];
+  f[7] = gap;
+}
+
+__global__ void k_pair_features(LatticeView lv, PartView pv, const int2 *pairs, int n, float *out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int2 pr = pairs[t];
+  if (pr.x < 0 || pr.x >= pv.n || pr.y < 0 || pr.y >= pv.n || pr.x == pr.y) {
+    for (int k = 0; k < 14; ++k) out[14 * t + k] = 0.f;
+    return;
+  }
+  float f[14], R[3][3];
+  pair_features(lv, pv, pr.x, pr.y, f, R);
+  for (int k = 0; k < 14; ++k) out[14 * t + k] = f[k];
+}
+
+// close pairs (gap below the cut-off) from the cell list, one block per cell
+// (lane b < 27 scans bin b), with their features
+__global__ void k_mlp_pairs(LatticeView lv, PartView pv, CellListView cl, PairBuf pb, float gap_cut) {
+  const int i = blockIdx.x;
+  if (threadIdx.x >= 27) return;
+  const int bin = cl.bin_of[i];
+  const int bc[3] = {bin % cl.nb[0], (bin / cl.nb[0]) % cl.nb[1], bin / (cl.nb[0] * cl.nb[1])};
+  int off[3][3], noff[3];
+  for (int k = 0; k < 3; ++k) noff[k] = bin_offsets(cl.nb[k], lv.per[k], bc[k], off[k]);
+  const int ix = threadIdx.x % 3, iy = (threadIdx.x / 3) % 3, iz = threadIdx.x / 9;
+  if (ix >= noff[0] || iy >= noff[1] || iz >= noff[2]) return;
+  const int b = wrapi(bc[0] + off[0][ix], cl.nb[0]) +
+                cl.nb[0] * (wrapi(bc[1] + off[1][iy], cl.nb[1]) + cl.nb[1] * wrapi(bc[2] + off[2][iz], cl.nb[2]));
+  const int e = cl.start[b + 1];
+  for (int k = cl.start[b]; k < e; ++k) {
+    const int j = cl.ids[k];
+    if (j == i) continue;
+    float f[14], R[3][3];
+    pair_features(lv, pv, i, j, f, R);
+    if (!(f[7] < gap_cut)) continue;
+    const int s = atomicAdd(pb.count, 1);
+    if (s >= pb.cap) {
+      atomicOr(pv.status, ST_OVERFLOW);
+      continue;
+    }
+    pb.pairs[s] = make_int2(i, j);
+    for (int q = 0; q < 14; ++q) pb.feat[14 * s + q] = f[q];
+  }
+}
+
+// the network's force and torque on i, back from its body frame to the lab
+// frame, added to the potentials of the step
+__global__ void k_mlp_apply(PartView pv, PairBuf pb) {
+  const int n = min(*pb.count, pb.cap);
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const int i = pb.pairs[s].x;
+    float R[3][3];
+    rotmat_f(pv.q + 4 * i, R);
+    const float *y = pb.out + 6 * s;
+    for (int k = 0; k < 3; ++k) {
+      atomicAdd(&pv.Fpot[3 * i + k], (double)(R[k][0] * y[0] + R[k][1] * y[1] + R[k][2] * y[2]));
+      atomicAdd(&pv.Tpot[3 * i + k], (double)(R[k][0] * y[3] + R[k][1] * y[4] + R[k][2] * y[5]));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host-side launchers
 
 static inline unsigned nblk(unsigned n, unsigned b) { return (n + b - 1) / b; }
@@ -1290,6 +1391,21 @@ void launch_cell_step(int dtype, const LatticeView &lv, const PartView &pv, int 
   if (dtype == 0) cell_step_typed<float>(lv, pv, par, st);
   else if (dtype == 1) cell_step_typed<__nv_bfloat16>(lv, pv, par, st);
   else cell_step_typed<__half>(lv, pv, par, st);
+  *nl += 3;
+}
+
+void launch_pair_features(const LatticeView &lv, const PartView &pv, const int2 *pairs, int n, float *out,
+                          cudaStream_t st) {
+  if (n > 0) k_pair_features<<<nblk(n, 128), 128, 0, st>>>(lv, pv, pairs, n, out);
+}
+
+void launch_mlp_correction(const LatticeView &lv, const PartView &pv, const CellListView &cl, const PairBuf &pb,
+                           float gap_cut, const void *mlp, cudaStream_t st, int64_t *nl) {
+  if (pv.n == 0) return;
+  cudaMemsetAsync(pb.count, 0, sizeof(int), st);
+  k_mlp_pairs<<<pv.n, 32, 0, st>>>(lv, pv, cl, pb, gap_cut);
+  launch_mlp_forward_dev(mlp, pb.feat, pb.count, pb.cap, pb.out, st);
+  k_mlp_apply<<<nblk((unsigned)pb.cap, 128) < 152u ? nblk((unsigned)pb.cap, 128) : 152u, 128, 0, st>>>(pv, pb);
   *nl += 3;
 }
 

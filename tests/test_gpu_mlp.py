@@ -97,3 +97,117 @@ def test_adam_training_fits_a_teacher():
     print("teacher fit: loss %.4e -> %.4e" % (first, last))
     assert last < first / 20
     bl.bl_mlp_destroy(m)
+
+
+def _overlap_state(seed=17, n=10):
+    from paper_1005_2594_gb300 import workloads
+
+    p = workloads.base_params(30, 26, 22, periodic=(1, 1, 0), R=(5.0, 2.5))
+    rng = np.random.default_rng(seed)
+    X = np.column_stack([rng.uniform(0, 30, n), rng.uniform(0, 26, n), rng.uniform(6.5, 15.5, n)])
+    _, q = workloads.random_axes_and_quaternions(rng, n)
+    V = rng.uniform(-0.02, 0.02, (n, 3))
+    L = rng.uniform(-5.0, 5.0, (n, 3))
+    return p, X, q, V, L
+
+
+def test_pair_features_match_oracle():
+    import torch
+
+    import oracle
+    from oracle import mlp
+    from paper_1005_2594_gb300 import bloodlb as bl
+
+    p, X, q, V, L = _overlap_state()
+    orc, sim = oracle.Oracle(p), bl.Simulation(p)
+    orc.set_particles(X, q, V, L)
+    sim.set_particles(X, q, V, L)
+    Om = orc.force_parts()["Om"]
+    n = X.shape[0]
+    pairs = np.array([(i, j) for i in range(n) for j in range(n) if i != j], dtype=np.int32)
+    pd = torch.tensor(pairs, device="cuda")
+    out = torch.zeros((len(pairs), 14), dtype=torch.float32, device="cuda")
+    bl.bl_pair_features(sim.ctx, pd, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    dims = (p["nx"], p["ny"], p["nz"])
+    ref = np.array([mlp.pair_features(p["R_par"], p["R_perp"], dims, p["periodic"], X[i], q[i], V[i], Om[i],
+                                      X[j], q[j], V[j], Om[j]) for i, j in pairs])
+    scale = np.abs(ref).max(axis=0)
+    err = (np.abs(got - ref) / scale).max()
+    print("pair features: max error relative to each feature's range %.2e" % err)
+    assert err < 1e-5
+
+
+def test_prescribed_motion_matches_oracle():
+    import oracle
+    from paper_1005_2594_gb300 import bloodlb as bl
+    from paper_1005_2594_gb300 import workloads
+
+    p = workloads.base_params(32, 32, 32, periodic=(1, 1, 1), R=(3.5, 1.5))
+    p["move_particles"] = 2
+    X = np.array([[10.2, 16.1, 15.7], [19.4, 15.8, 16.3]])
+    q = np.array([[1.0, 0, 0, 0], [np.cos(0.3), np.sin(0.3), 0, 0]])
+    V = np.array([[0.02, 0.0, 0.0], [-0.02, 0.0, 0.0]])
+    L = np.array([[0.0, 0.0, 0.5], [0.0, 0.0, -0.5]])
+    orc, sim = oracle.Oracle(p), bl.Simulation(p)
+    orc.set_particles(X, q, V, L)
+    sim.set_particles(X, q, V, L)
+    for _ in range(20):
+        orc.step(1)
+        sim.step(1)
+        np.testing.assert_array_equal(sim.owner(), orc.owner())
+    po, pg = orc.particles(), sim.particles()
+    for k in ("X", "q", "F", "T"):
+        assert rel(pg[k], po[k]) < 1e-5, k
+    np.testing.assert_array_equal(pg["V"], V)
+
+
+def test_attached_network_adds_rotated_correction_to_close_pairs():
+    """A network whose output is its bias b3 adds R_i b3 once per close pair
+    (gap below the cut-off, from the oracle's features) to the potential
+    part of the force and torque."""
+    import oracle
+    from oracle import mlp
+    from paper_1005_2594_gb300 import bloodlb as bl
+
+    p, X, q, V, L = _overlap_state(seed=23, n=12)
+    cut = 2.0
+    theta = np.zeros(mlp.N_PARAMS)
+    b3 = np.array([0.1, -0.2, 0.3, 0.01, 0.02, -0.03])
+    theta[-6:] = b3
+    norm = np.concatenate([np.zeros(14), np.ones(14), np.zeros(6), np.ones(6)])
+    m = bl.bl_mlp_create()
+    bl.bl_mlp_params_set(m, theta, norm)
+    a, b = bl.Simulation(p), bl.Simulation(p)
+    bl.bl_mlp_attach(b.ctx, m, cut)
+    for s in (a, b):
+        s.set_particles(X, q, V, L)
+        s.step(1)
+        s.sync()
+    dF = b.force_parts()["Fp"] - a.force_parts()["Fp"]
+    dT = b.force_parts()["Tp"] - a.force_parts()["Tp"]
+    orc = oracle.Oracle(p)
+    orc.set_particles(X, q, V, L)
+    Om = orc.force_parts()["Om"]
+    dims = (p["nx"], p["ny"], p["nz"])
+    n = X.shape[0]
+    eF, eT = np.zeros((n, 3)), np.zeros((n, 3))
+    npairs = 0
+    for i in range(n):
+        R = mlp.rotmat(q[i])
+        for j in range(n):
+            if i == j:
+                continue
+            f = mlp.pair_features(p["R_par"], p["R_perp"], dims, p["periodic"], X[i], q[i], V[i], Om[i], X[j],
+                                  q[j], V[j], Om[j])
+            if f[7] < cut:
+                eF[i] += R @ b3[:3]
+                eT[i] += R @ b3[3:]
+                npairs += 1
+    assert npairs > 0
+    np.testing.assert_allclose(dF, eF, atol=1e-5)
+    np.testing.assert_allclose(dT, eT, atol=1e-5)
+    a.close()
+    b.close()
+    bl.bl_mlp_destroy(m)

@@ -328,3 +328,23 @@ def test_face_on_disc_near_wall_stays_bounded():
         o.step(1)
         fmax = max(fmax, np.abs(o.particles()["F"]).max())
     assert np.isfinite(fmax) and fmax < 0.1
+
+
+def test_prescribed_motion_keeps_velocities_and_moves_exactly():
+    """move_particles = 2: the cells keep the V and Omega of their last set
+    (the forces are measured, not applied) and advance by V each step."""
+    import oracle
+    from paper_1005_2594_gb300 import workloads
+
+    p = workloads.base_params(32, 32, 32, periodic=(1, 1, 1), R=(3.5, 1.5))
+    p["move_particles"] = 2
+    X = np.array([[10.2, 16.1, 15.7], [20.4, 15.8, 16.3]])
+    q = np.array([[1.0, 0, 0, 0], [np.cos(0.3), np.sin(0.3), 0, 0]])
+    V = np.array([[0.01, 0.0, 0.0], [-0.01, 0.0, 0.0]])
+    orc = oracle.Oracle(p)
+    orc.set_particles(X, q, V, np.zeros((2, 3)))
+    orc.step(10)
+    pp = orc.particles()
+    np.testing.assert_array_equal(pp["V"], V)
+    np.testing.assert_allclose(pp["X"], X + 10 * V, atol=1e-12)
+    assert np.abs(pp["F"]).max() > 0  # the fluid pushes back; nothing applies it

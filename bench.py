@@ -148,6 +148,9 @@ def make_workload(name):
     if name == "ensemble64":  # (the reference arm samples the first member)
         p, X, q, d = workloads.ensemble(n_boxes=1, seed=1004)[0]
         return p, X, q, None, "ensemble member 0: " + d
+    if name == "tube512":
+        p, X, q, mask = workloads.tube()
+        return p, X, q, mask, "tube 512x256x256, radius 120 along x, g = 1e-6 on plasma and cells, %d (7,7,3) cells at 35 %% of the lumen" % len(X)
     if name == "duct256":
         p, X, q = workloads.duct(n=256, n_cells=8192, g=1e-6, seed=1003)
         return p, X, q, None, "duct 256^3, walls y z, g = 1e-6 along x, 8192 (7,7,3) cells"
@@ -341,6 +344,101 @@ def run_ensemble(args, ws, rank, local):
     return out
 
 
+def run_learned(args, ws, rank, local):
+    """The learned near-contact correction: the network is trained through
+    the library on approach runs it generates (coarse and 2x resolution),
+    its error is measured on held-out approach runs against the 2x and 4x
+    runs, and the tube workload is timed without and with the network
+    attached (gap cut-off 2 lattice units)."""
+    import torch
+
+    import __graft_entry__
+    from paper_1005_2594_gb300 import bloodlb as bl
+    from paper_1005_2594_gb300 import learned
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    X, Y, _, runs = learned.approach_samples(64, seed=11)
+    Xh, Yh, _, _ = learned.approach_samples(20, seed=12)
+    X4, Y4, _, _ = learned.approach_samples(8, seed=13, k=4)
+    t_data = time.time() - t0
+    t0 = time.time()
+    m, info = learned.fit(X, Y, runs, seed=0)
+    torch.cuda.synchronize()
+    t_fit = time.time() - t0
+    scale = Y.std(axis=0)
+    e2 = learned.errors(m, Xh, Yh, scale)
+    e4 = learned.errors(m, X4, Y4, scale)
+    P = learned.predict(m, Xh)
+
+    def rms_ratio(a, b):
+        return float(np.sqrt(((Yh - P)[:, a:b] ** 2).sum(1).mean() / (Yh[:, a:b] ** 2).sum(1).mean()))
+
+    p, Xc, qc, mask, desc = make_workload("tube512")
+    N = p["nx"] * p["ny"] * p["nz"]
+    sim = bl.Simulation(p, stream=stream.cuda_stream, wall_mask=mask)
+    sim.set_particles(Xc, qc)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    clocks = ClockSampler(local)
+    for mode in ("plain", "learned"):
+        if mode == "learned":
+            bl.bl_mlp_attach(sim.ctx, m, 2.0)
+        sim.step(args.warmup)
+        sim.sync()
+        l0 = bl.bl_launch_count(sim.ctx)
+        if mode == "learned":
+            clocks.start()
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms = allreduce_max(e0.elapsed_time(e1), ws)
+        sim.sync()
+        res[mode] = (ms, bl.bl_launch_count(sim.ctx) - l0)
+    clk = clocks.stop()
+    ms, launches = res["learned"]
+    ms_plain = res["plain"][0]
+    fluid = int((sim.owner() == -1).sum())
+    hbm, src = peaks()
+    bytes_step = fluid * 2 * 19 * 4 + N * 4
+    achieved = bytes_step * args.steps / (ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(job_value(ws, N, args.steps, ms), 2), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
+        "data": "synthetic (jittered fcc start, resting plasma; network trained on generated approach runs)",
+        "config": {"workload": desc, "lattice": [p["nx"], p["ny"], p["nz"]], "cells": int(len(Xc)),
+                   "fluid_nodes": fluid, "gap_cut": 2.0, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "populations %.0f MB > 129 MB L2, no flush" % (N * 19 * 4 / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "kernel": "whole coupled step with the network (sweep bytes over step time)", "peak_source": src},
+        "without_network": {"value": round(job_value(ws, N, args.steps, ms_plain), 2),
+                            "ms_per_step": round(ms_plain / args.steps, 5)},
+        "learned": {
+            "approach_runs": {"train": 64, "held_out_2x": 20, "held_out_4x": 8, "generation_s": round(t_data, 1)},
+            "training": {"seconds": round(t_fit, 2), **{k: (round(v, 4) if isinstance(v, float) else v)
+                                                         for k, v in info.items()}},
+            "error_vs_2x": {"without": round(e2[0], 4), "with": round(e2[1], 4), "ratio": round(e2[1] / e2[0], 4),
+                            "force_rms_ratio": round(rms_ratio(0, 3), 4),
+                            "torque_rms_ratio": round(rms_ratio(3, 6), 4)},
+            "error_vs_4x": {"without": round(e4[0], 4), "with": round(e4[1], 4), "ratio": round(e4[1] / e4[0], 4)},
+            "note": "mean squared error of the body-frame hydrodynamic force and torque on held-out approach "
+                    "runs, each output divided by its spread in the training data"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    sim.close()
+    bl.bl_mlp_destroy(m)
+    return out
+
+
 def run_e2e(sim, n, N, steps, stream):
     import torch
 
@@ -405,17 +503,31 @@ def run_reference(args, ws, rank):
     import oracle
 
     p, X, q, _, desc = make_workload(args.config)
-    sp, sX, sq, sample = reference_sample(p, X, q, 150.0, args.steps + args.warmup)
+    steps, warmup = args.steps, args.warmup
+    if args.config == "tube512":
+        # the cross-section is fixed by the radius: a slab of 8 x-planes of the
+        # same tube, and as many steps as fit the budget (~0.5 s each)
+        from paper_1005_2594_gb300 import workloads
+
+        sp, sX, sq, smask = workloads.tube(nx=8)
+        steps, warmup = max(1, min(steps, 200)), min(warmup, 3)
+        sample = "8x256x256 slab of the same tube (walls, fcc start, 35 %% of the lumen), %d cells, %d steps" % (
+            len(sX), steps)
+    else:
+        sp, sX, sq, sample = reference_sample(p, X, q, 150.0, steps + warmup)
+        smask = None
     o = oracle.Oracle(sp)
+    if smask is not None:
+        o.set_walls(smask)
     o.set_particles(sX, sq)
-    o.step(args.warmup)
+    o.step(warmup)
     t0 = time.perf_counter()
-    o.step(args.steps)
+    o.step(steps)
     dt = time.perf_counter() - t0
     Ns = sp["nx"] * sp["ny"] * sp["nz"]
-    v = Ns * args.steps / dt / 1e6
+    v = Ns * steps / dt / 1e6
     return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "steps": steps, "warmup": warmup, "ms_per_step": round(dt / steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded random packing, resting start)",
             "config": {"workload": desc, "sample": sample},
@@ -429,7 +541,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--config", default="shear128", choices=["shear128", "small32", "duct256", "ensemble64"])
+    ap.add_argument("--config", default="shear128", choices=["shear128", "small32", "duct256", "ensemble64", "tube512"])
     ap.add_argument("--store", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -441,8 +553,8 @@ def main():
         if rank == 0:
             print(json.dumps(out), flush=True)
         return
-    if args.config == "ensemble64":
-        out = run_ensemble(args, ws, rank, local)
+    if args.config in ("ensemble64", "tube512"):
+        out = (run_ensemble if args.config == "ensemble64" else run_learned)(args, ws, rank, local)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return

@@ -180,6 +180,11 @@ void launch_set_state(const LatticeView &lv, const PartView &pv, int mode, cudaS
 void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg, int mode,
                    cudaStream_t st, int64_t *nl);
 void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);
+// the geometry after a step's resolve: neighbour words around the changed
+// nodes, link lists and contact sums cell by cell (same result as
+// launch_geometry)
+void launch_geometry_step(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
+                          int64_t *nl);
 void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, const CellListView &cl, int *claim,
                          const ChangeList &chg, int par_next, int impulses, cudaStream_t st, int64_t *nl);
 void launch_clear_cells(int dtype, const LatticeView &lv, int par, cudaStream_t st, int64_t *nl);

@@ -514,7 +514,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     group_begin(c, 4, &slot, st);
     launch_claims(c->lv, c->pv, c->claim, c->chg, 0, st, &c->launches);
     launch_resolve_fill(c->dtype, c->lv, c->pv, c->cl, c->claim, c->chg, c->parity ^ 1, 1, st, &c->launches);
-    launch_geometry(c->lv, c->pv, st, &c->launches);
+    launch_geometry_step(c->lv, c->pv, c->chg, st, &c->launches);
     group_end(c, slot, st);
     std::swap(c->pv.kin, c->pv.kin_next);
   }

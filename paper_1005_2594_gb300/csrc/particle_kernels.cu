@@ -1232,6 +1232,192 @@ __global__ void __launch_bounds__(CB) k_resolve_fill(LatticeView lv, PartView pv
   }
 }
 
+// ---------------------------------------------------------------------------
+// geometry of the step, incrementally.  After resolve, a node's neighbour
+// word can differ from the last one only if its own owner or a neighbour's
+// changed, and every change is in the change list; the link lists and
+// contact sums of a cell come from the nodes it owns, which lie inside its
+// ellipsoid at X(t+1) (a cell owns only nodes it covers).
+
+// neighbour word of node (x, y, z) from the owner map: bit 0 fluid, bit r
+// neighbour x + c_r solid, NB_WALL / NB_CELL some solid neighbour is a wall /
+// a cell; zero for solid nodes
+__device__ __forceinline__ uint32_t node_word(const LatticeView &lv, int x, int y, int z) {
+  using D = D3Q19;
+  const unsigned nx = (unsigned)lv.nx, nxy = (unsigned)lv.nx * (unsigned)lv.ny;
+  if (lv.owner[(unsigned)x + nx * (unsigned)y + nxy * (unsigned)z] != FLUID) return 0u;
+  const int xs[3] = {x == 0 ? lv.nx - 1 : x - 1, x, x == lv.nx - 1 ? 0 : x + 1};
+  const int ys[3] = {y == 0 ? lv.ny - 1 : y - 1, y, y == lv.ny - 1 ? 0 : y + 1};
+  const int zs[3] = {z == 0 ? lv.nz - 1 : z - 1, z, z == lv.nz - 1 ? 0 : z + 1};
+  unsigned solid = 0, wall = 0;
+  sfor<1, Q>([&](auto R) {
+    constexpr int r = decltype(R)::value;
+    const int on = lv.owner[(unsigned)xs[1 + D::cx(r)] + nx * (unsigned)ys[1 + D::cy(r)] + nxy * (unsigned)zs[1 + D::cz(r)]];
+    solid |= (on != FLUID ? 1u : 0u) << r;
+    wall |= (on <= -2 ? 1u : 0u) << r;
+  });
+  return NB_FLUID | solid | (wall ? NB_WALL : 0u) | ((solid & ~wall) ? NB_CELL : 0u);
+}
+
+// neighbour words of every changed node x and of the nodes x - c_r that see
+// it; the whole lattice if the change list overflowed (grid-stride)
+__global__ void k_nbm_update(LatticeView lv, ChangeList chg) {
+  using D = D3Q19;
+  const int cnt = *chg.count;
+  const bool all = cnt > chg.cap;
+  const long long total = all ? (long long)lv.N : (long long)cnt * Q;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    int xyz[3];
+    if (all) {
+      node_xyz(lv, (unsigned)t, xyz);
+    } else {
+      const int c = (int)(t / Q), r = (int)(t - (long long)c * Q);
+      node_xyz(lv, (unsigned)chg.items[3 * c], xyz);
+      xyz[0] = wrapi(xyz[0] - D::cx(r), lv.nx);
+      xyz[1] = wrapi(xyz[1] - D::cy(r), lv.ny);
+      xyz[2] = wrapi(xyz[2] - D::cz(r), lv.nz);
+    }
+    lv.nbm[node_of(lv, xyz[0], xyz[1], xyz[2])] = node_word(lv, xyz[0], xyz[1], xyz[2]);
+  }
+}
+
+// link list and contact sums of one cell (one block per cell): the rows of
+// the cell's box, each cut to the outer interval of its ellipsoid at X(t+1),
+// flattened over the block; every node the cell owns appends the links from
+// its fluid neighbours (grouped by direction within a warp, so that the link
+// kernels read slots of one direction together) and adds its contact links
+// to exact integer sums
+__global__ void __launch_bounds__(CB) k_cell_links(LatticeView lv, PartView pv) {
+  using D = D3Q19;
+  const unsigned FULL = 0xffffffffu;
+  __shared__ int sh_w[CB / 32 + 1];
+  __shared__ int s_off[CB + 1], s_x0[CB], s_y[CB], s_z[CB];
+  __shared__ int s_len;
+  __shared__ int s_ci[CB / 32][6];
+  const int p = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) s_len = 0;
+  const int lo1 = pv.box[6 * p + 1], lo2 = pv.box[6 * p + 2];
+  const int by = pv.box[6 * p + 4] - lo1 + 1, bz = pv.box[6 * p + 5] - lo2 + 1;
+  const int rows = (by > 0 && bz > 0) ? by * bz : 0;
+  CellGeo g;
+  cell_geo(pv, p, g);
+  const float ip = (float)pv.inv_rperp2, kk = (float)(pv.inv_rpar2 - pv.inv_rperp2);
+  const int imin = lv.per[0] ? -(lv.nx / 2) : -g.Xi[0];
+  const int imax = lv.per[0] ? imin + lv.nx - 1 : lv.nx - 1 - g.Xi[0];
+  const float4 k0 = pv.kin_next[3 * p], k1 = pv.kin_next[3 * p + 1], k2 = pv.kin_next[3 * p + 2];
+  const int Xk[3] = {(int)k0.w, (int)k1.w, (int)k2.w};
+  unsigned long long *lk = pv.lk + (size_t)p * pv.lk_cap;
+  const unsigned below = (1u << lane) - 1u;
+  const unsigned nx = (unsigned)lv.nx, nxy = (unsigned)lv.nx * (unsigned)lv.ny;
+  int ci[6] = {0, 0, 0, 0, 0, 0};
+  for (int r0 = 0; r0 < rows; r0 += CB) {
+    const int t = r0 + threadIdx.x;
+    int len = 0, ao = 0, y = 0, z = 0;
+    if (t < rows) {
+      y = lo1 + t % by;
+      z = lo2 + t / by;
+      if (lv.per[1]) y = wrapi(y, lv.ny);
+      if (lv.per[2]) z = wrapi(z, lv.nz);
+      const RowQuad qn = row_quad((float)imin_image(y - g.Xi[1], lv.ny, lv.per[1]) - g.Xf[1],
+                                  (float)imin_image(z - g.Xi[2], lv.nz, lv.per[2]) - g.Xf[2], g.of, ip, kk);
+      int bo;
+      row_range(qn, 1.0f + ROW_EPS, g.Xf[0], ao, bo);
+      ao = max(ao, imin);
+      bo = min(bo, imax);
+      len = bo >= ao ? bo - ao + 1 : 0;
+    }
+    int tot;
+    const int off = block_scan(len, sh_w, &tot);
+    s_off[threadIdx.x] = off;
+    s_x0[threadIdx.x] = ao;
+    s_y[threadIdx.x] = y;
+    s_z[threadIdx.x] = z;
+    __syncthreads();
+    for (int kb = 0; kb < tot; kb += CB) {
+      const int k = kb + threadIdx.x;
+      unsigned lmask = 0u, cmask = 0u;
+      int xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
+      if (k < tot) {
+        // the row holding flattened node k: the last row starting at or before k
+        int lo = 0, hi = CB - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= k) lo = mid;
+          else hi = mid - 1;
+        }
+        int x = g.Xi[0] + s_x0[lo] + (k - s_off[lo]);
+        if (lv.per[0]) x = wrapi(x, lv.nx);
+        const int yy = s_y[lo], zz = s_z[lo];
+        xs[0] = x == 0 ? lv.nx - 1 : x - 1;
+        xs[1] = x;
+        xs[2] = x == lv.nx - 1 ? 0 : x + 1;
+        ys[0] = yy == 0 ? lv.ny - 1 : yy - 1;
+        ys[1] = yy;
+        ys[2] = yy == lv.ny - 1 ? 0 : yy + 1;
+        zs[0] = zz == 0 ? lv.nz - 1 : zz - 1;
+        zs[1] = zz;
+        zs[2] = zz == lv.nz - 1 ? 0 : zz + 1;
+        if (lv.owner[(unsigned)x + nx * (unsigned)yy + nxy * (unsigned)zz] == p) {
+          unsigned solid = 0, same = 0;
+          sfor<1, Q>([&](auto R) {
+            constexpr int r = decltype(R)::value;
+            const int on =
+                lv.owner[(unsigned)xs[1 + D::cx(r)] + nx * (unsigned)ys[1 + D::cy(r)] + nxy * (unsigned)zs[1 + D::cz(r)]];
+            solid |= (on != FLUID ? 1u : 0u) << r;
+            same |= (on == p ? 1u : 0u) << r;
+          });
+          lmask = NB_SOLID & ~solid;  // fluid neighbours
+          cmask = solid & ~same;      // other cells and walls
+        }
+      }
+      const int wtot = __reduce_add_sync(FULL, __popc(lmask));
+      if (wtot) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&s_len, wtot);
+        int run = __shfl_sync(FULL, base, 0);
+        sfor<1, Q>([&](auto R) {
+          constexpr int r = decltype(R)::value;
+          const bool has = (lmask >> r) & 1u;
+          const unsigned b = __ballot_sync(FULL, has);
+          if (has) {
+            const int pos = run + __popc(b & below);
+            if (pos < pv.lk_cap) lk[pos] = pack_xyzr(xs[1 + D::cx(r)], ys[1 + D::cy(r)], zs[1 + D::cz(r)], D::opp(r));
+          }
+          run += __popc(b);
+        });
+      }
+      if (cmask) {
+        const int di[3] = {imin_image(xs[1] - Xk[0], lv.nx, lv.per[0]), imin_image(ys[1] - Xk[1], lv.ny, lv.per[1]),
+                           imin_image(zs[1] - Xk[2], lv.nz, lv.per[2])};
+        sfor<1, Q>([&](auto R) {
+          constexpr int r = decltype(R)::value;
+          constexpr int m = D::m(r);
+          if ((cmask >> r) & 1u) {
+            ci[0] -= m * D::cx(r);
+            ci[1] -= m * D::cy(r);
+            ci[2] -= m * D::cz(r);
+            ci[3] -= m * (di[1] * D::cz(r) - di[2] * D::cy(r));
+            ci[4] -= m * (di[2] * D::cx(r) - di[0] * D::cz(r));
+            ci[5] -= m * (di[0] * D::cy(r) - di[1] * D::cx(r));
+          }
+        });
+      }
+    }
+    __syncthreads();  // the row tables are rewritten by the next chunk
+  }
+  block_sum_i<6>(ci, s_ci);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) {
+      pv.cK[3 * p + k] = ci[k];
+      pv.cIT[3 * p + k] = ci[3 + k];
+    }
+    pv.lk_count[p] = s_len;
+    if (s_len > pv.lk_cap) atomicOr(pv.status, ST_OVERFLOW);
+  }
+}
+
 // owners >= 0 become resting fluid (first particles_set), layout of parity par
 template <class S>
 __global__ void k_clear_cells(LatticeView lv, int par) {
@@ -1420,6 +1606,14 @@ void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const 
   if (pv.n == 0) return;
   k_claims<<<pv.n, CB, 0, st>>>(lv, pv, claim, chg, mode);
   *nl += 1;
+}
+
+void launch_geometry_step(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
+                          int64_t *nl) {
+  if (pv.n == 0) return;
+  k_nbm_update<<<4 * 152, 256, 0, st>>>(lv, chg);
+  k_cell_links<<<pv.n, CB, 0, st>>>(lv, pv);
+  *nl += 2;
 }
 
 void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, const CellListView &cl, int *claim,

@@ -175,16 +175,21 @@ void launch_links(const LatticeView &lv, int contact, int pass, int *block_count
 void launch_cell_list(const LatticeView &lv, const PartView &pv, const CellListView &cl, cudaStream_t st, int64_t *nl);
 void launch_forces(const LatticeView &lv, const PartView &pv, const CellListView &cl, const SurfBits &sb,
                    cudaStream_t st, int64_t *nl);
-void launch_cell_step(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st, int64_t *nl);
+// link sums and the implicit solve + leap-frog; then the link correction
+// (independent of the claims, which need only the solve)
+void launch_sums_solve(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st, int64_t *nl);
+void launch_link_correct(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st,
+                         int64_t *nl);
 void launch_set_state(const LatticeView &lv, const PartView &pv, int mode, cudaStream_t st, int64_t *nl);
 void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg, int mode,
                    cudaStream_t st, int64_t *nl);
 void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);
-// the geometry after a step's resolve: neighbour words around the changed
-// nodes, link lists and contact sums cell by cell (same result as
-// launch_geometry)
-void launch_geometry_step(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
-                          int64_t *nl);
+// the geometry after a step's resolve, in two independent parts (together
+// the same result as launch_geometry): neighbour words around the changed
+// nodes; link lists and contact sums cell by cell
+void launch_nbm_update(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
+                       int64_t *nl);
+void launch_cell_links(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);
 void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, const CellListView &cl, int *claim,
                          const ChangeList &chg, int par_next, int impulses, cudaStream_t st, int64_t *nl);
 void launch_clear_cells(int dtype, const LatticeView &lv, int par, cudaStream_t st, int64_t *nl);

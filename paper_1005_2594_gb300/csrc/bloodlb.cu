@@ -35,7 +35,9 @@ struct bl_ctx {
   // the cell list and the potentials of a step run on a second stream,
   // overlapped with the lattice sweep (they touch disjoint data)
   cudaStream_t side;
-  cudaEvent_t ev_fork, ev_join;
+  cudaEvent_t ev_fork, ev_join;     // cell list and potentials beside the sweep
+  cudaEvent_t ev_fork2, ev_join2;   // claims beside the link correction
+  cudaEvent_t ev_fork3, ev_join3;   // neighbour words beside the link lists
   // repeated steps replay a CUDA graph of two steps (even + odd parity) on
   // an internal stream, forked from and joined to the caller's stream
   cudaStream_t gstream;
@@ -229,7 +231,11 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork3, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming) != cudaSuccess) {
       rc = fail(c, BL_ECUDA, "streams");
       break;
     }
@@ -509,13 +515,33 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
   if (c->np > 0) {
     cudaStreamWaitEvent(st, c->ev_join, 0);
     group_begin(c, 3, &slot, st);
-    launch_cell_step(c->dtype, c->lv, c->pv, c->parity, st, &c->launches);
+    launch_sums_solve(c->dtype, c->lv, c->pv, c->parity, st, &c->launches);
     group_end(c, slot, st);
+    // the claims need only the solve: beside the link correction
+    cudaEventRecord(c->ev_fork2, st);
+    cudaStreamWaitEvent(c->side, c->ev_fork2, 0);
+    group_begin(c, 3, &slot, c->side);
+    launch_claims(c->lv, c->pv, c->claim, c->chg, 0, c->side, &c->launches);
+    group_end(c, slot, c->side);
+    cudaEventRecord(c->ev_join2, c->side);
+    group_begin(c, 3, &slot, st);
+    launch_link_correct(c->dtype, c->lv, c->pv, c->parity, st, &c->launches);
+    group_end(c, slot, st);
+    cudaStreamWaitEvent(st, c->ev_join2, 0);
     group_begin(c, 4, &slot, st);
-    launch_claims(c->lv, c->pv, c->claim, c->chg, 0, st, &c->launches);
     launch_resolve_fill(c->dtype, c->lv, c->pv, c->cl, c->claim, c->chg, c->parity ^ 1, 1, st, &c->launches);
-    launch_geometry_step(c->lv, c->pv, c->chg, st, &c->launches);
     group_end(c, slot, st);
+    // neighbour words beside the link lists
+    cudaEventRecord(c->ev_fork3, st);
+    cudaStreamWaitEvent(c->side, c->ev_fork3, 0);
+    group_begin(c, 4, &slot, c->side);
+    launch_nbm_update(c->lv, c->pv, c->chg, c->side, &c->launches);
+    group_end(c, slot, c->side);
+    cudaEventRecord(c->ev_join3, c->side);
+    group_begin(c, 4, &slot, st);
+    launch_cell_links(c->lv, c->pv, st, &c->launches);
+    group_end(c, slot, st);
+    cudaStreamWaitEvent(st, c->ev_join3, 0);
     std::swap(c->pv.kin, c->pv.kin_next);
   }
   c->parity ^= 1;
@@ -1014,6 +1040,8 @@ extern "C" void bl_destroy(bl_ctx *c) {
   if (c->gstream) cudaStreamDestroy(c->gstream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (cudaEvent_t e : {c->ev_fork2, c->ev_join2, c->ev_fork3, c->ev_join3})
+    if (e) cudaEventDestroy(e);
   free_particles(c);
   void *ptrs[] = {c->lv.pop, c->lv.owner, c->lv.rho_b, c->lv.nbm, c->claim, c->status, c->wacc.F, c->wacc.K,
                   c->sbits.bits, c->scratch};

@@ -945,16 +945,21 @@ constexpr float ROW_EPS = 2e-3f;
 // owned by another cell need no claim: their owner keeps them while it
 // covers them (first arrival), and hands them on through TOUCHED.
 // mode 1: no old ellipsoid (first particles_set, all owners fluid).
-// Also clears the cell's link count and contact sums for the geometry pass.
+// In particles_set (modes 1, 2) also clears the cell's link count and
+// contact sums for the lattice-wide geometry pass, which adds to them; in a
+// step (mode 0) the link correction may still be reading them, and the
+// step's geometry rewrites them.
 __global__ void __launch_bounds__(CB) k_claims(LatticeView lv, PartView pv, int *claim, ChangeList chg, int mode) {
   __shared__ int sh_len;
   const int p = blockIdx.x;
   if (threadIdx.x == 0) {
     sh_len = 0;
-    pv.lk_count[p] = 0;  // the geometry pass appends the links and adds the contact sums
-    for (int k = 0; k < 3; ++k) {
-      pv.cK[3 * p + k] = 0;
-      pv.cIT[3 * p + k] = 0;
+    if (mode != 0) {
+      pv.lk_count[p] = 0;
+      for (int k = 0; k < 3; ++k) {
+        pv.cK[3 * p + k] = 0;
+        pv.cIT[3 * p + k] = 0;
+      }
     }
     if (p == 0) *chg.count = 0;
   }
@@ -1564,20 +1569,28 @@ void launch_forces(const LatticeView &lv, const PartView &pv, const CellListView
 static unsigned link_chunks(const PartView &pv) { return (unsigned)((pv.lk_cap + CB - 1) / CB); }
 
 template <class S>
-static void cell_step_typed(const LatticeView &lv, const PartView &pv, int par, cudaStream_t st) {
+static void sums_solve_typed(const LatticeView &lv, const PartView &pv, int par, cudaStream_t st) {
   const dim3 grid_sum((unsigned)((pv.lk_cap + LCHUNK - 1) / LCHUNK), pv.n);
   k_link_sums<S><<<grid_sum, LT, 0, st>>>(lv, pv, par);
   k_solve<<<nblk(pv.n, 64), 64, 0, st>>>(lv, pv);
-  const dim3 grid(link_chunks(pv), pv.n);
-  k_link_correct<S><<<grid, CB, 0, st>>>(lv, pv, par);
 }
 
-void launch_cell_step(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st, int64_t *nl) {
+void launch_sums_solve(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  if (dtype == 0) cell_step_typed<float>(lv, pv, par, st);
-  else if (dtype == 1) cell_step_typed<__nv_bfloat16>(lv, pv, par, st);
-  else cell_step_typed<__half>(lv, pv, par, st);
-  *nl += 3;
+  if (dtype == 0) sums_solve_typed<float>(lv, pv, par, st);
+  else if (dtype == 1) sums_solve_typed<__nv_bfloat16>(lv, pv, par, st);
+  else sums_solve_typed<__half>(lv, pv, par, st);
+  *nl += 2;
+}
+
+void launch_link_correct(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st,
+                         int64_t *nl) {
+  if (pv.n == 0) return;
+  const dim3 grid(link_chunks(pv), pv.n);
+  if (dtype == 0) k_link_correct<float><<<grid, CB, 0, st>>>(lv, pv, par);
+  else if (dtype == 1) k_link_correct<__nv_bfloat16><<<grid, CB, 0, st>>>(lv, pv, par);
+  else k_link_correct<__half><<<grid, CB, 0, st>>>(lv, pv, par);
+  *nl += 1;
 }
 
 void launch_pair_features(const LatticeView &lv, const PartView &pv, const int2 *pairs, int n, float *out,
@@ -1608,12 +1621,17 @@ void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const 
   *nl += 1;
 }
 
-void launch_geometry_step(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
-                          int64_t *nl) {
+void launch_nbm_update(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
+                       int64_t *nl) {
   if (pv.n == 0) return;
   k_nbm_update<<<4 * 152, 256, 0, st>>>(lv, chg);
+  *nl += 1;
+}
+
+void launch_cell_links(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl) {
+  if (pv.n == 0) return;
   k_cell_links<<<pv.n, CB, 0, st>>>(lv, pv);
-  *nl += 2;
+  *nl += 1;
 }
 
 void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, const CellListView &cl, int *claim,

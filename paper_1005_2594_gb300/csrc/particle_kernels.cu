@@ -240,7 +240,7 @@ __device__ __forceinline__ void block_sum(float (&v)[K], float (*sh)[K]) {
   __syncthreads();
 }
 
-template <int K>
+template <int K, int NT = CB>
 __device__ __forceinline__ void block_sum_i(int (&v)[K], int (*sh)[K]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -250,7 +250,7 @@ __device__ __forceinline__ void block_sum_i(int (&v)[K], int (*sh)[K]) {
     for (int k = 0; k < K; ++k) sh[wid][k] = v[k];
   __syncthreads();
   if (threadIdx.x == 0)
-    for (int w = 1; w < CB / 32; ++w)
+    for (int w = 1; w < NT / 32; ++w)
 #pragma unroll
       for (int k = 0; k < K; ++k) v[k] += sh[w][k];
   __syncthreads();
@@ -258,6 +258,7 @@ __device__ __forceinline__ void block_sum_i(int (&v)[K], int (*sh)[K]) {
 
 // block-wide exclusive scan of one int per thread; returns the thread's
 // offset, writes the total to *total (all threads)
+template <int NT = CB>
 __device__ __forceinline__ int block_scan(int v, int *sh_w, int *total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int inc = v;
@@ -270,16 +271,16 @@ __device__ __forceinline__ int block_scan(int v, int *sh_w, int *total) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int s = 0;
-    for (int w = 0; w < CB / 32; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
       const int t = sh_w[w];
       sh_w[w] = s;
       s += t;
     }
-    sh_w[CB / 32] = s;
+    sh_w[NT / 32] = s;
   }
   __syncthreads();
   const int off = sh_w[wid] + inc - v;
-  *total = sh_w[CB / 32];
+  *total = sh_w[NT / 32];
   __syncthreads();
   return off;
 }
@@ -933,6 +934,8 @@ __device__ __forceinline__ void row_range(const RowQuad &q, float L, float xf, i
 // and nodes with s > 1 + ROW_EPS are outside.
 constexpr float ROW_EPS = 2e-3f;
 
+constexpr int PB = 128;  // threads of the claims and resolve blocks (8 blocks fit an SM)
+
 // Claims (one block per cell, one thread per lattice row of the cell's box).
 // A node's cover by cell p can change only where the old and the new
 // ellipsoid differ: on each row, the nodes of the hull of the two outer
@@ -949,7 +952,7 @@ constexpr float ROW_EPS = 2e-3f;
 // contact sums for the lattice-wide geometry pass, which adds to them; in a
 // step (mode 0) the link correction may still be reading them, and the
 // step's geometry rewrites them.
-__global__ void __launch_bounds__(CB) k_claims(LatticeView lv, PartView pv, int *claim, ChangeList chg, int mode) {
+__global__ void __launch_bounds__(PB) k_claims(LatticeView lv, PartView pv, int *claim, ChangeList chg, int mode) {
   __shared__ int sh_len;
   const int p = blockIdx.x;
   if (threadIdx.x == 0) {
@@ -988,7 +991,7 @@ __global__ void __launch_bounds__(CB) k_claims(LatticeView lv, PartView pv, int 
   const int imin = lv.per[0] ? -(lv.nx / 2) : -g.Xi[0];
   const int imax = lv.per[0] ? imin + lv.nx - 1 : lv.nx - 1 - g.Xi[0];
   unsigned long long *touched = pv.touched + (size_t)p * pv.touched_cap;
-  for (int t = threadIdx.x; t < rows; t += CB) {
+  for (int t = threadIdx.x; t < rows; t += PB) {
     int y = lo1 + t % by, z = lo2 + t / by;
     if (lv.per[1]) y = wrapi(y, lv.ny);
     if (lv.per[2]) z = wrapi(z, lv.nz);
@@ -1109,7 +1112,7 @@ __device__ __forceinline__ void atomic_add3(double *a, const double v[3]) {
 }
 
 template <class S>
-__global__ void __launch_bounds__(CB) k_resolve_fill(LatticeView lv, PartView pv, CellListView cl, int *claim,
+__global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv, CellListView cl, int *claim,
                                                       ChangeList chg, int par_next, int impulses) {
   using D = D3Q19;
   const int p = blockIdx.x;
@@ -1118,9 +1121,9 @@ __global__ void __launch_bounds__(CB) k_resolve_fill(LatticeView lv, PartView pv
   const int lane = threadIdx.x & 31;
   S *pop = reinterpret_cast<S *>(lv.pop);
   const int dims[3] = {lv.nx, lv.ny, lv.nz};
-  __shared__ int s_need[CB], s_res[CB];
+  __shared__ int s_need[PB], s_res[PB];
   __shared__ int s_ns;
-  for (int t0 = 0; t0 < nt; t0 += CB) {
+  for (int t0 = 0; t0 < nt; t0 += PB) {
     const int t = t0 + threadIdx.x;
     int old = 0, nw = 0, xyz[3] = {0, 0, 0};
     bool changed = false, act = false, need = false;
@@ -1148,7 +1151,7 @@ __global__ void __launch_bounds__(CB) k_resolve_fill(LatticeView lv, PartView pv
       }
     }
     __syncthreads();
-    for (int k = threadIdx.x >> 5; k < s_ns; k += CB / 32) {
+    for (int k = threadIdx.x >> 5; k < s_ns; k += PB / 32) {
       const int tt = s_need[k];
       int cc[3], r_unused;
       unpack_xyzr(touched[t0 + tt], cc, r_unused);
@@ -1293,13 +1296,15 @@ __global__ void k_nbm_update(LatticeView lv, ChangeList chg) {
 // its fluid neighbours (grouped by direction within a warp, so that the link
 // kernels read slots of one direction together) and adds its contact links
 // to exact integer sums
-__global__ void __launch_bounds__(CB) k_cell_links(LatticeView lv, PartView pv) {
+constexpr int LB = 128;  // threads of a link-list block (8 blocks fit an SM)
+
+__global__ void __launch_bounds__(LB) k_cell_links(LatticeView lv, PartView pv) {
   using D = D3Q19;
   const unsigned FULL = 0xffffffffu;
-  __shared__ int sh_w[CB / 32 + 1];
-  __shared__ int s_off[CB + 1], s_x0[CB], s_y[CB], s_z[CB];
+  __shared__ int sh_w[LB / 32 + 1];
+  __shared__ int s_off[LB + 1], s_x0[LB], s_y[LB], s_z[LB];
   __shared__ int s_len;
-  __shared__ int s_ci[CB / 32][6];
+  __shared__ int s_ci[LB / 32][6];
   const int p = blockIdx.x;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) s_len = 0;
@@ -1317,7 +1322,7 @@ __global__ void __launch_bounds__(CB) k_cell_links(LatticeView lv, PartView pv) 
   const unsigned below = (1u << lane) - 1u;
   const unsigned nx = (unsigned)lv.nx, nxy = (unsigned)lv.nx * (unsigned)lv.ny;
   int ci[6] = {0, 0, 0, 0, 0, 0};
-  for (int r0 = 0; r0 < rows; r0 += CB) {
+  for (int r0 = 0; r0 < rows; r0 += LB) {
     const int t = r0 + threadIdx.x;
     int len = 0, ao = 0, y = 0, z = 0;
     if (t < rows) {
@@ -1334,19 +1339,19 @@ __global__ void __launch_bounds__(CB) k_cell_links(LatticeView lv, PartView pv) 
       len = bo >= ao ? bo - ao + 1 : 0;
     }
     int tot;
-    const int off = block_scan(len, sh_w, &tot);
+    const int off = block_scan<LB>(len, sh_w, &tot);
     s_off[threadIdx.x] = off;
     s_x0[threadIdx.x] = ao;
     s_y[threadIdx.x] = y;
     s_z[threadIdx.x] = z;
     __syncthreads();
-    for (int kb = 0; kb < tot; kb += CB) {
+    for (int kb = 0; kb < tot; kb += LB) {
       const int k = kb + threadIdx.x;
       unsigned lmask = 0u, cmask = 0u;
       int xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
       if (k < tot) {
         // the row holding flattened node k: the last row starting at or before k
-        int lo = 0, hi = CB - 1;
+        int lo = 0, hi = LB - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
           if (s_off[mid] <= k) lo = mid;
@@ -1412,7 +1417,7 @@ __global__ void __launch_bounds__(CB) k_cell_links(LatticeView lv, PartView pv) 
     }
     __syncthreads();  // the row tables are rewritten by the next chunk
   }
-  block_sum_i<6>(ci, s_ci);
+  block_sum_i<6, LB>(ci, s_ci);
   if (threadIdx.x == 0) {
     for (int k = 0; k < 3; ++k) {
       pv.cK[3 * p + k] = ci[k];
@@ -1617,7 +1622,7 @@ void launch_set_state(const LatticeView &lv, const PartView &pv, int mode, cudaS
 void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg, int mode,
                    cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  k_claims<<<pv.n, CB, 0, st>>>(lv, pv, claim, chg, mode);
+  k_claims<<<pv.n, PB, 0, st>>>(lv, pv, claim, chg, mode);
   *nl += 1;
 }
 
@@ -1630,16 +1635,16 @@ void launch_nbm_update(const LatticeView &lv, const PartView &pv, const ChangeLi
 
 void launch_cell_links(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  k_cell_links<<<pv.n, CB, 0, st>>>(lv, pv);
+  k_cell_links<<<pv.n, LB, 0, st>>>(lv, pv);
   *nl += 1;
 }
 
 void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, const CellListView &cl, int *claim,
                          const ChangeList &chg, int par_next, int impulses, cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  if (dtype == 0) k_resolve_fill<float><<<pv.n, CB, 0, st>>>(lv, pv, cl, claim, chg, par_next, impulses);
-  else if (dtype == 1) k_resolve_fill<__nv_bfloat16><<<pv.n, CB, 0, st>>>(lv, pv, cl, claim, chg, par_next, impulses);
-  else k_resolve_fill<__half><<<pv.n, CB, 0, st>>>(lv, pv, cl, claim, chg, par_next, impulses);
+  if (dtype == 0) k_resolve_fill<float><<<pv.n, PB, 0, st>>>(lv, pv, cl, claim, chg, par_next, impulses);
+  else if (dtype == 1) k_resolve_fill<__nv_bfloat16><<<pv.n, PB, 0, st>>>(lv, pv, cl, claim, chg, par_next, impulses);
+  else k_resolve_fill<__half><<<pv.n, PB, 0, st>>>(lv, pv, cl, claim, chg, par_next, impulses);
   *nl += 1;
 }
 

@@ -164,6 +164,13 @@ def make_workload(name):
 SWEEP_TRAFFIC = {"sha": "e3b89d5a8bce7701", "config": "shear128", "store": 0, "bytes": 278206976}
 
 
+# the sweep kernel each storage type runs by default (FP32: variant 3 of the
+# library's sweep variants)
+SWEEP_KERNEL = {0: "k_lb_step_bulk (fused collide/stream/bounce-back, bulk-copy pipeline over 8 planes)",
+                1: "k_lb_step (fused collide/stream/bounce-back, one node per thread, BF16 store)",
+                2: "k_lb_step (fused collide/stream/bounce-back, one node per thread, FP16 store)"}
+
+
 def sweep_traffic(config, store):
     import hashlib
 
@@ -256,7 +263,7 @@ def run_gpu(args, ws, rank, local):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
                      "traffic": sweep_traffic(args.config, args.store), "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
-                     else "fallback 6.8 TB/s", "kernel": "k_lb_step (fused collide/stream/bounce-back)",
+                     else "fallback 6.8 TB/s", "kernel": SWEEP_KERNEL[args.store],
                      "bytes_per_launch": bytes_per, "launch_ms": round(k1_ms / max(k1_n, 1), 5)},
         "kernel_time_share": group_share,
         "instrumented": {"steps": k_inst, "ms_per_step": round(ms_inst / k_inst, 5),

@@ -204,6 +204,7 @@ void launch_mlp_forward_dev(const void *mlp, const float *x, const int *count, i
 // bit flags of the device status word
 constexpr int ST_UNSTABLE = 1;
 constexpr int ST_OVERFLOW = 2;
+constexpr int ST_BARRIER = 4;  // a bounded wait on an mbarrier gave up
 
 // ---------------------------------------------------------------------------
 // exact FP64 geometry (no contraction), matching the operation order of the

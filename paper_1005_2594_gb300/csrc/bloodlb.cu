@@ -217,7 +217,9 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
   lv.omega = (float)(1.0 / p->tau);
   lv.rho0 = (float)p->rho0;
   lv.has_force = 0;
-  lv.sweep = p->store_dtype == BL_STORE_F32 ? 1 : 0;  // FP32: the pipelined sweep over 4 planes
+  // FP32: the bulk-copy pipeline over 8 planes (rows of a multiple of 4
+  // nodes), else the pipeline over 4 planes
+  lv.sweep = p->store_dtype == BL_STORE_F32 ? (p->nx % 4 == 0 ? 3 : 1) : 0;
   for (int k = 0; k < 3; ++k) {
     lv.g[k] = (float)p->g[k];
     if (p->g[k] != 0.0) lv.has_force = 1;
@@ -613,6 +615,7 @@ static int read_status(bl_ctx *c) {
   CU(cudaStreamSynchronize(c->stream));
   if (st & ST_UNSTABLE) return fail(c, BL_EUNSTABLE, "unstable: rho <= 0, NaN or |u| >= 0.3 at some node, or a cell speed >= 0.5");
   if (st & ST_OVERFLOW) return fail(c, BL_EOVERFLOW, "internal list overflow");
+  if (st & ST_BARRIER) return fail(c, BL_EBARRIER, "a bounded wait for asynchronous copies timed out");
   return BL_OK;
 }
 
@@ -824,7 +827,7 @@ extern "C" int bl_autotune(bl_ctx *c, int trial_steps, int *choice) {
   if (!c || trial_steps < 2) return BL_EINVAL;
   if (c->sticky) return c->sticky;
   if (c->timing) return fail(c, BL_ESTATE, "bl_autotune with timing enabled");
-  const int nvar = c->dtype == BL_STORE_F32 ? 3 : 1;
+  const int nvar = c->dtype == BL_STORE_F32 ? (c->lv.nx % 4 == 0 ? 5 : 3) : 1;
   int best = 0;
   float best_ms = 0.f;
   cudaEvent_t a, b;
@@ -859,7 +862,7 @@ extern "C" int bl_autotune(bl_ctx *c, int trial_steps, int *choice) {
 }
 
 extern "C" int bl_sweep_variant(bl_ctx *c, int variant) {
-  if (!c || variant < 0 || variant > 2) return BL_EINVAL;
+  if (!c || variant < 0 || variant > 4) return BL_EINVAL;
   if (c->sticky) return c->sticky;
   if (variant != 0 && c->dtype != BL_STORE_F32) return BL_EINVAL;
   drop_graph(c);

@@ -165,54 +165,52 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
       f[rb] = relax(f[rb], w, E - O, -cu, -cF);
     });
     Store<S>::st(pop + n, f[0]);
-    if (solid == 0u) {
-      // no solid neighbour (most nodes): plain streaming
+    if (wall) {
+      // links into a wall (next to a wall only): the moving-wall term C for
+      // the population returning along rbar, 6 alpha_rbar rho c_rbar . v_wall,
+      // and the momentum the wall receives
       sfor<1, Q>([&](auto R) {
         constexpr int r = decltype(R)::value;
-        const unsigned dst = PAR == 0 ? (unsigned)D::opp(r) * N + n
-                                      : (unsigned)r * N + xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
-        Store<S>::st(pop + dst, f[r]);
-      });
-    } else {
-      sfor<1, Q>([&](auto R) {
-        constexpr int r = decltype(R)::value;
-        constexpr int rb = D::opp(r);
-        const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
-        if (!(solid & (1u << r))) {
-          const unsigned dst = PAR == 0 ? (unsigned)rb * N + n : (unsigned)r * N + nb;
-          Store<S>::st(pop + dst, f[r]);
-        } else {
-          // bounce-back into the slot where the next step reads direction rbar
-          const unsigned dst = PAR == 0 ? (unsigned)r * N + nb : (unsigned)rb * N + n;
-          float v = f[r];
-          if (wall & (1u << r)) {
-            const int w = -2 - lv.owner[nb];
-            // C for the population returning along rbar: 6 alpha_rbar rho c_rbar . v_wall
-            const float C = -(D::m(r) / 6.0f) * rho *
-                            (D::cx(r) * lv.wall_vel[w][0] + D::cy(r) * lv.wall_vel[w][1] + D::cz(r) * lv.wall_vel[w][2]);
-            v += C;
-            const float dp = 2.0f * f[r] + C;
-            if (wkey != w && wkey >= 0) {
-              // a node touching two different walls: flush the first one directly
-              for (int k = 0; k < 3; ++k) {
-                atomicAdd(&wa.F[3 * wkey + k], (double)wF[k]);
-                atomicAdd((unsigned long long *)&wa.K[3 * wkey + k], (unsigned long long)(long long)wK[k]);
-                wF[k] = 0.f;
-                wK[k] = 0;
-              }
+        if (wall & (1u << r)) {
+          const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
+          const int w = -2 - lv.owner[nb];
+          const float C = -(D::m(r) / 6.0f) * rho *
+                          (D::cx(r) * lv.wall_vel[w][0] + D::cy(r) * lv.wall_vel[w][1] + D::cz(r) * lv.wall_vel[w][2]);
+          const float dp = 2.0f * f[r] + C;
+          if (wkey != w && wkey >= 0) {
+            // a node touching two different walls: flush the first one directly
+            for (int k = 0; k < 3; ++k) {
+              atomicAdd(&wa.F[3 * wkey + k], (double)wF[k]);
+              atomicAdd((unsigned long long *)&wa.K[3 * wkey + k], (unsigned long long)(long long)wK[k]);
+              wF[k] = 0.f;
+              wK[k] = 0;
             }
-            wkey = w;
-            wF[0] += dp * D::cx(r);
-            wF[1] += dp * D::cy(r);
-            wF[2] += dp * D::cz(r);
-            wK[0] += D::m(r) * D::cx(r);
-            wK[1] += D::m(r) * D::cy(r);
-            wK[2] += D::m(r) * D::cz(r);
           }
-          Store<S>::st(pop + dst, v);
+          wkey = w;
+          wF[0] += dp * D::cx(r);
+          wF[1] += dp * D::cy(r);
+          wF[2] += dp * D::cz(r);
+          wK[0] += D::m(r) * D::cx(r);
+          wK[1] += D::m(r) * D::cy(r);
+          wK[2] += D::m(r) * D::cz(r);
+          f[r] += C;
         }
       });
     }
+    // streaming, or bounce-back into the slot where the next step reads
+    // direction rbar where the neighbour is solid: one store per direction,
+    // its slot chosen without a branch (so that a warp mixing open and
+    // boundary nodes writes each row of slots with one instruction)
+    //   parity 0: open -> [rbar][n],       solid -> [r][n + c_r]
+    //   parity 1: open -> [r][n + c_r],    solid -> [rbar][n]
+    sfor<1, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      constexpr int rb = D::opp(r);
+      const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
+      const bool sol = (solid >> r) & 1u;
+      const unsigned dst = (sol != (PAR == 1)) ? (unsigned)r * N + nb : (unsigned)rb * N + n;
+      Store<S>::st(pop + dst, f[r]);
+    });
     if (nbw & NB_CELL) lv.rho_b[n] = rho;
   }
 }
@@ -327,6 +325,133 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv
     for (int k = 0; k < PIPE_ST - 1; ++k) w[k] = w[k + 1];
   }
   cp_async_wait<0>();
+  flush_wall_momentum(wa, wkey, wF, wK);
+}
+
+// The FP32 sweep fed by bulk asynchronous copies (TMA, untiled): a block of
+// 128 threads takes a row segment of up to 128 nodes and ZC consecutive z
+// planes.  For each plane one thread copies the 19 source row segments and
+// the row of neighbour words into shared memory with cp.async.bulk, TS - 1
+// planes ahead of the plane being collided, each stage completing on its
+// mbarrier.  Parity 0 reads row (y, z) of array r; parity 1 reads row
+// (y - c_y, z - c_z) of array rbar, element x - c_x: from shared memory when
+// it lies in the segment (the whole row when the segment is the whole
+// periodic row), else directly from global memory.  Needs nx % 4 == 0 (16-byte
+// aligned rows); every wait is bounded (ST_BARRIER after ~2^26 polls).
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned phase) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+// bounded wait: false if the copies did not land within the limit
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phase) {
+  for (int it = 0; it < (1 << 26); ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+template <int PAR, bool FORCE, bool TAU1, int ZC, int TS>
+__global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc wa, int *status) {
+  using D = D3Q19;
+  __shared__ alignas(128) float sb[TS][Q + 1][128];  // [stage][array, Q = neighbour words][x]
+  __shared__ alignas(8) unsigned long long bar[TS];
+  __shared__ int s_ok;
+  const int nx = lv.nx, ny = lv.ny, nz = lv.nz;
+  const int tx = threadIdx.x;
+  const int x0 = blockIdx.x * 128;
+  const int W = min(128, nx - x0);  // segment width, a multiple of 4
+  const bool whole = W == nx;       // the segment is the whole row
+  const int y = blockIdx.y;
+  const int zb = blockIdx.z * ZC, ze = min(zb + ZC, nz);
+  const bool valid = tx < W;
+  const int x = x0 + (valid ? tx : W - 1);
+  const unsigned N = lv.N;
+  const unsigned nxy = (unsigned)nx * (unsigned)ny;
+  const unsigned xo[3] = {(unsigned)(x == 0 ? nx - 1 : x - 1), (unsigned)x, (unsigned)(x == nx - 1 ? 0 : x + 1)};
+  const unsigned yo[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1) * nx, (unsigned)y * nx,
+                          (unsigned)(y == ny - 1 ? 0 : y + 1) * nx};
+  const float *pop = reinterpret_cast<const float *>(lv.pop);
+  auto zoff = [&](int z, unsigned zo[3]) {
+    zo[0] = (unsigned)(z == 0 ? nz - 1 : z - 1) * nxy;
+    zo[1] = (unsigned)z * nxy;
+    zo[2] = (unsigned)(z == nz - 1 ? 0 : z + 1) * nxy;
+  };
+  // one thread: the copies of plane z into stage s
+  auto issue = [&](int z, int s) {
+    if (z >= ze) return;
+    unsigned zo[3];
+    zoff(z, zo);
+    const unsigned bytes = (unsigned)W * 4u;
+    mbar_expect_tx(&bar[s], (Q + 1) * bytes);
+    sfor<0, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      unsigned row;
+      if constexpr (PAR == 0 || r == 0) row = (unsigned)r * N + yo[1] + zo[1];
+      else row = (unsigned)D::opp(r) * N + yo[1 - D::cy(r)] + zo[1 - D::cz(r)];
+      bulk_g2s(&sb[s][r][0], pop + row + (unsigned)x0, bytes, &bar[s]);
+    });
+    bulk_g2s(&sb[s][Q][0], lv.nbm + yo[1] + zo[1] + (unsigned)x0, bytes, &bar[s]);
+  };
+  if (tx == 0) {
+    for (int k = 0; k < TS; ++k) mbar_init(&bar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_ok = 1;
+  }
+  __syncthreads();
+  if (tx == 0)
+    for (int k = 0; k < TS - 1; ++k) issue(zb + k, k);
+  int wkey = -1;
+  float wF[3] = {0.f, 0.f, 0.f};
+  int wK[3] = {0, 0, 0};
+  int z = zb;
+  for (; z < ze; ++z) {
+    const int i = z - zb, s = i % TS;
+    if (tx == 0) issue(z + TS - 1, (i + TS - 1) % TS);  // that stage was freed by the last barrier
+    if (!mbar_wait(&bar[s], (unsigned)(i / TS) & 1u)) {
+      atomicOr(status, ST_BARRIER);
+      s_ok = 0;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const uint32_t w = valid ? __float_as_uint(sb[s][Q][tx]) : 0u;
+    if (w & NB_FLUID) {
+      unsigned zo[3];
+      zoff(z, zo);
+      node_update<float, PAR, FORCE, TAU1>(
+          lv, wa, status, (unsigned)x + yo[1] + zo[1], xo, yo, zo, w,
+          [&](int r, unsigned slot) {
+            if (PAR == 0 || r == 0) return sb[s][r][tx];
+            int j = tx - D::cx(r);
+            if (whole) j = j < 0 ? j + W : (j >= W ? j - W : j);
+            return (j >= 0 && j < W) ? sb[s][r][j] : pop[slot];
+          },
+          wkey, wF, wK);
+    }
+    __syncthreads();  // stage s is read: free for refill
+  }
+  if (z < ze && tx == 0) {
+    // gave up: let the copies still in flight land before the block exits
+    for (int k = 0; k < TS; ++k) mbar_wait(&bar[k], 0u), mbar_wait(&bar[k], 1u);
+  }
   flush_wall_momentum(wa, wkey, wF, wK);
 }
 
@@ -640,14 +765,26 @@ static void launch_pipe(const LatticeView &lv, dim3 grid, dim3 block, const Wall
   k_lb_step_pipe<PAR, FORCE, TAU1, ZC><<<gp, block, 0, st>>>(lv, wa, status);
 }
 
+template <int PAR, bool FORCE, bool TAU1, int ZC, int TS>
+static void launch_bulk(const LatticeView &lv, dim3 grid, const WallAcc &wa, int *status, cudaStream_t st) {
+  const dim3 gp((lv.nx + 127) / 128, grid.y, (grid.z + ZC - 1) / ZC);
+  k_lb_step_bulk<PAR, FORCE, TAU1, ZC, TS><<<gp, 128, 0, st>>>(lv, wa, status);
+}
+
 // sweep variants (LatticeView::sweep): 0 one node per thread; 1, 2 the FP32
-// pipeline over 4 or 8 planes (BF16 / FP16 storage always take variant 0)
+// pipeline over 4 or 8 planes; 3, 4 the FP32 bulk-copy pipeline over 8 or 4
+// planes with 3 stages (nx % 4 == 0, else variant 0).  BF16 / FP16 storage always take
+// variant 0.
 template <class S, int PAR, bool FORCE, bool TAU1>
 static void launch_lb_variant(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
                               cudaStream_t st) {
   if constexpr (std::is_same<S, float>::value) {
     if (lv.sweep == 1) return launch_pipe<PAR, FORCE, TAU1, 4>(lv, grid, block, wa, status, st);
     if (lv.sweep == 2) return launch_pipe<PAR, FORCE, TAU1, 8>(lv, grid, block, wa, status, st);
+    if (lv.nx % 4 == 0) {
+      if (lv.sweep == 3) return launch_bulk<PAR, FORCE, TAU1, 8, 3>(lv, grid, wa, status, st);
+      if (lv.sweep == 4) return launch_bulk<PAR, FORCE, TAU1, 4, 3>(lv, grid, wa, status, st);
+    }
   }
   k_lb_step<S, PAR, FORCE, TAU1><<<grid, block, 0, st>>>(lv, wa, status);
 }

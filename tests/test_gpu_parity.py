@@ -341,7 +341,10 @@ def test_full_size_shear_cell_owner_map_and_one_step():
 def test_graph_replay_matches_single_steps():
     """Repeated steps replay a captured two-step graph; the result must match
     the same steps enqueued one by one (owner maps exactly; fields and cell
-    state to FP32 round-off, since float atomics may add in another order)."""
+    state to FP32 round-off, since float atomics may add in another order).
+    Force and torque are sums of many link terms that cancel to a small net
+    value, so the same round-off is larger relative to them: 1e-5, the bar of
+    the oracle parity, against 1e-6 for the integrated state."""
     oracle, bl, workloads = _mods()
     p, X, q, V, L = _coupled(0.0, seed=1011)
     a, b = bl.Simulation(p), bl.Simulation(p)
@@ -355,19 +358,23 @@ def test_graph_replay_matches_single_steps():
     b.sync()
     np.testing.assert_array_equal(a.owner(), b.owner())
     pa, pb = a.particles(), b.particles()
-    for k in ("X", "q", "V", "L", "F", "T"):
+    for k in ("X", "q", "V", "L"):
         assert rel(pb[k], pa[k]) < 1e-6, k
+    for k in ("F", "T"):
+        assert rel(pb[k], pa[k]) < 1e-5, k
     ra, ua, _ = a.fields()
     rb, ub, _ = b.fields()
     assert rel(ub, ua) < 1e-6 and rel(rb - 1.0, ra - 1.0) < 1e-5
 
 
 def test_sweep_variants_agree():
-    """The three thread mappings of the FP32 sweep compute the same step."""
+    """The thread mappings of the FP32 sweep (one node per thread, the two
+    pipelines with per-thread copies, the two bulk-copy pipelines) compute
+    the same step; here each row is one whole periodic segment."""
     oracle, bl, workloads = _mods()
     p, X, q, V, L = _coupled(0.0, seed=1021)
     sims = []
-    for v in (0, 1, 2):
+    for v in (0, 1, 2, 3, 4):
         s = bl.Simulation(p)
         s.sweep_variant(v)
         s.set_particles(X, q, V, L)
@@ -375,12 +382,39 @@ def test_sweep_variants_agree():
         s.sync()
         sims.append(s)
     ref = sims[1]
-    for s in (sims[0], sims[2]):
+    for s in sims[:1] + sims[2:]:
         np.testing.assert_array_equal(s.owner(), ref.owner())
         assert rel(s.particles()["X"], ref.particles()["X"]) < 1e-6
         assert rel(s.fields()[1], ref.fields()[1]) < 1e-6
     with pytest.raises(bl.BloodLBError):
         bl.Simulation(p, store_dtype=1).sweep_variant(1)  # the pipeline is FP32 only
+
+
+def test_bulk_sweep_on_split_rows_with_forcing():
+    """Rows longer than one 128-node segment (the segment edges read their
+    shifted neighbours from global memory), a body force and tau != 1: the
+    bulk-copy sweeps equal the one-node-per-thread sweep; a row length that
+    is not a multiple of 4 falls back to it."""
+    oracle, bl, workloads = _mods()
+    for nx in (136, 30):
+        p = workloads.base_params(nx, 14, 12, periodic=(1, 1, 0), R=(3.5, 1.5), g=(2e-5, 1e-5, 0.0),
+                                  wall_vel={4: (-0.01, 0.0, 0.0), 5: (0.01, 0.0, 0.0)})
+        p["tau"] = 0.8
+        X, q, _ = workloads.pack_cells(p, 12, 5)
+        sims = []
+        for v in (0, 3, 4):
+            s = bl.Simulation(p)
+            s.sweep_variant(v)
+            s.set_particles(X, q)
+            s.step(12)
+            s.sync()
+            sims.append(s)
+        for s in sims[1:]:
+            np.testing.assert_array_equal(s.owner(), sims[0].owner())
+            assert rel(s.particles()["X"], sims[0].particles()["X"]) < 1e-6
+            assert rel(s.fields()[1], sims[0].fields()[1]) < 1e-6
+        for s in sims:
+            s.close()
 
 
 def test_ensemble_matches_members_stepped_alone():
@@ -415,6 +449,6 @@ def test_autotune_keeps_a_valid_variant():
     s = bl.Simulation(p)
     s.set_particles(X, q, V, L)
     choice = s.autotune(6)
-    assert choice in (0, 1, 2)
+    assert choice in (0, 1, 2, 3, 4)
     s.step(4)
     s.sync()

@@ -217,9 +217,11 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
   lv.omega = (float)(1.0 / p->tau);
   lv.rho0 = (float)p->rho0;
   lv.has_force = 0;
-  // FP32: the bulk-copy pipeline over 8 planes (rows of a multiple of 4
-  // nodes), else the pipeline over 4 planes
-  lv.sweep = p->store_dtype == BL_STORE_F32 ? (p->nx % 4 == 0 ? 3 : 1) : 0;
+  // the bulk-copy pipeline over 8 planes where rows are 16-byte aligned (nx a
+  // multiple of 4 in FP32, of 8 in BF16 / FP16); else FP32 takes the pipeline
+  // over 4 planes and 16-bit storage one node per thread
+  if (p->store_dtype == BL_STORE_F32) lv.sweep = p->nx % 4 == 0 ? 3 : 1;
+  else lv.sweep = p->nx % 8 == 0 ? 3 : 0;
   for (int k = 0; k < 3; ++k) {
     lv.g[k] = (float)p->g[k];
     if (p->g[k] != 0.0) lv.has_force = 1;
@@ -827,14 +829,25 @@ extern "C" int bl_autotune(bl_ctx *c, int trial_steps, int *choice) {
   if (!c || trial_steps < 2) return BL_EINVAL;
   if (c->sticky) return c->sticky;
   if (c->timing) return fail(c, BL_ESTATE, "bl_autotune with timing enabled");
-  const int nvar = c->dtype == BL_STORE_F32 ? (c->lv.nx % 4 == 0 ? 5 : 3) : 1;
+  // candidate variants the storage type and the row length allow
+  int cand[5], nvar = 0;
+  cand[nvar++] = 0;
+  if (c->dtype == BL_STORE_F32) {
+    cand[nvar++] = 1;
+    cand[nvar++] = 2;
+  }
+  if (c->lv.nx % (c->dtype == BL_STORE_F32 ? 4 : 8) == 0) {
+    cand[nvar++] = 3;
+    cand[nvar++] = 4;
+  }
   int best = 0;
   float best_ms = 0.f;
   cudaEvent_t a, b;
   CU(cudaEventCreate(&a));
   CU(cudaEventCreate(&b));
   int rc = BL_OK;
-  for (int v = 0; v < nvar && rc == BL_OK; ++v) {
+  for (int iv = 0; iv < nvar && rc == BL_OK; ++iv) {
+    const int v = cand[iv];
     drop_graph(c);  // the graph holds the lattice view, variant included
     c->lv.sweep = v;
     if ((rc = bl_step(c, 2)) != BL_OK) break;  // capture + warm-up
@@ -847,7 +860,7 @@ extern "C" int bl_autotune(bl_ctx *c, int trial_steps, int *choice) {
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);
-    if (v == 0 || ms < best_ms) {
+    if (iv == 0 || ms < best_ms) {
       best = v;
       best_ms = ms;
     }
@@ -864,7 +877,7 @@ extern "C" int bl_autotune(bl_ctx *c, int trial_steps, int *choice) {
 extern "C" int bl_sweep_variant(bl_ctx *c, int variant) {
   if (!c || variant < 0 || variant > 4) return BL_EINVAL;
   if (c->sticky) return c->sticky;
-  if (variant != 0 && c->dtype != BL_STORE_F32) return BL_EINVAL;
+  if ((variant == 1 || variant == 2) && c->dtype != BL_STORE_F32) return BL_EINVAL;
   drop_graph(c);
   c->lv.sweep = variant;
   return BL_OK;

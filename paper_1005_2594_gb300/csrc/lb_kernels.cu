@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv
   flush_wall_momentum(wa, wkey, wF, wK);
 }
 
-// The FP32 sweep fed by bulk asynchronous copies (TMA, untiled): a block of
+// The sweep fed by bulk asynchronous copies (TMA, untiled): a block of
 // 128 threads takes a row segment of up to 128 nodes and ZC consecutive z
 // planes.  For each plane one thread copies the 19 source row segments and
 // the row of neighbour words into shared memory with cp.async.bulk, TS - 1
@@ -336,8 +336,9 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv
 // mbarrier.  Parity 0 reads row (y, z) of array r; parity 1 reads row
 // (y - c_y, z - c_z) of array rbar, element x - c_x: from shared memory when
 // it lies in the segment (the whole row when the segment is the whole
-// periodic row), else directly from global memory.  Needs nx % 4 == 0 (16-byte
-// aligned rows); every wait is bounded (ST_BARRIER after ~2^26 polls).
+// periodic row), else directly from global memory.  Needs 16-byte aligned
+// rows: nx % 4 == 0 for FP32 storage, nx % 8 == 0 for BF16 / FP16; every
+// wait is bounded (ST_BARRIER after ~2^26 polls).
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -369,10 +370,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                : "memory");
 }
 
-template <int PAR, bool FORCE, bool TAU1, int ZC, int TS>
+template <class S, int PAR, bool FORCE, bool TAU1, int ZC, int TS>
 __global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc wa, int *status) {
   using D = D3Q19;
-  __shared__ alignas(128) float sb[TS][Q + 1][128];  // [stage][array, Q = neighbour words][x]
+  __shared__ alignas(128) S sb[TS][Q][128];        // [stage][array][x]
+  __shared__ alignas(128) uint32_t sw[TS][128];    // [stage][x] neighbour words
   __shared__ alignas(8) unsigned long long bar[TS];
   __shared__ int s_ok;
   const int nx = lv.nx, ny = lv.ny, nz = lv.nz;
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc
   const unsigned xo[3] = {(unsigned)(x == 0 ? nx - 1 : x - 1), (unsigned)x, (unsigned)(x == nx - 1 ? 0 : x + 1)};
   const unsigned yo[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1) * nx, (unsigned)y * nx,
                           (unsigned)(y == ny - 1 ? 0 : y + 1) * nx};
-  const float *pop = reinterpret_cast<const float *>(lv.pop);
+  const S *pop = reinterpret_cast<const S *>(lv.pop);
   auto zoff = [&](int z, unsigned zo[3]) {
     zo[0] = (unsigned)(z == 0 ? nz - 1 : z - 1) * nxy;
     zo[1] = (unsigned)z * nxy;
@@ -400,8 +402,8 @@ __global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc
     if (z >= ze) return;
     unsigned zo[3];
     zoff(z, zo);
-    const unsigned bytes = (unsigned)W * 4u;
-    mbar_expect_tx(&bar[s], (Q + 1) * bytes);
+    const unsigned bytes = (unsigned)W * (unsigned)sizeof(S);
+    mbar_expect_tx(&bar[s], Q * bytes + (unsigned)W * 4u);
     sfor<0, Q>([&](auto R) {
       constexpr int r = decltype(R)::value;
       unsigned row;
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc
       else row = (unsigned)D::opp(r) * N + yo[1 - D::cy(r)] + zo[1 - D::cz(r)];
       bulk_g2s(&sb[s][r][0], pop + row + (unsigned)x0, bytes, &bar[s]);
     });
-    bulk_g2s(&sb[s][Q][0], lv.nbm + yo[1] + zo[1] + (unsigned)x0, bytes, &bar[s]);
+    bulk_g2s(&sw[s][0], lv.nbm + yo[1] + zo[1] + (unsigned)x0, (unsigned)W * 4u, &bar[s]);
   };
   if (tx == 0) {
     for (int k = 0; k < TS; ++k) mbar_init(&bar[k], 1);
@@ -432,17 +434,17 @@ __global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc
     }
     __syncthreads();
     if (!s_ok) break;
-    const uint32_t w = valid ? __float_as_uint(sb[s][Q][tx]) : 0u;
+    const uint32_t w = valid ? sw[s][tx] : 0u;
     if (w & NB_FLUID) {
       unsigned zo[3];
       zoff(z, zo);
-      node_update<float, PAR, FORCE, TAU1>(
+      node_update<S, PAR, FORCE, TAU1>(
           lv, wa, status, (unsigned)x + yo[1] + zo[1], xo, yo, zo, w,
-          [&](int r, unsigned slot) {
-            if (PAR == 0 || r == 0) return sb[s][r][tx];
+          [&](int r, unsigned slot) -> float {
+            if (PAR == 0 || r == 0) return Store<S>::ld(&sb[s][r][tx]);
             int j = tx - D::cx(r);
             if (whole) j = j < 0 ? j + W : (j >= W ? j - W : j);
-            return (j >= 0 && j < W) ? sb[s][r][j] : pop[slot];
+            return (j >= 0 && j < W) ? Store<S>::ld(&sb[s][r][j]) : Store<S>::ld(pop + slot);
           },
           wkey, wF, wK);
     }
@@ -765,26 +767,28 @@ static void launch_pipe(const LatticeView &lv, dim3 grid, dim3 block, const Wall
   k_lb_step_pipe<PAR, FORCE, TAU1, ZC><<<gp, block, 0, st>>>(lv, wa, status);
 }
 
-template <int PAR, bool FORCE, bool TAU1, int ZC, int TS>
+template <class S, int PAR, bool FORCE, bool TAU1, int ZC, int TS>
 static void launch_bulk(const LatticeView &lv, dim3 grid, const WallAcc &wa, int *status, cudaStream_t st) {
   const dim3 gp((lv.nx + 127) / 128, grid.y, (grid.z + ZC - 1) / ZC);
-  k_lb_step_bulk<PAR, FORCE, TAU1, ZC, TS><<<gp, 128, 0, st>>>(lv, wa, status);
+  k_lb_step_bulk<S, PAR, FORCE, TAU1, ZC, TS><<<gp, 128, 0, st>>>(lv, wa, status);
 }
 
+// row length for the bulk-copy sweep: 16-byte aligned rows of the storage type
+__host__ __device__ inline bool bulk_rows_ok(int nx, int store_bytes) { return nx % (16 / store_bytes) == 0; }
+
 // sweep variants (LatticeView::sweep): 0 one node per thread; 1, 2 the FP32
-// pipeline over 4 or 8 planes; 3, 4 the FP32 bulk-copy pipeline over 8 or 4
-// planes with 3 stages (nx % 4 == 0, else variant 0).  BF16 / FP16 storage always take
-// variant 0.
+// pipeline over 4 or 8 planes; 3, 4 the bulk-copy pipeline over 8 or 4 planes
+// with 3 stages (any storage type with 16-byte aligned rows, else variant 0)
 template <class S, int PAR, bool FORCE, bool TAU1>
 static void launch_lb_variant(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
                               cudaStream_t st) {
   if constexpr (std::is_same<S, float>::value) {
     if (lv.sweep == 1) return launch_pipe<PAR, FORCE, TAU1, 4>(lv, grid, block, wa, status, st);
     if (lv.sweep == 2) return launch_pipe<PAR, FORCE, TAU1, 8>(lv, grid, block, wa, status, st);
-    if (lv.nx % 4 == 0) {
-      if (lv.sweep == 3) return launch_bulk<PAR, FORCE, TAU1, 8, 3>(lv, grid, wa, status, st);
-      if (lv.sweep == 4) return launch_bulk<PAR, FORCE, TAU1, 4, 3>(lv, grid, wa, status, st);
-    }
+  }
+  if (bulk_rows_ok(lv.nx, (int)sizeof(S))) {
+    if (lv.sweep == 3) return launch_bulk<S, PAR, FORCE, TAU1, 8, 3>(lv, grid, wa, status, st);
+    if (lv.sweep == 4) return launch_bulk<S, PAR, FORCE, TAU1, 4, 3>(lv, grid, wa, status, st);
   }
   k_lb_step<S, PAR, FORCE, TAU1><<<grid, block, 0, st>>>(lv, wa, status);
 }

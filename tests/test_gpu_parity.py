@@ -390,6 +390,38 @@ def test_sweep_variants_agree():
         bl.Simulation(p, store_dtype=1).sweep_variant(1)  # the pipeline is FP32 only
 
 
+def test_bulk_sweep_with_16bit_storage():
+    """BF16 and FP16 storage: the bulk-copy sweep (2-byte rows) computes what
+    the one-node-per-thread sweep computes.  Without cells nothing but the
+    sweep touches the fields: equal to 1e-6.  With cells, float atomics in
+    the cell sums add in a timing-dependent order, and a last-bit change of
+    a cell velocity can move a stored 16-bit population by one unit of its
+    last place: owner maps exact, cell positions to 1e-6, fields to the
+    storage precision (2^-8 BF16, 2^-11 FP16)."""
+    oracle, bl, workloads = _mods()
+    p, X, q, V, L = _coupled(0.0, seed=1011)
+    for dtype, tol in ((1, 2.0 ** -8), (2, 2.0 ** -11)):
+        for cells in (False, True):
+            sims = []
+            for v in (0, 3):
+                s = bl.Simulation(p, store_dtype=dtype)
+                s.sweep_variant(v)
+                if cells:
+                    s.set_particles(X, q, V, L)
+                s.step(12)
+                s.sync()
+                sims.append(s)
+            np.testing.assert_array_equal(sims[1].owner(), sims[0].owner())
+            u1, u0 = sims[1].fields()[1], sims[0].fields()[1]
+            if cells:
+                assert rel(sims[1].particles()["X"], sims[0].particles()["X"]) < 1e-6
+                assert rel(u1, u0) < tol, (dtype, rel(u1, u0))
+            else:
+                assert rel(u1, u0) < 1e-6, (dtype, rel(u1, u0))
+            for s in sims:
+                s.close()
+
+
 def test_bulk_sweep_on_split_rows_with_forcing():
     """Rows longer than one 128-node segment (the segment edges read their
     shifted neighbours from global memory), a body force and tau != 1: the

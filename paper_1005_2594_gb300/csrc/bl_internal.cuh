@@ -186,7 +186,8 @@ void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const 
 void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);
 // the geometry after a step's resolve, in two independent parts (together
 // the same result as launch_geometry): neighbour words around the changed
-// nodes; link lists and contact sums cell by cell
+// nodes (after resolve); link lists and contact sums cell by cell from the
+// current owner map and kinematics (at the start of the next step)
 void launch_nbm_update(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
                        int64_t *nl);
 void launch_cell_links(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);

@@ -37,7 +37,8 @@ struct bl_ctx {
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;     // cell list and potentials beside the sweep
   cudaEvent_t ev_fork2, ev_join2;   // claims beside the link correction
-  cudaEvent_t ev_fork3, ev_join3;   // neighbour words beside the link lists
+  cudaStream_t side2;
+  cudaEvent_t ev_join3;             // link lists beside the sweep (second side stream)
   // repeated steps replay a CUDA graph of two steps (even + odd parity) on
   // an internal stream, forked from and joined to the caller's stream
   cudaStream_t gstream;
@@ -238,7 +239,7 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_fork3, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming) != cudaSuccess) {
       rc = fail(c, BL_ECUDA, "streams");
       break;
@@ -500,9 +501,15 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
 static int enqueue_step(bl_ctx *c, cudaStream_t st) {
   int slot;
   if (c->np > 0) {
-    // cell list and potentials from the state at t, beside the sweep
+    // cell list and potentials from the state at t, beside the sweep; on a
+    // second side stream the link lists of the current owner map
     cudaEventRecord(c->ev_fork, st);
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    cudaStreamWaitEvent(c->side2, c->ev_fork, 0);
+    group_begin(c, 4, &slot, c->side2);
+    launch_cell_links(c->lv, c->pv, c->side2, &c->launches);
+    group_end(c, slot, c->side2);
+    cudaEventRecord(c->ev_join3, c->side2);
     group_begin(c, 1, &slot, c->side);
     launch_cell_list(c->lv, c->pv, c->cl, c->side, &c->launches);
     group_end(c, slot, c->side);
@@ -518,6 +525,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
   c->launches++;
   if (c->np > 0) {
     cudaStreamWaitEvent(st, c->ev_join, 0);
+    cudaStreamWaitEvent(st, c->ev_join3, 0);
     group_begin(c, 3, &slot, st);
     launch_sums_solve(c->dtype, c->lv, c->pv, c->parity, st, &c->launches);
     group_end(c, slot, st);
@@ -534,18 +542,8 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     cudaStreamWaitEvent(st, c->ev_join2, 0);
     group_begin(c, 4, &slot, st);
     launch_resolve_fill(c->dtype, c->lv, c->pv, c->cl, c->claim, c->chg, c->parity ^ 1, 1, st, &c->launches);
+    launch_nbm_update(c->lv, c->pv, c->chg, st, &c->launches);
     group_end(c, slot, st);
-    // neighbour words beside the link lists
-    cudaEventRecord(c->ev_fork3, st);
-    cudaStreamWaitEvent(c->side, c->ev_fork3, 0);
-    group_begin(c, 4, &slot, c->side);
-    launch_nbm_update(c->lv, c->pv, c->chg, c->side, &c->launches);
-    group_end(c, slot, c->side);
-    cudaEventRecord(c->ev_join3, c->side);
-    group_begin(c, 4, &slot, st);
-    launch_cell_links(c->lv, c->pv, st, &c->launches);
-    group_end(c, slot, st);
-    cudaStreamWaitEvent(st, c->ev_join3, 0);
     std::swap(c->pv.kin, c->pv.kin_next);
   }
   c->parity ^= 1;
@@ -1056,8 +1054,9 @@ extern "C" void bl_destroy(bl_ctx *c) {
   if (c->gstream) cudaStreamDestroy(c->gstream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
-  for (cudaEvent_t e : {c->ev_fork2, c->ev_join2, c->ev_fork3, c->ev_join3})
+  for (cudaEvent_t e : {c->ev_fork2, c->ev_join2, c->ev_join3})
     if (e) cudaEventDestroy(e);
+  if (c->side2) cudaStreamDestroy(c->side2);
   free_particles(c);
   void *ptrs[] = {c->lv.pop, c->lv.owner, c->lv.rho_b, c->lv.nbm, c->claim, c->status, c->wacc.F, c->wacc.K,
                   c->sbits.bits, c->scratch};

@@ -1245,7 +1245,9 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
 // word can differ from the last one only if its own owner or a neighbour's
 // changed, and every change is in the change list; the link lists and
 // contact sums of a cell come from the nodes it owns, which lie inside its
-// ellipsoid at X(t+1) (a cell owns only nodes it covers).
+// ellipsoid at its current position (a cell owns only nodes it covers).
+// The link lists are built at the start of the next step, beside its sweep
+// (the sweep needs only the neighbour words), from the current kinematics.
 
 // neighbour word of node (x, y, z) from the owner map: bit 0 fluid, bit r
 // neighbour x + c_r solid, NB_WALL / NB_CELL some solid neighbour is a wall /
@@ -1316,7 +1318,7 @@ __global__ void __launch_bounds__(LB) k_cell_links(LatticeView lv, PartView pv) 
   const float ip = (float)pv.inv_rperp2, kk = (float)(pv.inv_rpar2 - pv.inv_rperp2);
   const int imin = lv.per[0] ? -(lv.nx / 2) : -g.Xi[0];
   const int imax = lv.per[0] ? imin + lv.nx - 1 : lv.nx - 1 - g.Xi[0];
-  const float4 k0 = pv.kin_next[3 * p], k1 = pv.kin_next[3 * p + 1], k2 = pv.kin_next[3 * p + 2];
+  const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
   const int Xk[3] = {(int)k0.w, (int)k1.w, (int)k2.w};
   unsigned long long *lk = pv.lk + (size_t)p * pv.lk_cap;
   const unsigned below = (1u << lane) - 1u;

@@ -356,7 +356,8 @@ def run_learned(args, ws, rank, local):
     the library on approach runs it generates (coarse and 2x resolution),
     its error is measured on held-out approach runs against the 2x and 4x
     runs, and the tube workload is timed without and with the network
-    attached (gap cut-off 2 lattice units)."""
+    attached for pairs from the smallest trained gap up to 2 lattice units
+    (closer pairs keep the plain method)."""
     import torch
 
     import __graft_entry__
@@ -392,7 +393,8 @@ def run_learned(args, ws, rank, local):
     clocks = ClockSampler(local)
     for mode in ("plain", "learned"):
         if mode == "learned":
-            bl.bl_mlp_attach(sim.ctx, m, 2.0)
+            # the trained gaps from below, up to the cut-off; closer pairs keep the plain method
+            bl.bl_mlp_attach_range(sim.ctx, m, info["gap_min"], 2.0)
         sim.step(args.warmup)
         sim.sync()
         l0 = bl.bl_launch_count(sim.ctx)
@@ -421,7 +423,7 @@ def run_learned(args, ws, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
         "data": "synthetic (jittered fcc start, resting plasma; network trained on generated approach runs)",
         "config": {"workload": desc, "lattice": [p["nx"], p["ny"], p["nz"]], "cells": int(len(Xc)),
-                   "fluid_nodes": fluid, "gap_cut": 2.0, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "fluid_nodes": fluid, "gap_range": [round(info["gap_min"], 3), 2.0], "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "populations %.0f MB > 129 MB L2, no flush" % (N * 19 * 4 / 1e6)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None,

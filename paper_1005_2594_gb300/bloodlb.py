@@ -36,7 +36,7 @@ ABI_FUNCTIONS = (
     "bl_boundary_links_get", "bl_contact_links_get", "bl_cell_list_get", "bl_cell_list_build_static",
     "bl_sweep_variant", "bl_autotune", "bl_ensemble_create", "bl_ensemble_step", "bl_ensemble_sync",
     "bl_ensemble_destroy", "bl_mlp_create", "bl_mlp_params_set", "bl_mlp_params_get", "bl_mlp_forward",
-    "bl_mlp_grad", "bl_mlp_adam", "bl_mlp_sync", "bl_mlp_destroy", "bl_mlp_attach", "bl_pair_features",
+    "bl_mlp_grad", "bl_mlp_adam", "bl_mlp_sync", "bl_mlp_destroy", "bl_mlp_attach", "bl_mlp_attach_range", "bl_pair_features",
     "bl_timing_enable",
     "bl_timing_read", "bl_launch_count", "bl_sync", "bl_last_error", "bl_destroy",
 )
@@ -115,6 +115,7 @@ def lib():
         "bl_mlp_sync": (ctypes.c_int, [vp]),
         "bl_mlp_destroy": (None, [vp]),
         "bl_mlp_attach": (ctypes.c_int, [vp, vp, ctypes.c_double]),
+        "bl_mlp_attach_range": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double]),
         "bl_pair_features": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         "bl_timing_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "bl_timing_read": (ctypes.c_int, [vp, D, ctypes.POINTER(i64), ctypes.c_int]),
@@ -310,6 +311,10 @@ def bl_mlp_destroy(m):
 
 def bl_mlp_attach(ctx, m, gap_cut):
     return _check(ctx, lib().bl_mlp_attach(ctx, m, float(gap_cut)))
+
+
+def bl_mlp_attach_range(ctx, m, gap_lo, gap_hi):
+    return _check(ctx, lib().bl_mlp_attach_range(ctx, m, float(gap_lo), float(gap_hi)))
 
 
 def bl_pair_features(ctx, pairs, out):

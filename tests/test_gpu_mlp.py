@@ -163,10 +163,12 @@ def test_prescribed_motion_matches_oracle():
     np.testing.assert_array_equal(pg["V"], V)
 
 
-def test_attached_network_adds_rotated_correction_to_close_pairs():
+@pytest.mark.parametrize("lo", [None, 0.5])
+def test_attached_network_adds_rotated_correction_to_close_pairs(lo):
     """A network whose output is its bias b3 adds R_i b3 once per close pair
-    (gap below the cut-off, from the oracle's features) to the potential
-    part of the force and torque."""
+    (gap below the cut-off, and not below lo when a range is given, from the
+    oracle's features) to the potential part of the force and torque; pairs
+    outside the range keep the plain method."""
     import oracle
     from oracle import mlp
     from paper_1005_2594_gb300 import bloodlb as bl
@@ -180,7 +182,10 @@ def test_attached_network_adds_rotated_correction_to_close_pairs():
     m = bl.bl_mlp_create()
     bl.bl_mlp_params_set(m, theta, norm)
     a, b = bl.Simulation(p), bl.Simulation(p)
-    bl.bl_mlp_attach(b.ctx, m, cut)
+    if lo is None:
+        bl.bl_mlp_attach(b.ctx, m, cut)
+    else:
+        bl.bl_mlp_attach_range(b.ctx, m, lo, cut)
     for s in (a, b):
         s.set_particles(X, q, V, L)
         s.step(1)
@@ -201,11 +206,15 @@ def test_attached_network_adds_rotated_correction_to_close_pairs():
                 continue
             f = mlp.pair_features(p["R_par"], p["R_perp"], dims, p["periodic"], X[i], q[i], V[i], Om[i], X[j],
                                   q[j], V[j], Om[j])
-            if f[7] < cut:
+            if f[7] < cut and (lo is None or f[7] >= lo):
                 eF[i] += R @ b3[:3]
                 eT[i] += R @ b3[3:]
                 npairs += 1
     assert npairs > 0
+    if lo is not None:  # the range leaves out some close pairs
+        n_close = sum(mlp.pair_features(p["R_par"], p["R_perp"], dims, p["periodic"], X[i], q[i], V[i], Om[i], X[j],
+                                        q[j], V[j], Om[j])[7] < cut for i in range(n) for j in range(n) if i != j)
+        assert n_close > npairs
     np.testing.assert_allclose(dF, eF, atol=1e-5)
     np.testing.assert_allclose(dT, eT, atol=1e-5)
     a.close()

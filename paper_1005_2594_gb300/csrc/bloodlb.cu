@@ -489,7 +489,11 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
   launch_claims(c->lv, c->pv, c->claim, c->chg, first ? 1 : 2, c->stream, &c->launches);
   launch_resolve_fill(c->dtype, c->lv, c->pv, c->cl, c->claim, c->chg, c->parity, first ? 0 : 1, c->stream,
                       &c->launches);
-  launch_geometry(c->lv, c->pv, c->stream, &c->launches);
+  // neighbour words: the whole lattice after a first placement; after a
+  // re-placement only around the nodes resolve changed (every step starts by
+  // building the link lists and contact sums of the current owner map)
+  if (first) launch_geometry(c->lv, c->pv, c->stream, &c->launches);
+  else launch_nbm_update(c->lv, c->pv, c->chg, c->stream, &c->launches);
   std::swap(c->pv.kin, c->pv.kin_next);
   if (check_launch(c, "particles_set")) return c->sticky;
   CU(cudaStreamSynchronize(c->stream));

@@ -43,6 +43,9 @@ struct bl_ctx {
   // an internal stream, forked from and joined to the caller's stream
   cudaStream_t gstream;
   cudaGraphExec_t gexec;
+  cudaGraphExec_t g1exec[2];  // one step from parity 0 / 1 (for odd step counts)
+  const void *g1kin[2];
+  int64_t g1_launches[2];
   int g_parity;
   const void *g_kin;
   int64_t g_launches;
@@ -448,7 +451,10 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
         return fail(c, BL_EINVAL, "periodic length %d < 2 max(R) + 4", dims[k]);
   }
   const bool first = n != c->np || c->np == 0;
-  drop_graph(c);  // the cell arrays may move; the graph holds their pointers
+  // the graphs hold the cell arrays' pointers and the cell constants by
+  // value: they stay valid for a re-placement with the same arrays and
+  // parameters (their keys, parity and kinematics buffer, are checked)
+  if (first || memcmp(&c->pp, pp, sizeof(bl_particle_params)) != 0) drop_graph(c);
   if (first) {
     // cells of a previous call become resting fluid
     launch_clear_cells(c->dtype, c->lv, c->parity, c->stream, &c->launches);
@@ -557,6 +563,10 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
 static void drop_graph(bl_ctx *c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   c->gexec = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    if (c->g1exec[k]) cudaGraphExecDestroy(c->g1exec[k]);
+    c->g1exec[k] = nullptr;
+  }
   c->epoch++;
 }
 
@@ -591,6 +601,33 @@ static int capture_graph(bl_ctx *c) {
   return BL_OK;
 }
 
+// the graph of one step from the current parity and cell state
+static int capture_graph1(bl_ctx *c) {
+  const int par = c->parity;
+  if (c->g1exec[par]) cudaGraphExecDestroy(c->g1exec[par]);
+  c->g1exec[par] = nullptr;
+  const int64_t l0 = c->launches;
+  const void *kin = c->pv.kin;
+  cudaGraph_t g = nullptr;
+  CU(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_step(c, c->gstream);
+  cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
+  c->parity = par;  // capturing ran nothing: undo the step's host-side flips
+  if (c->pv.kin != (const float4 *)kin) std::swap(c->pv.kin, c->pv.kin_next);
+  c->g1_launches[par] = c->launches - l0;
+  c->launches = l0;
+  if (rc != BL_OK) return rc;
+  if (e != cudaSuccess) return fail(c, BL_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->g1exec[par], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->g1exec[par] = nullptr;
+    return fail(c, BL_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  c->g1kin[par] = kin;
+  return BL_OK;
+}
+
 extern "C" int bl_step(bl_ctx *c, int nsteps) {
   if (!c || nsteps < 0) return BL_EINVAL;
   if (c->sticky) return c->sticky;
@@ -607,6 +644,21 @@ extern "C" int bl_step(bl_ctx *c, int nsteps) {
     }
     CU(cudaEventRecord(c->ev_join, c->gstream));
     CU(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  }
+  if (!c->timing && s < nsteps) {
+    // a last single step as a one-step graph
+    const int par = c->parity;
+    if (!c->g1exec[par] || c->g1kin[par] != (const void *)c->pv.kin)
+      if (capture_graph1(c)) return c->sticky;
+    CU(cudaEventRecord(c->ev_fork, c->stream));
+    CU(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0));
+    CU(cudaGraphLaunch(c->g1exec[par], c->gstream));
+    c->launches += c->g1_launches[par];
+    CU(cudaEventRecord(c->ev_join, c->gstream));
+    CU(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    c->parity ^= 1;  // what the step does on the host
+    if (c->np > 0) std::swap(c->pv.kin, c->pv.kin_next);
+    ++s;
   }
   for (; s < nsteps; ++s)
     if (enqueue_step(c, c->stream)) return c->sticky;

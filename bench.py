@@ -394,7 +394,7 @@ def run_learned(args, ws, rank, local):
     for mode in ("plain", "learned"):
         if mode == "learned":
             # the trained gaps from below, up to the cut-off; closer pairs keep the plain method
-            bl.bl_mlp_attach_range(sim.ctx, m, info["gap_min"], 2.0)
+            bl.bl_mlp_attach_range(sim.ctx, m, info["gap_min"], 2.0, info["speed_min"], info["speed_max"])
         sim.step(args.warmup)
         sim.sync()
         l0 = bl.bl_launch_count(sim.ctx)
@@ -423,7 +423,8 @@ def run_learned(args, ws, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
         "data": "synthetic (jittered fcc start, resting plasma; network trained on generated approach runs)",
         "config": {"workload": desc, "lattice": [p["nx"], p["ny"], p["nz"]], "cells": int(len(Xc)),
-                   "fluid_nodes": fluid, "gap_range": [round(info["gap_min"], 3), 2.0], "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "fluid_nodes": fluid, "gap_range": [round(info["gap_min"], 3), 2.0],
+                   "speed_range": [round(info["speed_min"], 4), round(info["speed_max"], 4)], "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "populations %.0f MB > 129 MB L2, no flush" % (N * 19 * 4 / 1e6)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None,
@@ -444,6 +445,59 @@ def run_learned(args, ws, rank, local):
         "clocks": clk,
     }
     sim.close()
+    bl.bl_mlp_destroy(m)
+    return out
+
+
+def run_rheology(args, ws, rank, local):
+    """Apparent viscosity (relative to the plasma) of a tube suspension: a
+    tube of radius 30 and length 128 with (7,7,3) cells at 35 % of the lumen,
+    driven by g = 2e-6 on plasma and cells, from rest: the coarse method
+    alone, with the learned correction (trained here on approach runs), and
+    the plain method at 2x resolution (4x the steps); each against the
+    plasma alone at its resolution.  Coarse runs take --steps steps (about
+    20000 reach steady flow), the 2x runs four times as many."""
+    import torch
+
+    import __graft_entry__
+    from paper_1005_2594_gb300 import bloodlb as bl
+    from paper_1005_2594_gb300 import learned, rheology
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    X, Y, _, runs = learned.approach_samples(64, seed=11)
+    m, info = learned.fit(X, Y, runs, seed=0)
+    rng = (info["gap_min"], 2.0, info["speed_min"], info["speed_max"])
+    res = {}
+    for name, k, cells, net in (("plasma_1x", 1, False, False), ("plain_1x", 1, True, False),
+                                ("learned_1x", 1, True, True), ("plasma_2x", 2, False, False),
+                                ("plain_2x", 2, True, False)):
+        p, Xc, qc, mask = rheology.tube_case(k, cells=cells)
+        steps = args.steps * k * k
+        Q, samples, ms = rheology.run(p, Xc, qc, mask, steps, model=m if net else None, gap_range=rng)
+        N = p["nx"] * p["ny"] * p["nz"]
+        res[name] = {"flux": Q, "flux_rel_spread": float(np.std(samples) / abs(Q)), "steps": steps,
+                     "cells": int(len(Xc)), "lattice": [p["nx"], p["ny"], p["nz"]],
+                     "mlups": N * steps / (ms * 1e-3) / 1e6}
+    mu = {"plain_1x": res["plasma_1x"]["flux"] / res["plain_1x"]["flux"],
+          "learned_1x": res["plasma_1x"]["flux"] / res["learned_1x"]["flux"],
+          "plain_2x": res["plasma_2x"]["flux"] / res["plain_2x"]["flux"]}
+    r = res["learned_1x"]
+    out = {
+        "metric": METRIC, "value": round(r["mlups"], 2), "unit": UNIT, "n_gpus": ws, "steps": r["steps"],
+        "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (network bf16)", "data": "synthetic (jittered fcc start, resting plasma)",
+        "config": {"workload": "tube radius 30, length 128, %d (7,7,3) cells at 35 %% of the lumen, g = 2e-6; "
+                               "value: coarse with the network (MLUPS of the stepping)" % r["cells"],
+                   "lattice": r["lattice"], "gap_range": [round(rng[0], 3), rng[1]],
+                   "speed_range": [round(rng[2], 4), round(rng[3], 4)]},
+        "rheology": {"mu_rel": {k: round(v, 4) for k, v in mu.items()},
+                     "note": "apparent viscosity relative to the plasma = plasma flux / suspension flux under the "
+                             "same driving, flux averaged over the second half of each run from rest",
+                     "runs": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                              for k, v in res.items()}},
+        "roofline": None,
+    }
     bl.bl_mlp_destroy(m)
     return out
 
@@ -550,7 +604,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--config", default="shear128", choices=["shear128", "small32", "duct256", "ensemble64", "tube512"])
+    ap.add_argument("--config", default="shear128", choices=["shear128", "small32", "duct256", "ensemble64", "tube512", "tube_rheology"])
     ap.add_argument("--store", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -562,8 +616,9 @@ def main():
         if rank == 0:
             print(json.dumps(out), flush=True)
         return
-    if args.config in ("ensemble64", "tube512"):
-        out = (run_ensemble if args.config == "ensemble64" else run_learned)(args, ws, rank, local)
+    if args.config in ("ensemble64", "tube512", "tube_rheology"):
+        fn = {"ensemble64": run_ensemble, "tube512": run_learned, "tube_rheology": run_rheology}[args.config]
+        out = fn(args, ws, rank, local)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return

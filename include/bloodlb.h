@@ -261,15 +261,16 @@ void bl_mlp_destroy(bl_mlp *m);
 
 /* Uses model m (NULL: none, the plain method) in every later step of
    context c: after the potentials, every ordered pair of cells with
-   gap_lo <= gap < gap_hi (lattice units; gap as in bl_pair_features) gets
-   the network's force and torque correction, rotated to the lab frame and
-   added to the potential part of the step's force (bl_force_parts_get Fp /
-   Tp); pairs outside the range keep the plain method (a network is not
-   used below the gaps it was trained on).  bl_mlp_attach(c, m, cut) is the
-   range (-infinity, cut).  BL_EINVAL unless gap_lo < gap_hi and |gap_hi| <
-   1000.  The model must outlive its use; the step runs it on the context's
-   streams. */
-int bl_mlp_attach_range(bl_ctx *c, bl_mlp *m, double gap_lo, double gap_hi);
+   gap_lo <= gap < gap_hi (lattice units; gap as in bl_pair_features) and
+   relative speed |V_j - V_i| in [speed_lo, speed_hi] gets the network's
+   force and torque correction, rotated to the lab frame and added to the
+   potential part of the step's force (bl_force_parts_get Fp / Tp); every
+   other pair keeps the plain method (a network is not used outside the
+   gaps and speeds it was trained on).  bl_mlp_attach(c, m, cut) is the range
+   gap < cut at any speed.  BL_EINVAL unless gap_lo < gap_hi, |gap_hi| <
+   1000 and 0 <= speed_lo <= speed_hi.  The model must outlive its use; the
+   step runs it on the context's streams. */
+int bl_mlp_attach_range(bl_ctx *c, bl_mlp *m, double gap_lo, double gap_hi, double speed_lo, double speed_hi);
 int bl_mlp_attach(bl_ctx *c, bl_mlp *m, double gap_cut);
 
 /* Features of n ordered pairs (device array of n x 2 int32 cell indices) from

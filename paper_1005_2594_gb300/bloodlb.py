@@ -115,7 +115,8 @@ def lib():
         "bl_mlp_sync": (ctypes.c_int, [vp]),
         "bl_mlp_destroy": (None, [vp]),
         "bl_mlp_attach": (ctypes.c_int, [vp, vp, ctypes.c_double]),
-        "bl_mlp_attach_range": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double]),
+        "bl_mlp_attach_range": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double]),
         "bl_pair_features": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         "bl_timing_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "bl_timing_read": (ctypes.c_int, [vp, D, ctypes.POINTER(i64), ctypes.c_int]),
@@ -313,8 +314,9 @@ def bl_mlp_attach(ctx, m, gap_cut):
     return _check(ctx, lib().bl_mlp_attach(ctx, m, float(gap_cut)))
 
 
-def bl_mlp_attach_range(ctx, m, gap_lo, gap_hi):
-    return _check(ctx, lib().bl_mlp_attach_range(ctx, m, float(gap_lo), float(gap_hi)))
+def bl_mlp_attach_range(ctx, m, gap_lo, gap_hi, speed_lo=0.0, speed_hi=float("inf")):
+    return _check(ctx, lib().bl_mlp_attach_range(ctx, m, float(gap_lo), float(gap_hi), float(speed_lo),
+                                                  float(min(speed_hi, 1e300))))
 
 
 def bl_pair_features(ctx, pairs, out):

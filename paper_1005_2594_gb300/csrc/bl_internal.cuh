@@ -198,7 +198,8 @@ void launch_clear_cells(int dtype, const LatticeView &lv, int par, cudaStream_t 
 void launch_pair_features(const LatticeView &lv, const PartView &pv, const int2 *pairs, int n, float *out,
                           cudaStream_t st);
 void launch_mlp_correction(const LatticeView &lv, const PartView &pv, const CellListView &cl, const PairBuf &pb,
-                           float gap_lo, float gap_cut, const void *mlp, cudaStream_t st, int64_t *nl);
+                           float gap_lo, float gap_cut, float speed_lo, float speed_hi, const void *mlp,
+                           cudaStream_t st, int64_t *nl);
 // forward pass of a bl_mlp over *count rows of x (at most cap), raw units
 void launch_mlp_forward_dev(const void *mlp, const float *x, const int *count, int cap, float *y, cudaStream_t st);
 

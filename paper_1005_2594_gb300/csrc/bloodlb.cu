@@ -53,7 +53,7 @@ struct bl_ctx {
   // learned near-contact correction (bl_mlp_attach): the model, its gap
   // cut-off and the close-pair buffers (32 pairs per cell)
   const void *mlp;
-  float gap_lo, gap_cut;
+  float gap_lo, gap_cut, speed_lo, speed_hi;
   PairBuf pb;
   int dtype;
   int parity;  // layout of the current populations (next step's parity)
@@ -525,7 +525,9 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     group_end(c, slot, c->side);
     group_begin(c, 2, &slot, c->side);
     launch_forces(c->lv, c->pv, c->cl, c->sbits, c->side, &c->launches);
-    if (c->mlp) launch_mlp_correction(c->lv, c->pv, c->cl, c->pb, c->gap_lo, c->gap_cut, c->mlp, c->side, &c->launches);
+    if (c->mlp)
+      launch_mlp_correction(c->lv, c->pv, c->cl, c->pb, c->gap_lo, c->gap_cut, c->speed_lo, c->speed_hi, c->mlp,
+                            c->side, &c->launches);
     group_end(c, slot, c->side);
     cudaEventRecord(c->ev_join, c->side);
   }
@@ -857,21 +859,25 @@ extern "C" const char *bl_last_error(const bl_ctx *c) { return c ? c->err : "nul
 // ---------------------------------------------------------------------------
 // learned near-contact correction
 
-extern "C" int bl_mlp_attach_range(bl_ctx *c, bl_mlp *m, double gap_lo, double gap_hi) {
+extern "C" int bl_mlp_attach_range(bl_ctx *c, bl_mlp *m, double gap_lo, double gap_hi, double speed_lo,
+                                   double speed_hi) {
   if (!c) return BL_EINVAL;
   if (c->sticky) return c->sticky;
-  if (m && !(gap_lo < gap_hi && gap_hi > -1e3 && gap_hi < 1e3 && gap_lo < 1e3))
-    return fail(c, BL_EINVAL, "gap range");
+  if (m && !(gap_lo < gap_hi && gap_hi > -1e3 && gap_hi < 1e3 && gap_lo < 1e3 && speed_lo <= speed_hi &&
+             speed_lo >= 0.0))
+    return fail(c, BL_EINVAL, "gap or speed range");
   drop_graph(c);
   c->mlp = m;
   c->gap_lo = gap_lo < -1e30 ? -3.0e38f : (float)gap_lo;
   c->gap_cut = (float)gap_hi;
+  c->speed_lo = (float)speed_lo;
+  c->speed_hi = speed_hi > 1e30 ? 3.0e38f : (float)speed_hi;
   if (m && alloc_pairbuf(c)) return c->sticky;
   return BL_OK;
 }
 
 extern "C" int bl_mlp_attach(bl_ctx *c, bl_mlp *m, double gap_cut) {
-  return bl_mlp_attach_range(c, m, -1e300, gap_cut);
+  return bl_mlp_attach_range(c, m, -1e300, gap_cut, 0.0, 1e300);
 }
 
 extern "C" int bl_pair_features(bl_ctx *c, const int32_t *pairs, int n, float *out) {

@@ -1506,9 +1506,11 @@ __global__ void k_pair_features(LatticeView lv, PartView pv, const int2 *pairs, 
   for (int k = 0; k < 14; ++k) out[14 * t + k] = f[k];
 }
 
-// close pairs (gap_lo <= gap < gap_cut) from the cell list, one block per cell
+// close pairs (gap_lo <= gap < gap_cut, relative speed |V_j - V_i| in
+// [speed_lo, speed_hi]) from the cell list, one block per cell
 // (lane b < 27 scans bin b), with their features
-__global__ void k_mlp_pairs(LatticeView lv, PartView pv, CellListView cl, PairBuf pb, float gap_lo, float gap_cut) {
+__global__ void k_mlp_pairs(LatticeView lv, PartView pv, CellListView cl, PairBuf pb, float gap_lo, float gap_cut,
+                            float speed_lo, float speed_hi) {
   const int i = blockIdx.x;
   if (threadIdx.x >= 27) return;
   const int bin = cl.bin_of[i];
@@ -1526,6 +1528,8 @@ __global__ void k_mlp_pairs(LatticeView lv, PartView pv, CellListView cl, PairBu
     float f[14], R[3][3];
     pair_features(lv, pv, i, j, f, R);
     if (!(f[7] >= gap_lo && f[7] < gap_cut)) continue;  // outside the range: the plain method
+    const float sp = sqrtf(f[8] * f[8] + f[9] * f[9] + f[10] * f[10]);
+    if (!(sp >= speed_lo && sp <= speed_hi)) continue;
     const int s = atomicAdd(pb.count, 1);
     if (s >= pb.cap) {
       atomicOr(pv.status, ST_OVERFLOW);
@@ -1606,10 +1610,11 @@ void launch_pair_features(const LatticeView &lv, const PartView &pv, const int2 
 }
 
 void launch_mlp_correction(const LatticeView &lv, const PartView &pv, const CellListView &cl, const PairBuf &pb,
-                           float gap_lo, float gap_cut, const void *mlp, cudaStream_t st, int64_t *nl) {
+                           float gap_lo, float gap_cut, float speed_lo, float speed_hi, const void *mlp,
+                           cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
   cudaMemsetAsync(pb.count, 0, sizeof(int), st);
-  k_mlp_pairs<<<pv.n, 32, 0, st>>>(lv, pv, cl, pb, gap_lo, gap_cut);
+  k_mlp_pairs<<<pv.n, 32, 0, st>>>(lv, pv, cl, pb, gap_lo, gap_cut, speed_lo, speed_hi);
   launch_mlp_forward_dev(mlp, pb.feat, pb.count, pb.cap, pb.out, st);
   k_mlp_apply<<<nblk((unsigned)pb.cap, 128) < 152u ? nblk((unsigned)pb.cap, 128) : 152u, 128, 0, st>>>(pv, pb);
   *nl += 3;

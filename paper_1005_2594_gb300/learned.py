@@ -247,8 +247,9 @@ def fit(X, Y, runs, seed=0, copies=16, clip=4.0, val_frac=0.2, epochs=2000, lr=1
     """the training recipe: whole runs split into training and validation
     sets, the training samples augmented by the pair's symmetries and their
     targets clipped at `clip` standard deviations, then `train` with early
-    stopping.  Returns (model handle, dict of losses, sizes and the gap range
-    of the training samples, outside which the network is not to be used)."""
+    stopping.  Returns (model handle, dict of losses, sizes and the ranges of
+    gap and relative speed of the training samples, outside which the network
+    is not to be used)."""
     rng = np.random.default_rng(seed)
     ids = np.unique(runs)
     rng.shuffle(ids)
@@ -259,7 +260,9 @@ def fit(X, Y, runs, seed=0, copies=16, clip=4.0, val_frac=0.2, epochs=2000, lr=1
     m, hist, vhist = train(Xt, Yt, epochs=epochs, lr=lr, seed=seed, model=model, Xv=X[val], Yv=Y[val])
     return m, {"train_samples": Xt.shape[0], "val_samples": int(val.sum()), "loss_first": hist[0],
                "loss_last": hist[-1], "val_best": min(vhist), "val_best_epoch": 25 * int(np.argmin(vhist)),
-               "gap_min": float(X[:, 7].min()), "gap_max": float(X[:, 7].max())}
+               "gap_min": float(X[:, 7].min()), "gap_max": float(X[:, 7].max()),
+               "speed_min": float(np.linalg.norm(X[:, 8:11], axis=1).min()),
+               "speed_max": float(np.linalg.norm(X[:, 8:11], axis=1).max())}
 
 
 def errors(m, X, Y, scale):

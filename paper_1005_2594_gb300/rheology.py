@@ -1,0 +1,106 @@
+"""Apparent viscosity of the suspension in tube flow.
+
+Sec. IV characterises the model by the apparent viscosity of a suspension
+driven through a tube by a body force: the viscosity a Newtonian fluid would
+need to carry the same volume flux Q, mu_app = pi R^4 rho_bar g / (8 Q),
+relative to the plasma's rho_bar nu.  On the lattice the walls sit midway
+between a staircase of nodes, so the radius that the Poiseuille formula
+needs is not R exactly; the relative viscosity is therefore taken as the
+ratio of fluxes under the same driving, plasma alone over suspension:
+mu_rel = Q_plasma / Q.
+
+Q is the volume flux along the tube axis (x): the axial velocity of the
+fluid nodes summed over the lattice and divided by the tube length, plus the
+cells' share, V_x times the cell volume over the length.
+
+The refined case (``tube_case(k)``) is the same physical system on a lattice
+k times finer under diffusive scaling at fixed tau: box, tube radius, cells
+and positions x k, body force / k^3 (an acceleration in lattice units), and
+the contact strength x k so that potential forces, like lattice forces, stay
+the same in lattice units.
+"""
+import math
+
+import numpy as np
+
+from . import bloodlb as bl
+from . import workloads
+
+
+def tube_case(k=1, radius=30.0, length=128, hct=0.35, g=2e-6, R=(7.0, 3.0), seed=1007, cells=True):
+    """params, X, q, wall mask of the tube refined k times (X, q empty
+    without cells).  The coarse cross-section is 2 radius + 8 nodes wide."""
+    n = int(2 * radius + 8)
+    p = workloads.base_params(length * k, n * k, n * k, periodic=(1, 1, 1), R=(R[0] * k, R[1] * k), eps=float(k),
+                              g=(g / k ** 3, 0.0, 0.0), body_force_on_cells=1)
+    mask = workloads.tube_mask(p, radius * k, axis=0)
+    if not cells:
+        return p, np.zeros((0, 3)), np.zeros((0, 4)), mask
+    pc = workloads.base_params(length, n, n, periodic=(1, 1, 1), R=R)
+    n_cells = int(round(hct * math.pi * radius ** 2 * length / workloads.cell_volume(pc)))
+    c = (n - 1) / 2.0
+    rmax = max(R)
+
+    def inside(x):
+        return np.hypot(x[:, 1] - c, x[:, 2] - c) + rmax + 1.0 < radius
+
+    X, q = workloads.fcc_cells(pc, n_cells, seed, inside)
+    # the same places on the finer lattice: the axis moves from (n - 1) / 2
+    # to (k n - 1) / 2
+    Xk = X * k
+    Xk[:, 1:] += (k - 1) / 2.0
+    return p, Xk, q, mask
+
+
+def flux(sim, p):
+    """volume flux along x (lattice units)"""
+    import torch
+
+    N = p["nx"] * p["ny"] * p["nz"]
+    rho = torch.empty(N, dtype=torch.float64, device="cuda")
+    u = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    bl.bl_fields_get(sim.ctx, N, rho, u, None, on_device=True)
+    torch.cuda.synchronize()
+    q_fluid = float(u[:, 0].sum()) / p["nx"]
+    if sim.n == 0:
+        return q_fluid
+    V = sim.particles()["V"]
+    vol = 4.0 / 3.0 * math.pi * p["R_perp"] ** 2 * p["R_par"]
+    return q_fluid + float(V[:, 0].sum()) * vol / p["nx"]
+
+
+def run(p, X, q, mask, steps, samples=20, model=None, gap_range=None, stream=None):
+    """steps of the tube from rest (with `model` attached over gap_range =
+    (gap_lo, gap_hi[, speed_lo, speed_hi])); the flux sampled at `samples` even
+    intervals over the second half.  Returns (mean flux, flux samples,
+    milliseconds of stepping, CUDA events on the stream, read-outs excluded)."""
+    import torch
+
+    st = torch.cuda.current_stream() if stream is None else stream
+    sim = bl.Simulation(p, stream=st.cuda_stream, wall_mask=mask)
+    if len(X):
+        sim.set_particles(X, q)
+        if model is not None:
+            bl.bl_mlp_attach_range(sim.ctx, model, *gap_range)
+    half = steps // 2
+    every = max(2, (steps - half) // samples) // 2 * 2
+    ms = 0.0
+
+    def advance(k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sim.step(k)
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    ms += advance(half)
+    out = []
+    done = half
+    while done + every <= steps:
+        ms += advance(every)
+        done += every
+        out.append(flux(sim, p))
+    sim.sync()
+    sim.close()
+    return float(np.mean(out)), out, ms

@@ -163,12 +163,13 @@ def test_prescribed_motion_matches_oracle():
     np.testing.assert_array_equal(pg["V"], V)
 
 
-@pytest.mark.parametrize("lo", [None, 0.5])
-def test_attached_network_adds_rotated_correction_to_close_pairs(lo):
+@pytest.mark.parametrize("lo,speed", [(None, None), (0.5, None), (0.5, (0.01, 0.03))])
+def test_attached_network_adds_rotated_correction_to_close_pairs(lo, speed):
     """A network whose output is its bias b3 adds R_i b3 once per close pair
-    (gap below the cut-off, and not below lo when a range is given, from the
-    oracle's features) to the potential part of the force and torque; pairs
-    outside the range keep the plain method."""
+    (gap below the cut-off, not below lo and relative speed within the
+    window when those are given, from the oracle's features) to the
+    potential part of the force and torque; the other pairs keep the plain
+    method."""
     import oracle
     from oracle import mlp
     from paper_1005_2594_gb300 import bloodlb as bl
@@ -184,8 +185,15 @@ def test_attached_network_adds_rotated_correction_to_close_pairs(lo):
     a, b = bl.Simulation(p), bl.Simulation(p)
     if lo is None:
         bl.bl_mlp_attach(b.ctx, m, cut)
-    else:
+    elif speed is None:
         bl.bl_mlp_attach_range(b.ctx, m, lo, cut)
+    else:
+        bl.bl_mlp_attach_range(b.ctx, m, lo, cut, speed[0], speed[1])
+
+    def selected(f):
+        sp = np.linalg.norm(f[8:11])
+        return f[7] < cut and (lo is None or f[7] >= lo) and (speed is None or speed[0] <= sp <= speed[1])
+
     for s in (a, b):
         s.set_particles(X, q, V, L)
         s.step(1)
@@ -206,7 +214,7 @@ def test_attached_network_adds_rotated_correction_to_close_pairs(lo):
                 continue
             f = mlp.pair_features(p["R_par"], p["R_perp"], dims, p["periodic"], X[i], q[i], V[i], Om[i], X[j],
                                   q[j], V[j], Om[j])
-            if f[7] < cut and (lo is None or f[7] >= lo):
+            if selected(f):
                 eF[i] += R @ b3[:3]
                 eT[i] += R @ b3[3:]
                 npairs += 1

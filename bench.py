@@ -151,6 +151,11 @@ def make_workload(name):
     if name == "tube512":
         p, X, q, mask = workloads.tube()
         return p, X, q, mask, "tube 512x256x256, radius 120 along x, g = 1e-6 on plasma and cells, %d (7,7,3) cells at 35 %% of the lumen" % len(X)
+    if name == "tube_rheology":
+        from paper_1005_2594_gb300 import rheology
+
+        p, X, q, mask = rheology.tube_case(1)
+        return p, X, q, mask, "tube radius 30, length 128, %d (7,7,3) cells at 35 %% of the lumen, g = 2e-6" % len(X)
     if name == "duct256":
         p, X, q = workloads.duct(n=256, n_cells=8192, g=1e-6, seed=1003)
         return p, X, q, None, "duct 256^3, walls y z, g = 1e-6 along x, 8192 (7,7,3) cells"
@@ -565,9 +570,14 @@ def run_reference(args, ws, rank):
         return None
     import oracle
 
-    p, X, q, _, desc = make_workload(args.config)
+    p, X, q, _mask, desc = make_workload(args.config)
     steps, warmup = args.steps, args.warmup
-    if args.config == "tube512":
+    if args.config == "tube_rheology":
+        # the coarse tube itself (about 0.7 s per oracle step): as many steps as fit
+        sp, sX, sq, smask = p, X, q, _mask
+        steps, warmup = max(1, min(steps, 100)), min(warmup, 3)
+        sample = "the whole coarse tube (128x68x68, %d cells), %d steps" % (len(sX), steps)
+    elif args.config == "tube512":
         # the cross-section is fixed by the radius: a slab of 8 x-planes of the
         # same tube, and as many steps as fit the budget (~0.5 s each)
         from paper_1005_2594_gb300 import workloads

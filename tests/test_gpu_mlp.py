@@ -228,3 +228,21 @@ def test_attached_network_adds_rotated_correction_to_close_pairs(lo, speed):
     a.close()
     b.close()
     bl.bl_mlp_destroy(m)
+
+
+def test_tube_flux_of_plasma_is_poiseuille():
+    """The tube observable: plasma alone, driven by g in a tube of radius R,
+    carries the Poiseuille flux pi R_eff^4 g / (8 nu) once developed, with the
+    staircase's effective radius within half a node of R."""
+    import math
+
+    from paper_1005_2594_gb300 import rheology
+
+    R = 10.0
+    p, X, q, mask = rheology.tube_case(1, radius=R, length=16, cells=False, g=1e-5)
+    Q, samples, _ = rheology.run(p, X, q, mask, 6000, samples=4)
+    nu = (p["tau"] - 0.5) / 3.0
+    R_eff = (8.0 * Q * nu / (math.pi * p["g"][0])) ** 0.25
+    print("tube radius %.1f: effective radius %.3f, flux spread %.1e" % (R, R_eff, np.std(samples) / Q))
+    assert abs(R_eff - R) < 0.5
+    assert np.std(samples) / Q < 1e-3  # developed

@@ -19,11 +19,12 @@
  *   are borrowed for the duration of the call only.
  * Streams: every call of a context is ordered on the CUDA stream given to
  *   bl_lb_init (NULL = the legacy default stream).  Inside a step the cell
- *   list and the potentials run on a second stream of the context beside
- *   the lattice sweep, and repeated steps replay a captured graph on a
- *   third; both are forked from and joined back to the caller's stream with
- *   events, so work the caller enqueues later still follows the step.  A
- *   context is not thread-safe; use one context per stream.
+ *   list, the potentials and the link lists run on two more streams of the
+ *   context beside the lattice sweep, and the claims beside the link
+ *   correction; steps replay captured graphs on a fourth stream.  All are
+ *   forked from and joined back to the caller's stream with events, so work
+ *   the caller enqueues later still follows the step.  A context is not
+ *   thread-safe; use one context per stream.
  * Lattice: nodes are numbered n = x + nx (y + ny z), x fastest.  A
  *   non-periodic axis carries solid wall layers at index 0 and N-1; faces
  *   are numbered x-,x+,y-,y+,z-,z+ = wall ids 0..5.  Owner codes: -1 fluid,
@@ -123,9 +124,10 @@ int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, const doubl
    collide + stream + bounce-back + momentum exchange + contact links, cell
    list, pair and wall potentials, leap-frog, re-discretisation with
    fill/drain.  With timing off, pairs of steps are launched as one CUDA
-   graph (captured on first use and again after bl_particles_set or
-   bl_walls_set).  Returns the sticky status known so far (device errors of
-   this call surface at the next bl_sync). */
+   graph and a last single step as a one-step graph (captured on first use,
+   and again when the cell arrays or parameters, the walls, the sweep variant
+   or the attached network change).  Returns the sticky status known so far
+   (device errors of this call surface at the next bl_sync). */
 int bl_step(bl_ctx *c, int nsteps);
 
 /* Moments of the current populations: rho (N doubles) and

@@ -1583,7 +1583,7 @@ template <class S>
 static void sums_solve_typed(const LatticeView &lv, const PartView &pv, int par, cudaStream_t st) {
   const dim3 grid_sum((unsigned)((pv.lk_cap + LCHUNK - 1) / LCHUNK), pv.n);
   k_link_sums<S><<<grid_sum, LT, 0, st>>>(lv, pv, par);
-  k_solve<<<nblk(pv.n, 64), 64, 0, st>>>(lv, pv);
+  k_solve<<<nblk(pv.n, 32), 32, 0, st>>>(lv, pv);
 }
 
 void launch_sums_solve(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st, int64_t *nl) {

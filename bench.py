@@ -164,9 +164,9 @@ def make_workload(name):
 
 # DRAM traffic of one lattice sweep (dram__bytes_read.sum + dram__bytes_write.sum,
 # mean of the even and odd launch) from the ncu capture summarised in
-# profiles/lattice_sweep_shear128_dram.md, valid for the kernel source it was
-# taken on (first 16 hex digits of its SHA-256) and that workload only
-SWEEP_TRAFFIC = {"sha": "370dfed0ae240562", "config": "shear128", "store": 0, "bytes": 272235264}
+# profiles/lattice_sweep_shear128_dram.md, valid for the sweep source it was
+# taken on (lb_sweep.cuh, first 16 hex digits of its SHA-256) and that workload only
+SWEEP_TRAFFIC = {"sha": "ad506e7e2729c60d", "config": "shear128", "store": 0, "bytes": 272235264}
 
 
 # the sweep kernel each storage type runs by default (FP32: variant 3 of the
@@ -179,7 +179,7 @@ SWEEP_KERNEL = {0: "k_lb_step_bulk (fused collide/stream/bounce-back, bulk-copy 
 def sweep_traffic(config, store):
     import hashlib
 
-    src = os.path.join(ROOT, "paper_1005_2594_gb300", "csrc", "lb_kernels.cu")
+    src = os.path.join(ROOT, "paper_1005_2594_gb300", "csrc", "lb_sweep.cuh")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     t = SWEEP_TRAFFIC
     if sha == t["sha"] and config == t["config"] and store == t["store"]:

@@ -1,0 +1,516 @@
+// lb_sweep.cuh -- the lattice sweep of the coupled step (kernels and their
+// launch for one storage type; lb_sweep_f32.cu, lb_sweep_bf16.cu and
+// lb_sweep_f16.cu instantiate it, so that the three compile in parallel).
+//
+// The sweep fuses, per node and per time step (arXiv:1005.2594, Sec. II):
+//   * moments rho, j and the Guo-forced velocity u = (j + rho g / 2) / rho,
+//   * BGK collision (Eq. col) with the third-order equilibrium (Eq. neq),
+//   * advection (Eq. adv) in the AA pattern on one buffer,
+//   * mid-link bounce-back (Eq. lbe-bb); on wall links with the moving-wall
+//     term C (Eqs. c, lbe-bb-corr) and the momentum exchange (Eq. deltap)
+//     into the wall's counter.
+//
+// AA pattern.  Slot r of node n sits at r * N + n.  An even step reads node
+// n's populations from its own slots [r][n] and writes the post-collision
+// value of direction r to [rbar][n]; an odd step reads [rbar][n - c_r] and
+// writes [r][n + c_r].  A population that meets a solid neighbour is written,
+// with C added, to the slot where the next step reads the opposite direction
+// of the same node: [r][n + c_r] in an even step, [rbar][n] in an odd one.
+// Every fluid node reads and writes its own 19 slots only, so the sweep is
+// race-free in place.  Populations are stored shifted, f~ = f - alpha rho_bar.
+//
+// Cells.  A population that meets a cell node is bounced here without the
+// moving-boundary term: the cell's velocity of the half step is not known
+// yet.  The sweep records the node's density; the cell kernels then sum the
+// cell's link momenta over its link list, solve for the half-step velocity
+// and add C to each of its bounced populations (reading Q3, implicit
+// coupling).
+// Walls move at a known velocity: their links get C here, and the wall's
+// momentum is summed per warp (constant part 2 alpha_r rho_bar c_r as exact
+// integers) before one atomic per wall and component.
+#pragma once
+
+#include "bl_internal.cuh"
+
+namespace bl {
+
+
+// blocks of 128 threads resident per SM: 8 caps the sweep at 64 registers
+#ifndef BL_LB_MINB
+#define BL_LB_MINB 8
+#endif
+
+// warp-level sum of the wall momenta, one atomic per wall and component
+// (all lanes of the warp call it)
+__device__ __forceinline__ void flush_wall_momentum(const WallAcc &wa, int &wkey, float (&wF)[3], int (&wK)[3]) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  unsigned pending = __ballot_sync(FULL, wkey >= 0);
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    const int lk = __shfl_sync(FULL, wkey, leader);
+    const bool mine = wkey == lk;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float vs = warp_sum(mine ? wF[k] : 0.f);
+      const int is = __reduce_add_sync(FULL, mine ? wK[k] : 0);
+      if (lane == leader) {
+        atomicAdd(&wa.F[3 * lk + k], (double)vs);
+        atomicAdd((unsigned long long *)&wa.K[3 * lk + k], (unsigned long long)(long long)is);
+      }
+    }
+    pending &= ~__ballot_sync(FULL, mine);
+    if (mine) wkey = -1;
+  }
+}
+
+// index of the slot from which node n reads direction r in a step of parity
+// PAR (xo, yo, zo: coordinates of its 3 x 3 x 3 neighbourhood, y and z
+// pre-multiplied by their strides)
+template <int PAR>
+__device__ __forceinline__ unsigned src_slot(int r, unsigned N, unsigned n, const unsigned xo[3], const unsigned yo[3],
+                                             const unsigned zo[3]) {
+  using D = D3Q19;
+  if (PAR == 0 || r == 0) return (unsigned)r * N + n;
+  return (unsigned)D::opp(r) * N + xo[1 - D::cx(r)] + yo[1 - D::cy(r)] + zo[1 - D::cz(r)];
+}
+
+// One fluid node of the sweep: moments, collision, streaming with
+// bounce-back and the wall momentum.  load(r, slot) gives the incoming
+// population of direction r (from the slot src_slot names).
+// FORCE: a body force is set (Guo forcing); TAU1: tau = 1, where the
+// relaxation gives the equilibrium itself
+template <class S, int PAR, bool FORCE, bool TAU1, class Load>
+__device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc &wa, int *status, unsigned n,
+                                            const unsigned xo[3], const unsigned yo[3], const unsigned zo[3],
+                                            uint32_t nbw, Load load, int &wkey, float (&wF)[3], int (&wK)[3]) {
+  using D = D3Q19;
+  const unsigned N = lv.N;
+  S *pop = reinterpret_cast<S *>(lv.pop);
+  if (nbw & NB_FLUID) {
+    // neighbour classes from the geometry pass: solid = any non-fluid node;
+    // the wall subset is looked up only next to a wall
+    const unsigned solid = nbw & NB_SOLID;
+    unsigned wall = 0;
+    if (nbw & NB_WALL) {
+      sfor<1, Q>([&](auto R) {
+        constexpr int r = decltype(R)::value;
+        if (solid & (1u << r)) {
+          const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
+          wall |= (lv.owner[nb] <= -2 ? 1u : 0u) << r;
+        }
+      });
+    }
+    // incoming populations of this node (layout of the step's parity)
+    float f[Q];
+    sfor<0, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      unsigned src;
+      if constexpr (PAR == 0 || r == 0) {
+        src = (unsigned)r * N + n;
+      } else {
+        src = (unsigned)D::opp(r) * N + xo[1 - D::cx(r)] + yo[1 - D::cy(r)] + zo[1 - D::cz(r)];
+      }
+      f[r] = load(r, src);
+    });
+    // moments (shifted: rho = rho_bar + sum f~, j = sum f~ c)
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    sfor<0, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      drho += f[r];
+      if constexpr (D::cx(r) != 0) jx += D::cx(r) * f[r];
+      if constexpr (D::cy(r) != 0) jy += D::cy(r) * f[r];
+      if constexpr (D::cz(r) != 0) jz += D::cz(r) * f[r];
+    });
+    const float rho = lv.rho0 + drho;
+    const float inv = 1.0f / rho;
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    if constexpr (FORCE) {
+      Fx = rho * lv.g[0];
+      Fy = rho * lv.g[1];
+      Fz = rho * lv.g[2];
+    }
+    const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv, uz = (jz + 0.5f * Fz) * inv;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    if (!(rho > 0.f) || !(uu < 0.09f)) atomicOr(status, ST_UNSTABLE);
+    const float om = lv.omega;
+    const float src_w = 1.0f - 0.5f * om;
+    const float uF = ux * Fx + uy * Fy + uz * Fz;
+    // relaxation toward the shifted equilibrium w (drho + rho t); rho t is
+    // taken as rho_bar t + drho t, which keeps the small deviation exact in
+    // FP32; the Guo source with cu = c.u, cF = c.F
+    auto relax = [&](float fr, float w, float t, float cu, float cF) {
+      const float feq = w * (drho + fmaf(drho, t, lv.rho0 * t));
+      float fs = TAU1 ? feq : fr - om * (fr - feq);
+      if constexpr (FORCE) fs += src_w * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
+      return fs;
+    };
+    // third-order equilibrium in pairs r, rbar = r + 1 (c_rbar = -c_r):
+    // t = E + O and E - O with the even part E = 4.5 cu^2 - 1.5 uu and the
+    // odd part O = cu (3 + 4.5 cu^2 - 4.5 uu)
+    const float a = 3.0f - 4.5f * uu, b = 1.5f * uu;
+    f[0] = relax(f[0], 12.0f / 36.0f, -b, 0.f, 0.f);
+    sfor<0, 9>([&](auto P) {
+      constexpr int r = 2 * decltype(P)::value + 1, rb = r + 1;
+      constexpr float w = D::m(r) / 36.0f;
+      float cu = 0.f, cF = 0.f;
+      if constexpr (D::cx(r) != 0) cu += D::cx(r) * ux;
+      if constexpr (D::cy(r) != 0) cu += D::cy(r) * uy;
+      if constexpr (D::cz(r) != 0) cu += D::cz(r) * uz;
+      if constexpr (FORCE) cF = D::cx(r) * Fx + D::cy(r) * Fy + D::cz(r) * Fz;
+      const float q = 4.5f * cu * cu;
+      const float E = q - b, O = cu * (a + q);
+      f[r] = relax(f[r], w, E + O, cu, cF);
+      f[rb] = relax(f[rb], w, E - O, -cu, -cF);
+    });
+    Store<S>::st(pop + n, f[0]);
+    if (wall) {
+      // links into a wall (next to a wall only): the moving-wall term C for
+      // the population returning along rbar, 6 alpha_rbar rho c_rbar . v_wall,
+      // and the momentum the wall receives
+      sfor<1, Q>([&](auto R) {
+        constexpr int r = decltype(R)::value;
+        if (wall & (1u << r)) {
+          const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
+          const int w = -2 - lv.owner[nb];
+          const float C = -(D::m(r) / 6.0f) * rho *
+                          (D::cx(r) * lv.wall_vel[w][0] + D::cy(r) * lv.wall_vel[w][1] + D::cz(r) * lv.wall_vel[w][2]);
+          const float dp = 2.0f * f[r] + C;
+          if (wkey != w && wkey >= 0) {
+            // a node touching two different walls: flush the first one directly
+            for (int k = 0; k < 3; ++k) {
+              atomicAdd(&wa.F[3 * wkey + k], (double)wF[k]);
+              atomicAdd((unsigned long long *)&wa.K[3 * wkey + k], (unsigned long long)(long long)wK[k]);
+              wF[k] = 0.f;
+              wK[k] = 0;
+            }
+          }
+          wkey = w;
+          wF[0] += dp * D::cx(r);
+          wF[1] += dp * D::cy(r);
+          wF[2] += dp * D::cz(r);
+          wK[0] += D::m(r) * D::cx(r);
+          wK[1] += D::m(r) * D::cy(r);
+          wK[2] += D::m(r) * D::cz(r);
+          f[r] += C;
+        }
+      });
+    }
+    // streaming, or bounce-back into the slot where the next step reads
+    // direction rbar where the neighbour is solid: one store per direction,
+    // its slot chosen without a branch (so that a warp mixing open and
+    // boundary nodes writes each row of slots with one instruction)
+    //   parity 0: open -> [rbar][n],       solid -> [r][n + c_r]
+    //   parity 1: open -> [r][n + c_r],    solid -> [rbar][n]
+    sfor<1, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      constexpr int rb = D::opp(r);
+      const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
+      const bool sol = (solid >> r) & 1u;
+      const unsigned dst = (sol != (PAR == 1)) ? (unsigned)r * N + nb : (unsigned)rb * N + n;
+      Store<S>::st(pop + dst, f[r]);
+    });
+    if (nbw & NB_CELL) lv.rho_b[n] = rho;
+  }
+}
+
+template <class S, int PAR, bool FORCE, bool TAU1>
+__global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, WallAcc wa, int *status) {
+  const int nx = lv.nx, ny = lv.ny;
+  const int x0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const bool valid = x0 < nx;
+  const int x = valid ? x0 : nx - 1;
+  const unsigned nxy = (unsigned)nx * (unsigned)ny;
+  const unsigned n = (unsigned)x + (unsigned)nx * (unsigned)y + nxy * (unsigned)z;
+  // coordinates of the 3 x 3 x 3 neighbourhood, periodic wrap on every axis
+  // (a walled axis has wall layers at both ends, never crossed by a link)
+  const unsigned xo[3] = {(unsigned)(x == 0 ? nx - 1 : x - 1), (unsigned)x, (unsigned)(x == nx - 1 ? 0 : x + 1)};
+  const unsigned yo[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1) * nx, (unsigned)y * nx,
+                          (unsigned)(y == ny - 1 ? 0 : y + 1) * nx};
+  const unsigned zo[3] = {(unsigned)(z == 0 ? lv.nz - 1 : z - 1) * nxy, (unsigned)z * nxy,
+                          (unsigned)(z == lv.nz - 1 ? 0 : z + 1) * nxy};
+  const S *pop = reinterpret_cast<const S *>(lv.pop);
+  const uint32_t nbw = valid ? lv.nbm[n] : 0u;
+  // wall momentum of this thread: wall id, variable part, constant-part integers
+  int wkey = -1;
+  float wF[3] = {0.f, 0.f, 0.f};
+  int wK[3] = {0, 0, 0};
+  if (nbw & NB_FLUID)
+    node_update<S, PAR, FORCE, TAU1>(lv, wa, status, n, xo, yo, zo, nbw,
+                                     [&](int, unsigned slot) { return Store<S>::ld(pop + slot); }, wkey, wF, wK);
+  flush_wall_momentum(wa, wkey, wF, wK);
+}
+
+// The FP32 sweep as a software pipeline along z: a block of 128 threads takes
+// a row segment and ZC consecutive z planes; while a node is collided,
+// the populations of the next PIPE_ST - 1 nodes above it are on their way
+// into shared memory (asynchronous 4-byte copies, one group per node).  The
+// neighbour word of a node is loaded just before its copies are issued;
+// solid nodes copy nothing.
+#ifndef BL_PIPE_ST
+#define BL_PIPE_ST 2
+#endif
+constexpr int PIPE_ST = BL_PIPE_ST;
+
+__device__ __forceinline__ void cp_async4(void *dst_smem, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int G>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(G) : "memory");
+}
+
+template <int PAR, bool FORCE, bool TAU1, int ZC>
+__global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv, WallAcc wa, int *status) {
+  __shared__ float stage[PIPE_ST][Q][128];
+  const int nx = lv.nx, ny = lv.ny, nz = lv.nz;
+  const int tx = threadIdx.x;
+  const int x0 = blockIdx.x * blockDim.x + tx;
+  const int y = blockIdx.y;
+  const int zb = blockIdx.z * ZC, ze = min(zb + ZC, nz);
+  const bool valid = x0 < nx;
+  const int x = valid ? x0 : nx - 1;
+  const unsigned N = lv.N;
+  const unsigned nxy = (unsigned)nx * (unsigned)ny;
+  const unsigned xo[3] = {(unsigned)(x == 0 ? nx - 1 : x - 1), (unsigned)x, (unsigned)(x == nx - 1 ? 0 : x + 1)};
+  const unsigned yo[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1) * nx, (unsigned)y * nx,
+                          (unsigned)(y == ny - 1 ? 0 : y + 1) * nx};
+  const unsigned rowb = (unsigned)x + (unsigned)nx * (unsigned)y;
+  const float *pop = reinterpret_cast<const float *>(lv.pop);
+  auto zoff = [&](int z, unsigned zo[3]) {
+    zo[0] = (unsigned)(z == 0 ? nz - 1 : z - 1) * nxy;
+    zo[1] = (unsigned)z * nxy;
+    zo[2] = (unsigned)(z == nz - 1 ? 0 : z + 1) * nxy;
+  };
+  // neighbour word of node z, and its copies into stage buffer b when fluid
+  auto issue = [&](int z, int b) -> uint32_t {
+    if (!valid || z >= ze) return 0u;
+    unsigned zo[3];
+    zoff(z, zo);
+    const unsigned n = rowb + zo[1];
+    const uint32_t w = lv.nbm[n];
+    if (w & NB_FLUID)
+      sfor<0, Q>([&](auto R) {
+        constexpr int r = decltype(R)::value;
+        cp_async4(&stage[b][r][tx], pop + src_slot<PAR>(r, N, n, xo, yo, zo));
+      });
+    return w;
+  };
+  int wkey = -1;
+  float wF[3] = {0.f, 0.f, 0.f};
+  int wK[3] = {0, 0, 0};
+  uint32_t w[PIPE_ST];  // neighbour words of the nodes in flight, oldest first
+#pragma unroll
+  for (int k = 0; k < PIPE_ST - 1; ++k) {
+    w[k] = issue(zb + k, k);
+    cp_async_commit();
+  }
+  for (int z = zb; z < ze; ++z) {
+    const int i = z - zb;
+    w[PIPE_ST - 1] = issue(z + PIPE_ST - 1, (i + PIPE_ST - 1) % PIPE_ST);
+    cp_async_commit();
+    cp_async_wait<PIPE_ST - 1>();  // the copies of node z have landed
+    const int b = i % PIPE_ST;
+    if (w[0] & NB_FLUID) {
+      unsigned zo[3];
+      zoff(z, zo);
+      node_update<float, PAR, FORCE, TAU1>(lv, wa, status, rowb + zo[1], xo, yo, zo, w[0],
+                                           [&](int r, unsigned) { return stage[b][r][tx]; }, wkey, wF, wK);
+    }
+#pragma unroll
+    for (int k = 0; k < PIPE_ST - 1; ++k) w[k] = w[k + 1];
+  }
+  cp_async_wait<0>();
+  flush_wall_momentum(wa, wkey, wF, wK);
+}
+
+// The sweep fed by bulk asynchronous copies (TMA, untiled): a block of
+// 128 threads takes a row segment of up to 128 nodes and ZC consecutive z
+// planes.  For each plane one thread copies the 19 source row segments and
+// the row of neighbour words into shared memory with cp.async.bulk, TS - 1
+// planes ahead of the plane being collided, each stage completing on its
+// mbarrier.  Parity 0 reads row (y, z) of array r; parity 1 reads row
+// (y - c_y, z - c_z) of array rbar, element x - c_x: from shared memory when
+// it lies in the segment (the whole row when the segment is the whole
+// periodic row), else directly from global memory.  Needs 16-byte aligned
+// rows: nx % 4 == 0 for FP32 storage, nx % 8 == 0 for BF16 / FP16; every
+// wait is bounded (ST_BARRIER after ~2^26 polls).
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned phase) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+// bounded wait: false if the copies did not land within the limit
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phase) {
+  for (int it = 0; it < (1 << 26); ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+template <class S, int PAR, bool FORCE, bool TAU1, int ZC, int TS>
+__global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc wa, int *status) {
+  using D = D3Q19;
+  __shared__ alignas(128) S sb[TS][Q][128];        // [stage][array][x]
+  __shared__ alignas(128) uint32_t sw[TS][128];    // [stage][x] neighbour words
+  __shared__ alignas(8) unsigned long long bar[TS];
+  __shared__ int s_ok;
+  const int nx = lv.nx, ny = lv.ny, nz = lv.nz;
+  const int tx = threadIdx.x;
+  const int x0 = blockIdx.x * 128;
+  const int W = min(128, nx - x0);  // segment width, a multiple of 4
+  const bool whole = W == nx;       // the segment is the whole row
+  const int y = blockIdx.y;
+  const int zb = blockIdx.z * ZC, ze = min(zb + ZC, nz);
+  const bool valid = tx < W;
+  const int x = x0 + (valid ? tx : W - 1);
+  const unsigned N = lv.N;
+  const unsigned nxy = (unsigned)nx * (unsigned)ny;
+  const unsigned xo[3] = {(unsigned)(x == 0 ? nx - 1 : x - 1), (unsigned)x, (unsigned)(x == nx - 1 ? 0 : x + 1)};
+  const unsigned yo[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1) * nx, (unsigned)y * nx,
+                          (unsigned)(y == ny - 1 ? 0 : y + 1) * nx};
+  const S *pop = reinterpret_cast<const S *>(lv.pop);
+  auto zoff = [&](int z, unsigned zo[3]) {
+    zo[0] = (unsigned)(z == 0 ? nz - 1 : z - 1) * nxy;
+    zo[1] = (unsigned)z * nxy;
+    zo[2] = (unsigned)(z == nz - 1 ? 0 : z + 1) * nxy;
+  };
+  // one thread: the copies of plane z into stage s
+  auto issue = [&](int z, int s) {
+    if (z >= ze) return;
+    unsigned zo[3];
+    zoff(z, zo);
+    const unsigned bytes = (unsigned)W * (unsigned)sizeof(S);
+    mbar_expect_tx(&bar[s], Q * bytes + (unsigned)W * 4u);
+    sfor<0, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      unsigned row;
+      if constexpr (PAR == 0 || r == 0) row = (unsigned)r * N + yo[1] + zo[1];
+      else row = (unsigned)D::opp(r) * N + yo[1 - D::cy(r)] + zo[1 - D::cz(r)];
+      bulk_g2s(&sb[s][r][0], pop + row + (unsigned)x0, bytes, &bar[s]);
+    });
+    bulk_g2s(&sw[s][0], lv.nbm + yo[1] + zo[1] + (unsigned)x0, (unsigned)W * 4u, &bar[s]);
+  };
+  if (tx == 0) {
+    for (int k = 0; k < TS; ++k) mbar_init(&bar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_ok = 1;
+  }
+  __syncthreads();
+  if (tx == 0)
+    for (int k = 0; k < TS - 1; ++k) issue(zb + k, k);
+  int wkey = -1;
+  float wF[3] = {0.f, 0.f, 0.f};
+  int wK[3] = {0, 0, 0};
+  int z = zb;
+  for (; z < ze; ++z) {
+    const int i = z - zb, s = i % TS;
+    if (tx == 0) issue(z + TS - 1, (i + TS - 1) % TS);  // that stage was freed by the last barrier
+    if (!mbar_wait(&bar[s], (unsigned)(i / TS) & 1u)) {
+      atomicOr(status, ST_BARRIER);
+      s_ok = 0;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const uint32_t w = valid ? sw[s][tx] : 0u;
+    if (w & NB_FLUID) {
+      unsigned zo[3];
+      zoff(z, zo);
+      node_update<S, PAR, FORCE, TAU1>(
+          lv, wa, status, (unsigned)x + yo[1] + zo[1], xo, yo, zo, w,
+          [&](int r, unsigned slot) -> float {
+            if (PAR == 0 || r == 0) return Store<S>::ld(&sb[s][r][tx]);
+            int j = tx - D::cx(r);
+            if (whole) j = j < 0 ? j + W : (j >= W ? j - W : j);
+            return (j >= 0 && j < W) ? Store<S>::ld(&sb[s][r][j]) : Store<S>::ld(pop + slot);
+          },
+          wkey, wF, wK);
+    }
+    __syncthreads();  // stage s is read: free for refill
+  }
+  if (z < ze && tx == 0) {
+    // gave up: let the copies still in flight land before the block exits
+    for (int k = 0; k < TS; ++k) mbar_wait(&bar[k], 0u), mbar_wait(&bar[k], 1u);
+  }
+  flush_wall_momentum(wa, wkey, wF, wK);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch of the sweep
+
+template <int PAR, bool FORCE, bool TAU1, int ZC>
+static void launch_pipe(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
+                        cudaStream_t st) {
+  const dim3 gp(grid.x, grid.y, (grid.z + ZC - 1) / ZC);
+  k_lb_step_pipe<PAR, FORCE, TAU1, ZC><<<gp, block, 0, st>>>(lv, wa, status);
+}
+
+template <class S, int PAR, bool FORCE, bool TAU1, int ZC, int TS>
+static void launch_bulk(const LatticeView &lv, dim3 grid, const WallAcc &wa, int *status, cudaStream_t st) {
+  const dim3 gp((lv.nx + 127) / 128, grid.y, (grid.z + ZC - 1) / ZC);
+  k_lb_step_bulk<S, PAR, FORCE, TAU1, ZC, TS><<<gp, 128, 0, st>>>(lv, wa, status);
+}
+
+// row length for the bulk-copy sweep: 16-byte aligned rows of the storage type
+__host__ __device__ inline bool bulk_rows_ok(int nx, int store_bytes) { return nx % (16 / store_bytes) == 0; }
+
+// sweep variants (LatticeView::sweep): 0 one node per thread; 1, 2 the FP32
+// pipeline over 4 or 8 planes; 3, 4 the bulk-copy pipeline over 8 or 4 planes
+// with 3 stages (any storage type with 16-byte aligned rows, else variant 0)
+template <class S, int PAR, bool FORCE, bool TAU1>
+static void launch_lb_variant(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
+                              cudaStream_t st) {
+  if constexpr (std::is_same<S, float>::value) {
+    if (lv.sweep == 1) return launch_pipe<PAR, FORCE, TAU1, 4>(lv, grid, block, wa, status, st);
+    if (lv.sweep == 2) return launch_pipe<PAR, FORCE, TAU1, 8>(lv, grid, block, wa, status, st);
+  }
+  if (bulk_rows_ok(lv.nx, (int)sizeof(S))) {
+    if (lv.sweep == 3) return launch_bulk<S, PAR, FORCE, TAU1, 8, 3>(lv, grid, wa, status, st);
+    if (lv.sweep == 4) return launch_bulk<S, PAR, FORCE, TAU1, 4, 3>(lv, grid, wa, status, st);
+  }
+  k_lb_step<S, PAR, FORCE, TAU1><<<grid, block, 0, st>>>(lv, wa, status);
+}
+
+template <class S, int PAR, bool FORCE>
+static void launch_lb_tau(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
+                          cudaStream_t st) {
+  if (lv.omega == 1.0f) launch_lb_variant<S, PAR, FORCE, true>(lv, grid, block, wa, status, st);
+  else launch_lb_variant<S, PAR, FORCE, false>(lv, grid, block, wa, status, st);
+}
+
+template <class S>
+static void launch_lb_typed(const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st) {
+  const int bx = lv.nx >= 128 ? 128 : ((lv.nx + 31) / 32) * 32;
+  dim3 block(bx, 1, 1);
+  dim3 grid((lv.nx + bx - 1) / bx, lv.ny, lv.nz);
+  if (par == 0) {
+    if (lv.has_force) launch_lb_tau<S, 0, true>(lv, grid, block, wa, status, st);
+    else launch_lb_tau<S, 0, false>(lv, grid, block, wa, status, st);
+  } else {
+    if (lv.has_force) launch_lb_tau<S, 1, true>(lv, grid, block, wa, status, st);
+    else launch_lb_tau<S, 1, false>(lv, grid, block, wa, status, st);
+  }
+}
+
+}  // namespace bl

@@ -1,0 +1,10 @@
+// lb_sweep_bf16.cu -- the lattice sweep (lb_sweep.cuh) for BF16 storage.
+#include "lb_sweep.cuh"
+
+namespace bl {
+
+void launch_lb_step_bf16(const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st) {
+  launch_lb_typed<__nv_bfloat16>(lv, par, wa, status, st);
+}
+
+}  // namespace bl

@@ -1,0 +1,10 @@
+// lb_sweep_f16.cu -- the lattice sweep (lb_sweep.cuh) for FP16 storage.
+#include "lb_sweep.cuh"
+
+namespace bl {
+
+void launch_lb_step_f16(const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st) {
+  launch_lb_typed<__half>(lv, par, wa, status, st);
+}
+
+}  // namespace bl

@@ -166,7 +166,7 @@ def make_workload(name):
 # mean of the even and odd launch) from the ncu capture summarised in
 # profiles/lattice_sweep_shear128_dram.md, valid for the sweep source it was
 # taken on (lb_sweep.cuh, first 16 hex digits of its SHA-256) and that workload only
-SWEEP_TRAFFIC = {"sha": "ad506e7e2729c60d", "config": "shear128", "store": 0, "bytes": 272235264}
+SWEEP_TRAFFIC = {"sha": "ad506e7e2729c60d", "config": "shear128", "store": 0, "bytes": 271938944}
 
 
 # the sweep kernel each storage type runs by default (FP32: variant 3 of the

@@ -1,14 +1,16 @@
 // bloodlb.cu -- host side of the C ABI declared in include/bloodlb.h.
 //
 // One context owns one lattice and its cells on one CUDA stream.  A time step
-// (arXiv:1005.2594, Sec. II and III) is enqueued as five kernel groups:
-//   0  fused collide / stream / bounce-back / momentum exchange / contact links
+// (arXiv:1005.2594, Sec. II and III) is enqueued as five kernel groups (the
+// groups of the timing read-out):
+//   0  fused collide / stream / bounce-back / wall momentum (the sweep)
 //   1  cell list (count, scan, scatter, per-bin sort)
-//   2  pair and wall potentials
-//   3  leap-frog + ownership claims
-//   4  resolve + fill/drain
-// The host never waits inside bl_step; device failures are raised into a
-// status word that bl_sync reads.
+//   2  pair and wall potentials (+ the learned correction)
+//   3  link sums, implicit solve + leap-frog, link correction, claims
+//   4  link lists and contact sums, resolve + fill/drain, neighbour words
+// Groups 1-2 and the link lists run on two side streams beside the sweep,
+// the claims beside the link correction.  The host never waits inside
+// bl_step; device failures are raised into a status word that bl_sync reads.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -32,15 +34,17 @@ struct bl_ctx {
   bl_lb_params lp;
   bl_particle_params pp;
   cudaStream_t stream;  // the caller's stream: every call is ordered on it
-  // the cell list and the potentials of a step run on a second stream,
-  // overlapped with the lattice sweep (they touch disjoint data)
+  // the cell list and the potentials of a step run on a second stream, the
+  // link lists on a third, overlapped with the lattice sweep (they touch
+  // disjoint data); the claims run on the second beside the link correction
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;     // cell list and potentials beside the sweep
   cudaEvent_t ev_fork2, ev_join2;   // claims beside the link correction
   cudaStream_t side2;
   cudaEvent_t ev_join3;             // link lists beside the sweep (second side stream)
-  // repeated steps replay a CUDA graph of two steps (even + odd parity) on
-  // an internal stream, forked from and joined to the caller's stream
+  // repeated steps replay a CUDA graph of two steps (even + odd parity), a
+  // lone step a one-step graph, on an internal stream forked from and joined
+  // to the caller's stream
   cudaStream_t gstream;
   cudaGraphExec_t gexec;
   cudaGraphExec_t g1exec[2];  // one step from parity 0 / 1 (for odd step counts)
@@ -50,8 +54,9 @@ struct bl_ctx {
   const void *g_kin;
   int64_t g_launches;
   int epoch;  // counts graph invalidations (cell arrays moved, walls or sweep variant changed)
-  // learned near-contact correction (bl_mlp_attach): the model, its gap
-  // cut-off and the close-pair buffers (32 pairs per cell)
+  // learned near-contact correction (bl_mlp_attach_range): the model, the
+  // gap and relative-speed window it is used in, the close-pair buffers
+  // (32 pairs per cell)
   const void *mlp;
   float gap_lo, gap_cut, speed_lo, speed_hi;
   PairBuf pb;

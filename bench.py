@@ -256,6 +256,8 @@ def run_gpu(args, ws, rank, local):
     # end-to-end through the C ABI with host buffers: each step uploads the
     # cell state (bl_particles_set), steps once and reads back forces and state
     e2e = run_e2e(sim, X.shape[0], N, args.e2e_steps, stream)
+    prec = precision_error(p, X, q, mask, args.store, args.precision_steps, stream) \
+        if args.store != 0 and args.precision_steps > 0 else None
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
@@ -277,6 +279,8 @@ def run_gpu(args, ws, rank, local):
         "clocks": clk,
         "e2e": e2e,
     }
+    if prec is not None:
+        out["precision_error"] = prec
     return out, (p, X, q, desc)
 
 
@@ -454,6 +458,47 @@ def run_learned(args, ws, rank, local):
     return out
 
 
+def precision_error(p, X, q, mask, store, steps, stream):
+    """Reduced-precision storage against FP32 storage (which matches the FP64
+    oracle to 1e-5 over 100 steps at 32^3): both from the same state, `steps`
+    steps.  Over that many steps a cell can cross a node a step earlier in one
+    run than in the other; the node is then refilled at another time and its
+    velocity differs by the cell's, so besides the RMS error over the common
+    fluid nodes the largest error is given over the nodes at least 3 nodes
+    away from any owner difference, with the number of owner differences;
+    cell positions: the largest difference in lattice units."""
+    import numpy as np
+    from scipy import ndimage
+
+    from paper_1005_2594_gb300 import bloodlb as bl
+
+    out = []
+    for st in (0, store):
+        sim = bl.Simulation(p, store_dtype=st, stream=stream.cuda_stream, wall_mask=mask)
+        sim.set_particles(X, q)
+        sim.step(steps)
+        sim.sync()
+        _, u, own = sim.fields()
+        out.append((u, own, sim.particles()["X"]))
+        sim.close()
+    (u0, o0, X0), (u1, o1, X1) = out
+    fl = (o0 == -1) & (o1 == -1)
+    diff = (o0 != o1).reshape(p["nz"], p["ny"], p["nx"])
+    near = ndimage.binary_dilation(diff, structure=np.ones((3, 3, 3), bool), iterations=3,
+                                   border_value=0).reshape(-1)
+    away = fl & ~near
+    e = np.linalg.norm(u1 - u0, axis=1)
+    scale = np.abs(u0[fl]).max()
+    d = X1 - X0
+    for k, n in enumerate((p["nx"], p["ny"], p["nz"])):
+        d[:, k] -= n * np.round(d[:, k] / n)
+    return {"vs": "FP32 storage", "steps": steps,
+            "u_rel_rms": float(np.sqrt((e[fl] ** 2).mean() / (np.linalg.norm(u0[fl], axis=1) ** 2).mean())),
+            "u_rel_max_away": float(e[away].max() / scale) if away.any() else None,
+            "u_rel_max": float(e[fl].max() / scale),
+            "owner_differences": int(diff.sum()), "X_max_abs": float(np.abs(d).max())}
+
+
 def run_rheology(args, ws, rank, local):
     """Apparent viscosity (relative to the plasma) of a tube suspension: a
     tube of radius 30 and length 128 with (7,7,3) cells at 35 % of the lumen,
@@ -618,6 +663,8 @@ def main():
     ap.add_argument("--store", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision-steps", type=int, default=1000,
+                    help="with --store 1|2: steps of the error check against FP32 storage (0: none)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()

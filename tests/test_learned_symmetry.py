@@ -104,3 +104,23 @@ def test_augment_keeps_the_originals_and_unit_quaternions():
     # lengths of the polar and axial vectors are invariant
     for a, b in ((0, 3), (8, 11), (11, 14)):
         np.testing.assert_allclose(np.linalg.norm(Xa[:, a:b], axis=1), np.tile(np.linalg.norm(X[:, a:b], axis=1), 4))
+
+
+def test_approach_runs_start_at_the_stated_gap():
+    """The training runs' set-up: two cells gap0 apart (the oracle's contact
+    distance with the fluid-coupling half-axes), moving towards each other
+    along the line of centres with equal and opposite velocities."""
+    from paper_1005_2594_gb300 import learned
+
+    rng = np.random.default_rng(4)
+    R = (7.0, 3.0)
+    for _ in range(20):
+        X, q, V, W, steps = learned.approach_setup(rng, L=48, R=R, gap0=4.5)
+        r = X[1] - X[0]
+        n = r / np.linalg.norm(r)
+        oi, oj = mlp.rotmat(q[0])[:, 2], mlp.rotmat(q[1])[:, 2]
+        gap = np.linalg.norm(r) - mlp.contact_distance(R[1], R[0], oi, oj, n)
+        assert abs(gap - 4.5) < 1e-9
+        np.testing.assert_allclose(V[0], -V[1], atol=1e-15)
+        assert V[0] @ n > 0 and V[1] @ n < 0  # approaching
+        assert steps * 2 * (V[0] @ n) <= 4.5 - 0.2 + 1e-9  # stops short of contact

@@ -113,6 +113,9 @@ int bl_walls_set(bl_ctx *c, const uint8_t *mask);
    gives no impulses.  A later call with the same n re-discretises against
    the current owner map with the first-arrival rule and fill/drain
    impulses, exactly as a time step does (Sec. II).  n may be 0.
+   The first call waits for the device; a later call is enqueued on the
+   stream and returns at once (its device errors surface at the next
+   bl_sync); the host arrays may be reused when it returns.
    Requirements (BL_EINVAL otherwise): r_cut >= max(R_par, R_perp) + 1, so
    that the cells covering a node lie in the cell-list bins around it; every
    periodic length >= 2 max(R_par, R_perp) + 4, so that a cell does not

@@ -507,7 +507,10 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
   else launch_nbm_update(c->lv, c->pv, c->chg, c->stream, &c->launches);
   std::swap(c->pv.kin, c->pv.kin_next);
   if (check_launch(c, "particles_set")) return c->sticky;
-  CU(cudaStreamSynchronize(c->stream));
+  // a first placement waits (device errors surface here); a re-placement
+  // returns at once like bl_step: the state was staged by the copy call
+  // (pageable host memory), and device errors surface at the next bl_sync
+  if (first) CU(cudaStreamSynchronize(c->stream));
   return BL_OK;
 }
 

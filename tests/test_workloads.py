@@ -42,3 +42,22 @@ def test_ensemble_members_are_uneven_and_seeded():
     for p, X, q, desc in boxes:
         assert p["periodic"] == (1, 1, 0) and len(X) > 0
         assert np.abs(p["wall_vel"][5, 0]) > 0
+
+
+def test_refined_tube_is_the_same_system_under_diffusive_scaling():
+    """rheology.tube_case(k): lengths x k (box, radius, cells, positions about
+    the axis), body force / k^3, contact strength x k; the same cells."""
+    from paper_1005_2594_gb300 import rheology
+
+    p1, X1, q1, m1 = rheology.tube_case(1)
+    p2, X2, q2, m2 = rheology.tube_case(2)
+    assert (p2["nx"], p2["ny"], p2["nz"]) == (2 * p1["nx"], 2 * p1["ny"], 2 * p1["nz"])
+    assert p2["R_perp"] == 2 * p1["R_perp"] and p2["R_par"] == 2 * p1["R_par"]
+    assert abs(p2["g"][0] * 8 - p1["g"][0]) < 1e-18 and p2["eps"] == 2 * p1["eps"]
+    np.testing.assert_array_equal(q2, q1)
+    c1, c2 = (p1["ny"] - 1) / 2.0, (p2["ny"] - 1) / 2.0
+    np.testing.assert_allclose(X2[:, 0], 2 * X1[:, 0])
+    np.testing.assert_allclose(X2[:, 1:] - c2, 2 * (X1[:, 1:] - c1))  # same place relative to the axis
+    # the lumen doubles in radius: 4x the wall-free cross-section, 8x the volume up to the staircase
+    ratio = (m2 == 0).sum() / (m1 == 0).sum()
+    assert 7.8 < ratio < 8.2

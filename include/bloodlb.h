@@ -173,6 +173,15 @@ int bl_populations_set(bl_ctx *c, const double *pop);
 int bl_boundary_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count);
 int bl_contact_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count);
 
+/* The per-cell bounce-link lists that the step sums the link momentum of
+   Eq. (deltap) over and gives the moving-boundary term of Eq. (c) to, built
+   by the step's own kernel from the current owner map: (fluid node y,
+   direction r with y + c_r inside cell p, p) as int32 triples in (node, r)
+   order, i.e. the boundary links of bl_boundary_links_get whose owner is a
+   cell.  Writes min(count, cap) triples to the host array out and the full
+   count to *count; BL_EOVERFLOW if a list outgrew its capacity. */
+int bl_cell_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count);
+
 /* Cell list of the current positions in canonical (bin, id) order:
    nb_k = max(1, floor(N_k / r_cut)), bin_k = floor((X_k / N_k) nb_k)
    clamped; start has nb0 nb1 nb2 + 1 entries, ids n entries (host).
@@ -188,9 +197,11 @@ int bl_cell_list_get(bl_ctx *c, int32_t nb[3], int32_t *start, int32_t *ids);
    ids (n int32) on cuda_stream; nb receives the bin counts (host).  Scratch
    lives in a fixed array reserved on every GPU that loads the library
    (2.25 MiB, held until exit): at most 65536 cells and 262144 bins, larger
-   requests return BL_EINVAL.  The first call on a device looks up that array
-   and should come before any stream capture; calls that overlap on the GPU
-   share the array and race.  No context is needed; errors are returned, not
+   requests return BL_EINVAL (nb is then left untouched).  The first call on
+   a device looks up that array and should come before any stream capture;
+   the address is cached per device for the life of the process, which
+   assumes the device's primary context and no cudaDeviceReset in between.
+   Calls that overlap on the GPU share the array and race.  No context is needed; errors are returned, not
    kept. */
 int bl_cell_list_build_static(const double *X, int n, const int32_t dims[3], double r_cut, int32_t nb[3],
                               int32_t *start, int32_t *ids, void *cuda_stream);

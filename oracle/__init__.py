@@ -73,6 +73,7 @@ def lib():
         L.orc_get_particles.argtypes = [vp, D, D, D, D, D, D]
         L.orc_get_force_parts.argtypes = [vp, D, D, D, D, D, D, D]
         L.orc_get_pending.argtypes = [vp, D, D]
+        L.orc_get_wall_parts.argtypes = [vp, D, D]
         L.orc_get_counters.argtypes = [vp, D, D]
         L.orc_boundary_links.restype = ctypes.c_long
         L.orc_boundary_links.argtypes = [vp, I, ctypes.c_long]
@@ -230,6 +231,12 @@ class Oracle:
         out = {k: np.zeros((n, 3)) for k in ("Fh", "Th", "Fc", "Tc", "Fp", "Tp", "Om")}
         lib().orc_get_force_parts(self._h, *(_dp(out[k]) for k in ("Fh", "Th", "Fc", "Tc", "Fp", "Tp", "Om")))
         return out
+
+    def wall_parts(self):
+        """wall-potential part (Eq. sigmaw) of the last step's Fp, Tp"""
+        Fw, Tw = np.zeros((self.np, 3)), np.zeros((self.np, 3))
+        lib().orc_get_wall_parts(self._h, _dp(Fw), _dp(Tw))
+        return Fw, Tw
 
     def pending(self):
         PF, PT = np.zeros((self.np, 3)), np.zeros((self.np, 3))

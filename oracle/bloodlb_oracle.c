@@ -107,6 +107,7 @@ typedef struct {
   double *Fh, *Th;            /* link forces of the last step: bounce-back + contact */
   double *Fc, *Tc;            /* contact-link part only (diagnostic) */
   double *Fp, *Tp;            /* pair + wall potential forces of the last step */
+  double *Fw, *Tw;            /* wall part of Fp, Tp alone (diagnostic) */
   double *PF, *PT;            /* fill/drain impulses waiting for the next integration */
   double *Ftot, *Ttot;        /* total force / torque used in the last integration */
   double wallmom[NWALL][3];   /* momentum given to each wall by its links in the last step */
@@ -436,7 +437,7 @@ static void *xcalloc(long n, long sz) {
 
 static void free_particles(orc_state *s) {
   double **arrs[] = {&s->X, &s->q, &s->V, &s->L, &s->Om, &s->Fh, &s->Th, &s->Fc, &s->Tc,
-                     &s->Fp, &s->Tp, &s->PF, &s->PT, &s->Ftot, &s->Ttot};
+                     &s->Fp, &s->Tp, &s->Fw, &s->Tw, &s->PF, &s->PT, &s->Ftot, &s->Ttot};
   for (unsigned i = 0; i < sizeof(arrs) / sizeof(arrs[0]); ++i) {
     free(*arrs[i]);
     *arrs[i] = NULL;
@@ -597,7 +598,7 @@ int orc_set_particles(orc_state *s, int np, const double *X, const double *q, co
     free_particles(s);
     s->np = np;
     double **arrs3[] = {&s->X, &s->V, &s->L, &s->Om, &s->Fh, &s->Th, &s->Fc, &s->Tc,
-                        &s->Fp, &s->Tp, &s->PF, &s->PT, &s->Ftot, &s->Ttot};
+                        &s->Fp, &s->Tp, &s->Fw, &s->Tw, &s->PF, &s->PT, &s->Ftot, &s->Ttot};
     for (unsigned i = 0; i < sizeof(arrs3) / sizeof(arrs3[0]); ++i)
       *arrs3[i] = (double *)xcalloc(3 * (long)np, sizeof(double));
     s->q = (double *)xcalloc(4 * (long)np, sizeof(double));
@@ -618,7 +619,8 @@ static void step_once(orc_state *s) {
   orc_params *p = &s->p;
   const long N = s->N;
   const double cs2 = 1.0 / 3.0;
-  for (int k = 0; k < 3 * s->np; ++k) s->Fh[k] = s->Th[k] = s->Fc[k] = s->Tc[k] = s->Fp[k] = s->Tp[k] = 0.0;
+  for (int k = 0; k < 3 * s->np; ++k)
+    s->Fh[k] = s->Th[k] = s->Fc[k] = s->Tc[k] = s->Fp[k] = s->Tp[k] = s->Fw[k] = s->Tw[k] = 0.0;
   memset(s->wallmom, 0, sizeof(s->wallmom));
   s->sumC = 0.0;
 
@@ -690,7 +692,10 @@ static void step_once(orc_state *s) {
         for (int k = 0; k < 3; ++k) rv[k] = min_image(p, k, xc[k] - s->X[3 * i + k]);
         double Fi[3], Ti[3];
         if (orc_wall(p, rv, &o[3 * i], Fi, Ti) > 0.0)
-          for (int k = 0; k < 3; ++k) { s->Fp[3 * i + k] += Fi[k]; s->Tp[3 * i + k] += Ti[k]; }
+          for (int k = 0; k < 3; ++k) {
+            s->Fp[3 * i + k] += Fi[k]; s->Tp[3 * i + k] += Ti[k];
+            s->Fw[3 * i + k] += Fi[k]; s->Tw[3 * i + k] += Ti[k];
+          }
       }
     }
   }
@@ -879,6 +884,13 @@ void orc_get_force_parts(const orc_state *s, double *Fh, double *Th, double *Fc,
   if (Fp) memcpy(Fp, s->Fp, sizeof(double) * n3);
   if (Tp) memcpy(Tp, s->Tp, sizeof(double) * n3);
   if (Om) memcpy(Om, s->Om, sizeof(double) * n3);
+}
+
+/* wall-potential part of the last step's Fp, Tp (Eq. sigmaw alone) */
+void orc_get_wall_parts(const orc_state *s, double *Fw, double *Tw) {
+  long n3 = 3L * s->np;
+  if (Fw) memcpy(Fw, s->Fw, sizeof(double) * n3);
+  if (Tw) memcpy(Tw, s->Tw, sizeof(double) * n3);
 }
 
 void orc_get_pending(const orc_state *s, double *PF, double *PT) {

@@ -33,7 +33,7 @@ TIMING_GROUPS = ("lattice_sweep", "cell_list", "potentials", "leapfrog_claims", 
 ABI_FUNCTIONS = (
     "bl_lb_init", "bl_walls_set", "bl_particles_set", "bl_step", "bl_fields_get", "bl_forces_get",
     "bl_force_parts_get", "bl_wall_momentum_get", "bl_populations_get", "bl_populations_set",
-    "bl_boundary_links_get", "bl_contact_links_get", "bl_cell_list_get", "bl_cell_list_build_static",
+    "bl_boundary_links_get", "bl_contact_links_get", "bl_cell_links_get", "bl_cell_list_get", "bl_cell_list_build_static",
     "bl_sweep_variant", "bl_autotune", "bl_ensemble_create", "bl_ensemble_step", "bl_ensemble_sync",
     "bl_ensemble_destroy", "bl_mlp_create", "bl_mlp_params_set", "bl_mlp_params_get", "bl_mlp_forward",
     "bl_mlp_grad", "bl_mlp_adam", "bl_mlp_sync", "bl_mlp_destroy", "bl_mlp_attach", "bl_mlp_attach_range", "bl_pair_features",
@@ -98,6 +98,7 @@ def lib():
         "bl_populations_set": (ctypes.c_int, [vp, D]),
         "bl_boundary_links_get": (ctypes.c_int, [vp, I, i64, ctypes.POINTER(i64)]),
         "bl_contact_links_get": (ctypes.c_int, [vp, I, i64, ctypes.POINTER(i64)]),
+        "bl_cell_links_get": (ctypes.c_int, [vp, I, i64, ctypes.POINTER(i64)]),
         "bl_cell_list_get": (ctypes.c_int, [vp, I, I, I]),
         "bl_cell_list_build_static": (ctypes.c_int, [vp, ctypes.c_int, I, ctypes.c_double, I, vp, vp, vp]),
         "bl_sweep_variant": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -388,6 +389,10 @@ def bl_contact_links_get(ctx):
     return _links(lib().bl_contact_links_get, ctx)
 
 
+def bl_cell_links_get(ctx):
+    return _links(lib().bl_cell_links_get, ctx)
+
+
 def bl_cell_list_get(ctx, n):
     nb = np.zeros(3, dtype=np.int32)
     _check(ctx, lib().bl_cell_list_get(ctx, _ip(nb), None, None))
@@ -494,6 +499,10 @@ class Simulation:
 
     def contact_links(self):
         return bl_contact_links_get(self.ctx)
+
+    def cell_links(self):
+        """the step's own per-cell bounce-link lists, (node, r, cell) sorted"""
+        return bl_cell_links_get(self.ctx)
 
     def cell_list(self):
         return bl_cell_list_get(self.ctx, self.n)

@@ -128,6 +128,7 @@ struct PartView {
   double inv_rpar2, inv_rperp2, R_par, R_perp;
   float sig_par, sig_perp, eps, eps_w, mu, nu, chi_prime, r_cut;
   float chi, sigbar, sigbar_w, chi_w, sigw_max;
+  double chi_d, sigbar_d, sigbar_w_d, chi_w_d;  // the same in FP64 (contact geometry)
 };
 
 struct CellListView {

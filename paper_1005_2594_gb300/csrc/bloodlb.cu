@@ -16,6 +16,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <climits>
 #include <utility>
 #include <vector>
@@ -363,14 +364,16 @@ static int alloc_particles(bl_ctx *c, int n) {
   CU(cudaMemsetAsync(pv.touched_count, 0, sizeof(int) * (size_t)n, c->stream));
   // cell list bins: nb_k = max(1, floor(N_k / r_cut))
   const int dims[3] = {c->lv.nx, c->lv.ny, c->lv.nz};
-  long long nbins = 1;
+  // bin counts in double, checked before any conversion to int
+  double nbins_d = 1.0;
   for (int k = 0; k < 3; ++k) {
-    int nb = (int)floor((double)dims[k] / c->pp.r_cut);
-    if (nb < 1) nb = 1;
-    c->cl.nb[k] = nb;
-    nbins *= nb;
+    const double nb = fmax(1.0, floor((double)dims[k] / c->pp.r_cut));
+    if (!(nb <= (double)(1 << 26))) return fail(c, BL_EINVAL, "r_cut gives too many bins");
+    c->cl.nb[k] = (int)nb;
+    nbins_d *= nb;
   }
-  if (nbins > (1 << 26)) return fail(c, BL_EINVAL, "r_cut gives too many bins");
+  if (!(nbins_d <= (double)(1 << 26))) return fail(c, BL_EINVAL, "r_cut gives too many bins");
+  const long long nbins = (long long)nbins_d;
   c->cl.nbins = (int)nbins;
   CU(cudaMalloc(&c->cl.bin_of, sizeof(int) * (size_t)n));
   CU(cudaMalloc(&c->cl.count, sizeof(int) * (size_t)nbins));
@@ -431,6 +434,10 @@ static void fill_particle_constants(bl_ctx *c) {
   pv.sigbar_w = (float)sqrt(sq2 + sw2);
   const double chi_w = (sp2 - sq2) / (sp2 + sw2);
   pv.chi_w = (float)chi_w;
+  pv.chi_d = (sp2 - sq2) / (sp2 + sq2);
+  pv.sigbar_d = 2.0 * pp.sig_perp;
+  pv.sigbar_w_d = sqrt(sq2 + sw2);
+  pv.chi_w_d = chi_w;
   // largest cell-wall range: face on sqrt(sig_par^2 + sig_w^2), side on sigbar_w
   pv.sigw_max = (float)(fmax(sqrt(sq2 + sw2), sqrt(sp2 + sw2)) * 1.0001);
 }
@@ -823,6 +830,49 @@ extern "C" int bl_boundary_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64
 
 extern "C" int bl_contact_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count) {
   return links_get(c, 1, out, cap, count);
+}
+
+extern "C" int bl_cell_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count) {
+  if (!c || !count || cap < 0) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  *count = 0;
+  if (c->np == 0) return BL_OK;
+  // the lists the next step sums over, built by the step's own kernel from
+  // the current owner map and kinematics
+  launch_cell_links(c->lv, c->pv, c->stream, &c->launches);
+  if (check_launch(c, "cell links")) return c->sticky;
+  const int n = c->np, capl = c->pv.lk_cap;
+  std::vector<int> cnt(n);
+  std::vector<unsigned long long> lk((size_t)n * capl);
+  CU(cudaMemcpyAsync(cnt.data(), c->pv.lk_count, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(lk.data(), c->pv.lk, sizeof(unsigned long long) * lk.size(), cudaMemcpyDeviceToHost, c->stream));
+  if (read_status(c)) return c->sticky;
+  struct Link {
+    long long node;
+    int r, p;
+  };
+  std::vector<Link> links;
+  const long long nx = c->lv.nx, ny = c->lv.ny;
+  for (int p = 0; p < n; ++p) {
+    if (cnt[p] > capl) return fail(c, BL_EOVERFLOW, "cell %d: link list overflow", p);
+    for (int i = 0; i < cnt[p]; ++i) {
+      const unsigned long long e = lk[(size_t)p * capl + i];
+      const long long x = (long long)((e >> 5) & 0xFFFFFull), y = (long long)((e >> 25) & 0xFFFFFull),
+                      z = (long long)(e >> 45);
+      links.push_back(Link{x + nx * (y + ny * z), (int)(e & 31ull), p});
+    }
+  }
+  std::sort(links.begin(), links.end(), [](const Link &a, const Link &b) {
+    return a.node != b.node ? a.node < b.node : (a.r != b.r ? a.r < b.r : a.p < b.p);
+  });
+  *count = (int64_t)links.size();
+  if (out)
+    for (int64_t k = 0; k < (int64_t)links.size() && k < cap; ++k) {
+      out[3 * k] = (int32_t)links[k].node;
+      out[3 * k + 1] = links[k].r;
+      out[3 * k + 2] = links[k].p;
+    }
+  return BL_OK;
 }
 
 extern "C" int bl_cell_list_get(bl_ctx *c, int32_t nb[3], int32_t *start, int32_t *ids) {

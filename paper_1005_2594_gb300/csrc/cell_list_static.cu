@@ -14,7 +14,10 @@
 //
 // Set-up: the first call on a device looks up the device address of that
 // array (cudaGetSymbolAddress) with the device current and caches it; make
-// this first call before any stream capture.  Every later call on the device
+// this first call before any stream capture.  The cache is kept per device
+// ordinal for the life of the process: it assumes the device's primary
+// context (the one the CUDA runtime and PyTorch use) and no cudaDeviceReset
+// between calls, after which the cached address would be stale.  Every later call on the device
 // reuses the same array, so calls that overlap on the GPU (on different
 // streams, or from several threads) race on it and must be serialised by the
 // caller.  The counters are cleared at the start of each call.
@@ -58,18 +61,24 @@ extern "C" int bl_cell_list_build_static(const double *X, int n, const int32_t d
   if (n > kMaxCells) return BL_EINVAL;  // more cells than the reserved scratch holds
   if (n > 0 && (!X || !ids)) return BL_EINVAL;
   if (!start) return BL_EINVAL;
-  long long nbins = 1;
+  // bin counts in double, checked against the reserved scratch before any
+  // conversion to int (a tiny r_cut gives quotients far beyond INT_MAX);
+  // nb is written only once the request is accepted
+  int nbk[3];
+  double nbins_d = 1.0;
   for (int k = 0; k < 3; ++k) {
     if (dims[k] < 1) return BL_EINVAL;
-    int b = (int)floor((double)dims[k] / r_cut);
-    if (b < 1) b = 1;
-    nb[k] = b;
-    nbins *= b;
+    const double b = fmax(1.0, floor((double)dims[k] / r_cut));
+    if (!(b <= (double)kMaxBins)) return BL_EINVAL;
+    nbk[k] = (int)b;
+    nbins_d *= b;
   }
-  if (nbins > kMaxBins) return BL_EINVAL;  // more bins than the reserved scratch holds
+  if (!(nbins_d <= (double)kMaxBins)) return BL_EINVAL;  // more bins than the reserved scratch holds
+  const long long nbins = (long long)nbins_d;
   int *scratch = nullptr;
   int rc = scratch_of_current_device(&scratch);
   if (rc != BL_OK) return rc;
+  for (int k = 0; k < 3; ++k) nb[k] = nbk[k];
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   bl::CellListView cl{};
   for (int k = 0; k < 3; ++k) cl.nb[k] = nb[k];

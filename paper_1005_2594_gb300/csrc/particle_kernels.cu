@@ -126,22 +126,38 @@ __global__ void k_cl_sort(CellListView cl) {
 // ---------------------------------------------------------------------------
 // potentials (FP32)
 
-// cell-cell pair, force and torque on i; r = X_j - X_i
-__device__ __forceinline__ void bp_pair(const float r[3], const float oi[3], const float oj[3], const PartView &pv,
-                                        float F[3], float T[3]) {
-  const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-  if (!(r2 > 0.f)) return;
-  const float rl = sqrtf(r2), ir = 1.0f / rl;
-  const float rh[3] = {r[0] * ir, r[1] * ir, r[2] * ir};
-  const float a = rh[0] * oi[0] + rh[1] * oi[1] + rh[2] * oi[2];
-  const float b = rh[0] * oj[0] + rh[1] * oj[1] + rh[2] * oj[2];
-  const float c = oi[0] * oj[0] + oi[1] * oj[1] + oi[2] * oj[2];
+// Contact geometry in FP64.  In contact the overlap h = 1 - r / sigma is a
+// small difference of O(1) numbers (h ~ 1e-2), and the force is
+// proportional to it: rounding r and sigma to FP32 (~1e-7) would put ~1e-5
+// into the force.  So r (from the FP64 positions), the angles a, b, c, the
+// shape function S, sigma and h are formed in FP64; the strength, its
+// derivatives and the force and torque, which multiply h without cancelling
+// it, in FP32.
+
+// cell-cell pair, force and torque on i; r = X_j - X_i (Eqs. phi, epsilon,
+// sigma; the Gay-Berne factor eps2^mu of the variant)
+__device__ __forceinline__ void bp_pair(const double rd[3], const double oid[3], const double ojd[3],
+                                        const PartView &pv, float F[3], float T[3]) {
+  const double r2d = rd[0] * rd[0] + rd[1] * rd[1] + rd[2] * rd[2];
+  if (!(r2d > 0.0)) return;
+  const double rld = sqrt(r2d), ird = 1.0 / rld;
+  const double rhd[3] = {rd[0] * ird, rd[1] * ird, rd[2] * ird};
+  const double ad = rhd[0] * oid[0] + rhd[1] * oid[1] + rhd[2] * oid[2];
+  const double bd = rhd[0] * ojd[0] + rhd[1] * ojd[1] + rhd[2] * ojd[2];
+  const double cd = oid[0] * ojd[0] + oid[1] * ojd[1] + oid[2] * ojd[2];
+  const double apd = ad + bd, amd = ad - bd;
+  const double Sd = 1.0 - 0.5 * pv.chi_d * (apd * apd / (1.0 + pv.chi_d * cd) + amd * amd / (1.0 - pv.chi_d * cd));
+  const double sigd = pv.sigbar_d / sqrt(Sd);
+  if (rld >= sigd) return;
+  const float h = (float)(1.0 - rld / sigd);
+  const float rl = (float)rld, ir = (float)ird, sigma = (float)sigd, S = (float)Sd;
+  const float rh[3] = {(float)rhd[0], (float)rhd[1], (float)rhd[2]};
+  const float oi[3] = {(float)oid[0], (float)oid[1], (float)oid[2]};
+  const float oj[3] = {(float)ojd[0], (float)ojd[1], (float)ojd[2]};
+  const float a = (float)ad, b = (float)bd, c = (float)cd;
   const float chi = pv.chi;
-  const float ap = a + b, am = a - b;
+  const float ap = (float)apd, am = (float)amd;
   const float dp = 1.0f + chi * c, dm = 1.0f - chi * c;
-  const float S = 1.0f - 0.5f * chi * (ap * ap / dp + am * am / dm);
-  const float sigma = pv.sigbar * rsqrtf(S);
-  if (rl >= sigma) return;
   const float e1 = 1.0f - chi * chi * c * c;
   float eps = pv.eps * (pv.nu == 1.0f ? rsqrtf(e1) : powf(e1, -0.5f * pv.nu));
   float e2 = 1.0f, de2a = 0.f, de2b = 0.f, de2c = 0.f;
@@ -160,7 +176,6 @@ __device__ __forceinline__ void bp_pair(const float r[3], const float oi[3], con
   const float eps_a = pv.mu != 0.0f ? eps * pv.mu * de2a / e2 : 0.f;
   const float eps_b = pv.mu != 0.0f ? eps * pv.mu * de2b / e2 : 0.f;
   const float eps_c = eps * (pv.nu * chi * chi * c / e1 + (pv.mu != 0.0f ? pv.mu * de2c / e2 : 0.f));
-  const float h = 1.0f - rl / sigma;
   const float k = eps * h * rl / (sigma * S);
   const float phi_r = -2.0f * eps * h / sigma;
   const float phi_a = h * h * eps_a - k * dSa;
@@ -176,18 +191,22 @@ __device__ __forceinline__ void bp_pair(const float r[3], const float oi[3], con
   T[2] -= oi[0] * dpi[1] - oi[1] * dpi[0];
 }
 
-// cell-wall sphere, force and torque on the cell; r = x_wall - X
-__device__ __forceinline__ void bp_wall(const float r[3], const float oi[3], const PartView &pv, float F[3], float T[3]) {
-  const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-  if (!(r2 > 0.f) || r2 >= pv.sigw_max * pv.sigw_max) return;
-  const float rl = sqrtf(r2), ir = 1.0f / rl;
-  const float rh[3] = {r[0] * ir, r[1] * ir, r[2] * ir};
-  const float a = rh[0] * oi[0] + rh[1] * oi[1] + rh[2] * oi[2];
-  const float D = 1.0f - pv.chi_w * a * a;
-  const float sigma = pv.sigbar_w * rsqrtf(D);
-  if (rl >= sigma) return;
+// cell-wall sphere (Eq. sigmaw), force and torque on the cell; r = x_wall - X
+__device__ __forceinline__ void bp_wall(const double rd[3], const double oid[3], const PartView &pv, float F[3],
+                                        float T[3]) {
+  const double r2d = rd[0] * rd[0] + rd[1] * rd[1] + rd[2] * rd[2];
+  if (!(r2d > 0.0)) return;
+  const double rld = sqrt(r2d), ird = 1.0 / rld;
+  const double rhd[3] = {rd[0] * ird, rd[1] * ird, rd[2] * ird};
+  const double ad = rhd[0] * oid[0] + rhd[1] * oid[1] + rhd[2] * oid[2];
+  const double Dd = 1.0 - pv.chi_w_d * ad * ad;
+  const double sigd = pv.sigbar_w_d / sqrt(Dd);
+  if (rld >= sigd) return;
+  const float h = (float)(1.0 - rld / sigd);
+  const float rl = (float)rld, ir = (float)ird, sigma = (float)sigd, D = (float)Dd, a = (float)ad;
+  const float rh[3] = {(float)rhd[0], (float)rhd[1], (float)rhd[2]};
+  const float oi[3] = {(float)oid[0], (float)oid[1], (float)oid[2]};
   const float eps = pv.eps_w;
-  const float h = 1.0f - rl / sigma;
   const float dsig_a = sigma * pv.chi_w * a / D;
   const float phi_r = -2.0f * eps * h / sigma;
   const float phi_a = 2.0f * eps * h * rl / (sigma * sigma) * dsig_a;
@@ -370,7 +389,10 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
   const float4 a0 = pv.kin[3 * i], a1 = pv.kin[3 * i + 1], a2 = pv.kin[3 * i + 2];
   const int Xi[3] = {(int)a0.w, (int)a1.w, (int)a2.w};
   const float fi[3] = {a0.x, a0.y, a0.z};
-  const float oi[3] = {(float)pv.o[3 * i], (float)pv.o[3 * i + 1], (float)pv.o[3 * i + 2]};
+  // FP64 state of the step's start (the solve rewrites it only after the join)
+  const double Xd[3] = {pv.X[3 * i], pv.X[3 * i + 1], pv.X[3 * i + 2]};
+  const double oid[3] = {pv.o[3 * i], pv.o[3 * i + 1], pv.o[3 * i + 2]};
+  const double fd[3] = {Xd[0] - (double)Xi[0], Xd[1] - (double)Xi[1], Xd[2] - (double)Xi[2]};  // exact
   const int dims[3] = {lv.nx, lv.ny, lv.nz};
   float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
   if (threadIdx.x < 27) {
@@ -385,6 +407,8 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
       const int bz = wrapi(bc[2] + off[2][iz], cl.nb[2]);
       const int b = bx + cl.nb[0] * (by + cl.nb[1] * bz);
       const float rc2 = pv.r_cut * pv.r_cut;
+      const float smax = 2.0f * fmaxf(pv.sig_par, pv.sig_perp);
+      const float smax2 = smax * smax * 1.0001f;
       const int e = cl.start[b + 1];
       for (int k = cl.start[b]; k < e; ++k) {
         const int j = cl.ids[k];
@@ -394,9 +418,14 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
         const float fj[3] = {b0.x, b0.y, b0.z};
         float r[3];
         for (int m = 0; m < 3; ++m) r[m] = (float)imin_image(Xj[m] - Xi[m], dims[m], lv.per[m]) + (fj[m] - fi[m]);
-        if (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] >= rc2) continue;
-        const float oj[3] = {(float)pv.o[3 * j], (float)pv.o[3 * j + 1], (float)pv.o[3 * j + 2]};
-        bp_pair(r, oi, oj, pv, F, T);
+        const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        // no contact distance exceeds 2 max(sigma_perp, sigma_par): a pair
+        // farther than that in FP32, with margin, needs no FP64 geometry
+        if (r2 >= rc2 || r2 > smax2) continue;
+        double rd[3];
+        for (int m = 0; m < 3; ++m) rd[m] = min_image_exact(__dsub_rn(pv.X[3 * j + m], Xd[m]), dims[m], lv.per[m]);
+        const double ojd[3] = {pv.o[3 * j], pv.o[3 * j + 1], pv.o[3 * j + 2]};
+        bp_pair(rd, oid, ojd, pv, F, T);
       }
     }
   }
@@ -405,8 +434,9 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
     const int side = 2 * R + 1;
     const float rw2 = pv.sigw_max * pv.sigw_max;
     for (int t = threadIdx.x; t < side * side; t += CB) {
-      int y = Xi[1] - R + t % side, z = Xi[2] - R + t / side;
-      const float ry = (float)(y - Xi[1]) - fi[1], rz = (float)(z - Xi[2]) - fi[2];
+      const int oy = t % side - R, oz = t / side - R;  // node offsets from rint(X)
+      int y = Xi[1] + oy, z = Xi[2] + oz;
+      const float ry = (float)oy - fi[1], rz = (float)oz - fi[2];
       if (ry * ry + rz * rz >= rw2) continue;
       if (lv.per[1]) y = wrapi(y, lv.ny);
       else if (y < 0 || y >= lv.ny) continue;
@@ -418,8 +448,8 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
         if (lv.per[0]) x = wrapi(x, lv.nx);
         else if (x < 0 || x >= lv.nx) continue;
         if (!((row[x >> 5] >> (x & 31)) & 1u)) continue;
-        const float r[3] = {(float)dx - fi[0], ry, rz};
-        bp_wall(r, oi, pv, F, T);
+        const double rd[3] = {(double)dx - fd[0], (double)oy - fd[1], (double)oz - fd[2]};
+        bp_wall(rd, oid, pv, F, T);
       }
     }
   }

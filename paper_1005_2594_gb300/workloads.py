@@ -374,3 +374,86 @@ def tube(nx=512, ny=256, nz=256, radius=120.0, hct=0.35, g=1e-6, seed=1005, R=(7
 
     X, q = fcc_cells(p, n_cells, seed, inside)
     return p, X, q, tube_mask(p, radius, axis=0)
+
+
+def _axis_quaternion(ax):
+    """quaternion (w, x, y, z) turning e_z into the unit vector ax"""
+    ax = np.asarray(ax, dtype=np.float64)
+    ax = ax / np.linalg.norm(ax)
+    v = np.array([-ax[1], ax[0], 0.0])
+    s = np.linalg.norm(v)
+    ang = math.atan2(s, ax[2])
+    v = v / s if s > 1e-300 else np.array([1.0, 0.0, 0.0])
+    return np.array([math.cos(ang / 2), *(math.sin(ang / 2) * v)])
+
+
+def sediment_stacks(mu=0.0, seed=1011):
+    """Contacts that last: the small shear cell (32^3, walls z moving -/+0.01
+    along x, cells R = (3.5, 1.5)) with the paper's potential range and
+    strength (sigma = 12/11 R, eps = eps_w = 0.05), cells 1.5 times denser than
+    the plasma under a body force g = -5e-5 along z on plasma and cells.
+    Stacks of nearly face-on cells rest on the lower wall (within the wall
+    sphere of Eq. sigmaw, each on the one below within its pair range), two
+    side-on cells lie on the wall, and a pair and a single cell float higher
+    up, the pair within its range.  Returns params, X, q."""
+    R = (3.5, 1.5)
+    sig = (R[0] * 12.0 / 11.0, R[1] * 12.0 / 11.0)
+    p = base_params(32, 32, 32, periodic=(1, 1, 0), R=R, sigma=sig, eps=0.05, mu=mu,
+                    g=(0.0, 0.0, -5e-5), body_force_on_cells=1,
+                    wall_vel={4: (-0.01, 0.0, 0.0), 5: (0.01, 0.0, 0.0)})
+    p["rho_p"] = 1.5
+    rng = np.random.default_rng(seed)
+
+    def tilted(t, a):
+        return np.array([math.cos(t / 2), math.sin(t / 2) * math.cos(a), math.sin(t / 2) * math.sin(a), 0.0])
+
+    X, q = [], []
+    face = math.sqrt(sig[1] ** 2 + 0.25)  # face-on reach of the wall sphere from the wall node layer z = 0
+    for (x, y, h) in ((6.0, 6.0, 2), (20.0, 8.0, 3), (9.0, 22.0, 2), (24.0, 24.0, 1)):
+        z = face - 0.12
+        for _ in range(h):
+            X.append([x + rng.uniform(-0.5, 0.5), y + rng.uniform(-0.5, 0.5), z])
+            q.append(tilted(rng.uniform(0.0, 0.15), rng.uniform(0.0, 2 * math.pi)))
+            z += 2 * sig[1] - 0.10
+    side = math.sqrt(sig[0] ** 2 + 0.25)
+    for (x, y) in ((15.0, 16.0), (28.0, 14.0)):
+        X.append([x, y, side - 0.10])
+        a = rng.uniform(0.0, 2 * math.pi)
+        q.append(np.array([math.cos(math.pi / 4), math.sin(math.pi / 4) * math.cos(a),
+                           math.sin(math.pi / 4) * math.sin(a), 0.0]))
+    for (x, y, z) in ((16.0, 4.0, 18.0), (16.0 + 2 * sig[0] - 0.2, 4.3, 18.2), (5.0, 14.0, 22.0)):
+        X.append([x, y, z])
+        q.append(tilted(rng.uniform(0.0, 0.5), rng.uniform(0.0, 2 * math.pi)))
+    q = np.array(q)
+    return p, np.array(X), q / np.linalg.norm(q, axis=1)[:, None]
+
+
+def tube_contacts(mu=0.0, seed=1013, radius=11.0):
+    """Cells resting on the wall of a tube given as a wall mask: 40 x 28 x 28
+    periodic box, tube of the given radius along x, body force (2e-5, 0, -5e-5)
+    on plasma and cells, cells 1.5 times denser than the plasma, sigma =
+    12/11 R, eps = eps_w = 0.05.  Four cells lie nearly face-on on the lower
+    part of the tube wall (within the wall sphere of its surface nodes), two
+    of them with a second cell resting on top.  Returns params, X, q, mask."""
+    R = (3.5, 1.5)
+    sig = (R[0] * 12.0 / 11.0, R[1] * 12.0 / 11.0)
+    nx, ny, nz = 40, 28, 28
+    p = base_params(nx, ny, nz, periodic=(1, 1, 1), R=R, sigma=sig, eps=0.05, mu=mu,
+                    g=(2e-5, 0.0, -5e-5), body_force_on_cells=1)
+    p["rho_p"] = 1.5
+    mask = tube_mask(p, radius, axis=0)
+    rng = np.random.default_rng(seed)
+    cy, cz = (ny - 1) / 2.0, (nz - 1) / 2.0
+    face = math.sqrt(sig[1] ** 2 + 0.25)
+    X, q = [], []
+    for k, x in enumerate((5.0, 14.0, 23.0, 32.0)):
+        th = rng.uniform(-0.4, 0.4)
+        d = radius + 0.5 - face + 0.05
+        nvec = np.array([0.0, math.sin(th), -math.cos(th)])  # outward wall normal at the cell
+        X.append([x, cy + d * nvec[1], cz + d * nvec[2]])
+        qa = _axis_quaternion(nvec + rng.uniform(-0.1, 0.1, 3))
+        q.append(qa)
+        if k % 2 == 0:
+            X.append([x + 0.3, X[-1][1] - (2 * sig[1] - 0.1) * nvec[1], X[-1][2] - (2 * sig[1] - 0.1) * nvec[2]])
+            q.append(qa)
+    return p, np.array(X), np.array(q), mask

@@ -7,9 +7,9 @@ Bars (written here, from the method's arithmetic):
   operation order on both sides; the FP32 filter only skips nodes farther
   than 1e-3 in s from the surface, far above its error);
 * fields and forces in FP32 storage: max |gpu - oracle| / max |oracle| below
-  1e-5 for rho, u, F, T and the cell state after 100 steps; the density
-  deviation rho - rho_bar, a small difference of O(1) numbers carried in
-  FP32 storage, to 1e-3 of its own range;
+  1e-5 for rho, u, F, T and the cell state after 100 steps, and for the
+  density deviation rho - rho_bar on its own range (the populations are
+  stored shifted by alpha_r rho_bar, so the deviation is carried directly);
 * BF16 / FP16 storage: the measured error is printed and bounded by the
   storage precision (8 and 11 significant bits of the shifted populations).
 """
@@ -75,15 +75,25 @@ def test_lattice_only_parity(shape, periodic, g):
     for k in range(3):
         orc.step(21)
         sim.step(21)  # odd count: both AA parities are exercised
+    sim.wall_momentum()  # the read-out resets the counters: the next read is one step
+    orc.step(1)
+    sim.step(1)
     rho_o, u_o, own = orc.fields()
     rho_g, u_g, _ = sim.fields()
     fl = own == -1
     assert rel(u_g[fl], u_o[fl]) < 1e-5
     assert rel(rho_g[fl], rho_o[fl]) < 1e-5
-    assert rel(rho_g[fl] - 1.0, rho_o[fl] - 1.0) < 1e-3
+    # the density deviation, to 1e-5 of its range; this nearly uniform fluid
+    # deviates by < 1e-4, below which the bar is the FP32 resolution of the
+    # 19 stored shifted populations (|f~| < 3e-3 here: 19 x 3e-3 x 2^-24 per
+    # store, a few stores deep): 1e-8 absolute
+    d_o, d_g = rho_o[fl] - 1.0, rho_g[fl] - 1.0
+    assert np.abs(d_g - d_o).max() < max(1e-5 * np.abs(d_o).max(), 1e-8)
+    walled = [w for w in range(6) if not p["periodic"][w // 2]]
     wm_g, wm_o = sim.wall_momentum(), orc.counters()["wallmom"]
-    # the GPU counter sums all 63 steps; compare the last step by differencing
-    assert np.isfinite(wm_g).all()
+    if walled:
+        assert np.abs(wm_o[walled]).max() > 0
+        assert rel(wm_g[walled], wm_o[walled]) < 1e-5, (wm_g[walled], wm_o[walled])
 
 
 def test_wall_momentum_per_step():
@@ -109,6 +119,16 @@ def _coupled(mu, n_cells=20, seed=1001):
     return p, X, q, V, L
 
 
+def _check_cell_links(sim, orc):
+    """the step's own per-cell link lists equal the oracle's boundary links
+    whose owner is a cell (Eq. deltap's link set), bit for bit"""
+    bo = orc.boundary_links()
+    ref = bo[bo[:, 2] >= 0]
+    got = sim.cell_links()
+    assert len(ref) > 0
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_owner_map_and_lists_bitexact():
     oracle, bl, workloads = _mods()
     for seed in (1001, 1011, 1021):
@@ -119,6 +139,7 @@ def test_owner_map_and_lists_bitexact():
         np.testing.assert_array_equal(sim.owner(), orc.owner())
         np.testing.assert_array_equal(sim.boundary_links(), orc.boundary_links())
         np.testing.assert_array_equal(sim.contact_links(), orc.contact_links())
+        _check_cell_links(sim, orc)
         nb_g, st_g, ids_g = sim.cell_list()
         nb_o, st_o, ids_o = orc.cell_list()
         np.testing.assert_array_equal(nb_g, nb_o)
@@ -185,6 +206,8 @@ def test_random_resets_and_overlap_steps_bitexact():
         orc.step(1)
         sim.step(1)
         np.testing.assert_array_equal(sim.owner(), orc.owner())
+        if s % 5 == 4:
+            _check_cell_links(sim, orc)
     sim.sync()
 
 
@@ -211,9 +234,8 @@ def test_coupled_100_steps(mu):
     for k in ("F", "T", "X", "q", "V", "L"):
         errs[k] = rel(pg[k], po[k])
     print("coupled 32^3, 20 cells, mu=%g, 100 steps: %s" % (mu, {k: "%.2e" % v for k, v in errs.items()}))
-    for k in ("u", "rho", "F", "T", "X", "q", "V", "L"):
+    for k in ("u", "rho", "rho-rho0", "F", "T", "X", "q", "V", "L"):
         assert errs[k] < 1e-5, (k, errs[k])
-    assert errs["rho-rho0"] < 1e-3
 
 
 def test_force_parts_first_step():
@@ -484,3 +506,66 @@ def test_autotune_keeps_a_valid_variant():
     assert choice in (0, 1, 2, 3, 4)
     s.step(4)
     s.sync()
+
+
+def test_ensemble_members_match_oracle():
+    """Each member of an ensemble advanced by the ensemble graph (uneven
+    lattices, their own cells and wall speeds) against its own FP64 oracle
+    over 100 steps: owner maps bit-exact every 25 steps, fields and cell
+    state to 1e-5."""
+    oracle, bl, workloads = _mods()
+    boxes = workloads.ensemble(n_boxes=3, seed=91, R=(3.5, 1.5), sizes=(24, 32), hct=(0.1, 0.2))
+    sims, orcs = [], []
+    for p, X, q, _ in boxes:
+        s, o = bl.Simulation(p), oracle.Oracle(p)
+        s.set_particles(X, q)
+        o.set_particles(X, q)
+        sims.append(s)
+        orcs.append(o)
+    ens = bl.Ensemble(sims)
+    for block in range(4):
+        ens.step(24)
+        ens.step(1)  # pairs of steps as one graph, then a single step
+        for o in orcs:
+            o.step(25)
+        ens.sync()
+        for s, o in zip(sims, orcs):
+            np.testing.assert_array_equal(s.owner(), o.owner())
+    for s, o in zip(sims, orcs):
+        rho_o, u_o, own = o.fields()
+        rho_g, u_g, _ = s.fields()
+        fl = own == -1
+        po, pg = o.particles(), s.particles()
+        assert rel(u_g[fl], u_o[fl]) < 1e-5
+        assert rel(rho_g[fl], rho_o[fl]) < 1e-5
+        for k in ("F", "T", "X", "q", "V", "L"):
+            assert rel(pg[k], po[k]) < 1e-5, k
+    ens.close()
+
+
+def test_split_rows_with_cells_100_steps():
+    """Rows of 136 nodes: the bulk-copy sweep takes them as a 128-node and an
+    8-node segment whose edge nodes read their shifted neighbours from global
+    memory (the path of the 256^3 workloads), here with cells, a body force
+    and tau = 0.8, against the oracle over 100 steps."""
+    oracle, bl, workloads = _mods()
+    p = workloads.base_params(136, 16, 18, periodic=(1, 1, 0), R=(3.5, 1.5), g=(2e-5, 1e-5, 0.0),
+                              wall_vel={4: (-0.01, 0.0, 0.0), 5: (0.01, 0.0, 0.0)})
+    p["tau"] = 0.8
+    X, q, _ = workloads.pack_cells(p, 14, 29)
+    orc, sim = oracle.Oracle(p), bl.Simulation(p)
+    sim.sweep_variant(3)
+    orc.set_particles(X, q)
+    sim.set_particles(X, q)
+    for block in range(4):
+        orc.step(25)
+        sim.step(25)
+        np.testing.assert_array_equal(sim.owner(), orc.owner())
+    rho_o, u_o, own = orc.fields()
+    rho_g, u_g, _ = sim.fields()
+    fl = own == -1
+    po, pg = orc.particles(), sim.particles()
+    assert rel(u_g[fl], u_o[fl]) < 1e-5
+    assert rel(rho_g[fl], rho_o[fl]) < 1e-5
+    for k in ("F", "T", "X", "q", "V", "L"):
+        assert rel(pg[k], po[k]) < 1e-5, k

@@ -278,6 +278,100 @@ def test_cell_list_canonical():
             assert [bx, by, bz] == [min(int(math.floor(f[k])), nb[k] - 1) for k in range(3)]
 
 
+@pytest.mark.parametrize("dims,r_cut", [((32, 32, 32), 7.5), ((37, 30, 45), 7.0), ((50, 31, 24), 10.3),
+                                         ((23, 23, 64), 7.6)])
+def test_cell_list_holds_every_close_pair_in_adjacent_bins(dims, r_cut):
+    """What the cell list is for: every pair of cells closer than r_cut lies in
+    the same or neighbouring bins (periodic wrap), so the 27-bin search of the
+    potentials and of the owner search misses no pair.  Besides random
+    positions, pairs are placed just inside r_cut across a bin boundary along
+    each axis, in both orders: a bin narrower than r_cut (a ceiling in place of
+    the floor of N / r_cut, or an off-by-one bin count) puts such a pair two
+    bins apart.  Brute force over all pairs, minimum image on every axis."""
+    p = workloads.base_params(*dims, periodic=(1, 1, 1), R=(1.0, 1.0), r_cut=r_cut)
+    L = np.array(dims, float)
+    rng = np.random.default_rng(int(10 * r_cut) + dims[0])
+    pts = [rng.uniform(0, 1, 3) * L for _ in range(40)]
+    for k in range(3):
+        nb_guess = max(1, int(L[k] // r_cut))
+        w = L[k] / nb_guess
+        for b in range(nb_guess):
+            for d in (-1.0, 1.0):
+                a = rng.uniform(0, 1, 3) * L
+                a[k] = (b * w + (1e-7 if d < 0 else w - 1e-7)) % L[k]
+                c = a.copy()
+                c[k] = (a[k] + d * (r_cut - 1e-6)) % L[k]
+                pts += [a, c]
+    X = np.array(pts)
+    q = np.tile([1.0, 0.0, 0.0, 0.0], (len(X), 1))
+    o = oracle.Oracle(p)
+    o.set_particles(X, q)
+    nb, start, ids = o.cell_list()
+    bins = np.zeros((len(X), 3), int)
+    for b in range(len(start) - 1):
+        bz, rem = divmod(b, nb[0] * nb[1])
+        by, bx = divmod(rem, nb[0])
+        bins[ids[start[b]:start[b + 1]]] = (bx, by, bz)
+    close = 0
+    for i in range(len(X)):
+        d = X - X[i]
+        d -= L * np.round(d / L)
+        near = np.flatnonzero(np.einsum("ij,ij->i", d, d) < r_cut * r_cut)
+        for j in near:
+            db = np.abs(bins[j] - bins[i])
+            db = np.minimum(db, nb - db)
+            assert (db <= 1).all(), (i, j, bins[i], bins[j], nb)
+            close += 1
+    assert close > len(X)
+
+
+def test_surface_wall_nodes_of_a_tube_brute_force():
+    """Reading Q13 (Sec. III): the wall potential acts from the surface wall
+    nodes only, the wall nodes linked to a non-wall node by some c_r.  A
+    side-on cell lies against the staircase wall of a tube given as a mask,
+    close enough that wall nodes one layer behind the surface are within its
+    wall-sphere range; the oracle's wall force and torque of the first step
+    must equal the sum of Eq. (sigmaw) over the surface nodes found here by
+    brute force (all 18 neighbours of every mask node), and differ from the
+    sum over all wall nodes in range."""
+    R = (3.5, 1.5)
+    p = workloads.base_params(24, 26, 26, periodic=(1, 1, 1), R=R, sigma=(3.8, 1.65), eps=0.05)
+    mask = workloads.tube_mask(p, 10.0, axis=0).reshape(26, 26, 24)
+    wall = mask > 0
+    surf = np.zeros_like(wall)
+    for c in C_IFACE[1:]:
+        nbw = np.roll(wall, shift=(-c[2], -c[1], -c[0]), axis=(0, 1, 2))
+        surf |= wall & ~nbw
+    # a cell with its axis along the tube, its rim against the lower wall
+    q = np.array([[math.cos(math.pi / 4), 0.0, math.sin(math.pi / 4), 0.0]])  # axis along x
+    o_ax = oracle.axis(q[0])
+    X = np.array([[11.7, 12.6, 4.6]])
+    o = oracle.Oracle(p)
+    o.set_walls(mask.reshape(-1))
+    o.set_particles(X, q)
+    o.step(1)
+    Fw, Tw = o.wall_parts()
+    L = np.array([24, 26, 26], float)
+
+    def total(sel):
+        F, T = np.zeros(3), np.zeros(3)
+        for z, y, x in zip(*np.nonzero(sel)):
+            d = np.array([x, y, z], float) - X[0]
+            d -= L * np.round(d / L)
+            phi, Fi, Ti = oracle.wall(p, d, o_ax)
+            F += Fi
+            T += Ti
+        return F, T
+
+    Fs, Ts = total(surf)
+    Fa, Ta = total(wall)
+    assert np.abs(Fs).max() > 0
+    np.testing.assert_allclose(Fw[0], Fs, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(Tw[0], Ts, rtol=1e-12, atol=1e-15)
+    # wall nodes behind the surface are in range: the selection matters
+    assert np.abs(Fa - Fs).max() > 1e-3 * np.abs(Fs).max()
+
+
 def test_link_lists_brute_force():
     p, X, q = workloads.small_shear()
     o = oracle.Oracle(p)

@@ -70,3 +70,7 @@ def test_static_cell_list_rejects_oversize_requests():
     assert rc == bl.BL_EINVAL
     rc, _ = bl.bl_cell_list_build_static(Xd, 1, (4096, 4096, 64), 1.0, out, out)
     assert rc == bl.BL_EINVAL
+    # a tiny r_cut: bin counts far beyond INT_MAX are rejected, not converted
+    rc, nb = bl.bl_cell_list_build_static(Xd, 1, (64, 64, 64), 1e-12, out, out)
+    assert rc == bl.BL_EINVAL
+    assert (nb == 0).all()  # a rejected request leaves nb untouched

@@ -84,56 +84,119 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+    """SM clocks, their maximum, power and the clock-event (throttle) reasons
+    of the benchmarked GPU, polled every ~1 ms through NVML (the driver's
+    management library, loaded with ctypes) while the timed region runs;
+    nvidia-smi at its shortest interval where NVML cannot be loaded.  The GPU
+    is found by its PCI bus id, so the sample is of the device the bench runs
+    on even when NVML numbers the machine's GPUs differently."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
+    def __init__(self, cuda_index):
+        self.cuda_index = cuda_index
+        self.samples = []  # (sm_mhz, sm_max_mhz, power_w, reasons)
+        self.stop_ev = threading.Event()
+        self.thread = None
         self.proc = None
-        self.lines = []
+        self.source = None
+
+    def _bus_id(self):
+        try:
+            import torch
+
+            pr = torch.cuda.get_device_properties(self.cuda_index)
+            return "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        except Exception:
+            return None
+
+    def _nvml(self):
+        import ctypes
+
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        bus = self._bus_id()
+        ok = bus is not None and lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) == 0
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(self.cuda_index, ctypes.byref(h)) != 0:
+            return None
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, reasons_fn
+
+    def _poll_nvml(self, lib, h, reasons_fn):
+        import ctypes
+
+        mhz, mx, mw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))  # 1 = NVML_CLOCK_SM
+        while not self.stop_ev.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0:
+                pw = mw.value / 1000.0 if lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(mw)) == 0 else None
+                rr = rs.value if reasons_fn(h, ctypes.byref(rs)) == 0 else 0
+                self.samples.append((float(mhz.value), float(mx.value), pw,
+                                     [n for bit, n in self.REASONS.items() if rr & bit]))
+            time.sleep(0.001)
 
     def start(self):
         try:
+            nv = self._nvml()
+        except Exception:
+            nv = None
+        if nv is not None:
+            self.source = "nvml, ~1 ms"
+            self.thread = threading.Thread(target=self._poll_nvml, args=nv, daemon=True)
+            self.thread.start()
+            return
+        try:
+            bus = self._bus_id()
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+                ["nvidia-smi", "-i", bus or str(self.cuda_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "10"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi, 10 ms"
+            self.thread = threading.Thread(target=self._read_smi, daemon=True)
+            self.thread.start()
         except Exception:
             self.proc = None
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
-    def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.t.join(timeout=2)
-        sm, smax, reasons = [], [], set()
+    def _read_smi(self):
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                pw = float(parts[2]) if parts[2] not in ("", "[N/A]") else None
+                self.samples.append((float(parts[0]), float(parts[1]), pw,
+                                     [n for n, v in zip(names, parts[3:7]) if v.lower().startswith("active")]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+
+    def stop(self):
+        self.stop_ev.set()
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        if self.source is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no NVML and no nvidia-smi"], "samples": 0}
+        sm = [x[0] for x in self.samples]
+        pw = [x[2] for x in self.samples if x[2] is not None]
+        reasons = sorted({r for x in self.samples for r in x[3]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(x[1] for x in self.samples) if sm else None,
+                "power_w_max": round(max(pw), 1) if pw else None,
+                "reasons": reasons, "samples": len(sm), "source": self.source}
 
 
 def make_workload(name):
@@ -163,17 +226,22 @@ def make_workload(name):
 
 
 # DRAM traffic of one lattice sweep (dram__bytes_read.sum + dram__bytes_write.sum,
-# mean of the even and odd launch) from the ncu capture summarised in
-# profiles/lattice_sweep_shear128_dram.md, valid for the sweep source it was
-# taken on (lb_sweep.cuh, first 16 hex digits of its SHA-256) and that workload only
+# mean of the even and odd launch) from the ncu capture of the shear-cell
+# workload at FP32 storage kept with the profiles, valid for the sweep source
+# it was taken on (lb_sweep.cuh, first 16 hex digits of its SHA-256) and that
+# workload only
 SWEEP_TRAFFIC = {"sha": "ad506e7e2729c60d", "config": "shear128", "store": 0, "bytes": 271938944}
 
 
-# the sweep kernel each storage type runs by default (FP32: variant 3 of the
-# library's sweep variants)
-SWEEP_KERNEL = {0: "k_lb_step_bulk (fused collide/stream/bounce-back, bulk-copy pipeline over 8 planes)",
-                1: "k_lb_step (fused collide/stream/bounce-back, one node per thread, BF16 store)",
-                2: "k_lb_step (fused collide/stream/bounce-back, one node per thread, FP16 store)"}
+def sweep_kernel(nx, store):
+    """the sweep kernel the library runs by default for this row length and
+    storage type (the bulk-copy pipeline needs 16-byte aligned rows)"""
+    name = {0: "FP32", 1: "BF16", 2: "FP16"}[store]
+    if nx % (4 if store == 0 else 8) == 0:
+        return "k_lb_step_bulk (fused collide/stream/bounce-back, bulk-copy pipeline over 8 planes, %s store)" % name
+    if store == 0:
+        return "k_lb_step_pipe (fused collide/stream/bounce-back, per-thread copy pipeline, FP32 store)"
+    return "k_lb_step (fused collide/stream/bounce-back, one node per thread, %s store)" % name
 
 
 def sweep_traffic(config, store):
@@ -270,8 +338,13 @@ def run_gpu(args, ws, rank, local):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
                      "traffic": sweep_traffic(args.config, args.store), "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
-                     else "fallback 6.8 TB/s", "kernel": SWEEP_KERNEL[args.store],
-                     "bytes_per_launch": bytes_per, "launch_ms": round(k1_ms / max(k1_n, 1), 5)},
+                     else "fallback 6.8 TB/s", "kernel": sweep_kernel(p["nx"], args.store),
+                     "bytes_per_launch": bytes_per, "launch_ms": round(k1_ms / max(k1_n, 1), 5),
+                     # the coupled step as a whole: the same algorithmic bytes (the
+                     # link, contact, potential and fill/drain work adds none when
+                     # fused) over the graph-replayed step time
+                     "step_achieved": round(bytes_per / (ms_max / args.steps * 1e-3) / 1e9, 1),
+                     "step_frac": round(bytes_per / (ms_max / args.steps * 1e-3) / 1e9 / hbm, 4)},
         "kernel_time_share": group_share,
         "instrumented": {"steps": k_inst, "ms_per_step": round(ms_inst / k_inst, 5),
                          "note": "per-kernel CUDA events, no graph replay; roofline and shares from this run"},
@@ -585,6 +658,68 @@ def cpu_oracle_step_time(p, X, q, nsteps=1):
     return (time.perf_counter() - t0) / nsteps
 
 
+def _oracle_worker(p, X, q, mask, warmup, steps, barrier, out):
+    """one process of the all-core oracle timing: its own copy of the sample,
+    stepped after every process has set up"""
+    import oracle
+
+    o = oracle.Oracle(p)
+    if mask is not None:
+        o.set_walls(mask)
+    o.set_particles(X, q)
+    o.step(warmup)
+    barrier.wait()
+    t0 = time.perf_counter()
+    o.step(steps)
+    out.put(time.perf_counter() - t0)
+
+
+def host_cores(sites):
+    """processes for the all-core oracle timing: one per core, as many as
+    60 % of the available host memory holds (the oracle keeps about 0.5 KB
+    per lattice site)"""
+    n = os.cpu_count() or 1
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                n = min(n, max(1, int(int(ln.split()[1]) * 1024 * 0.6 // (sites * 500))))
+    except OSError:
+        pass
+    return n
+
+
+def cpu_model():
+    try:
+        for ln in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_all_cores(p, X, q, mask, warmup, steps, procs=None):
+    """The FP64 oracle, as it stands (single-threaded C), run as one process
+    per host core, each stepping its own copy of the sample; the processes
+    start stepping together (a barrier after set-up).  Returns the aggregate
+    MLUPS (every process's site updates over the slowest process's time),
+    the process count and the slowest time.  Processes are spawned, never
+    forked, since this process has used the GPU."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    Ns = p["nx"] * p["ny"] * p["nz"]
+    n = procs or host_cores(Ns)
+    barrier, out = ctx.Barrier(n), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(p, X, q, mask, warmup, steps, barrier, out)) for _ in range(n)]
+    for pr in ps:
+        pr.start()
+    times = [out.get() for _ in ps]
+    for pr in ps:
+        pr.join()
+    return n * Ns * steps / max(times) / 1e6, n, max(times)
+
+
 def reference_sample(p, X, q, budget_s, nsteps):
     """largest lateral sub-box of the workload (same height, walls, wall speed,
     cell shape and volume fraction) whose oracle steps fit the time budget"""
@@ -613,8 +748,6 @@ def run_reference(args, ws, rank):
     """FP64 CPU oracle on the host cores, bounded sample of the same workload."""
     if rank != 0:
         return None
-    import oracle
-
     p, X, q, _mask, desc = make_workload(args.config)
     steps, warmup = args.steps, args.warmup
     if args.config == "tube_rheology":
@@ -634,22 +767,15 @@ def run_reference(args, ws, rank):
     else:
         sp, sX, sq, sample = reference_sample(p, X, q, 150.0, steps + warmup)
         smask = None
-    o = oracle.Oracle(sp)
-    if smask is not None:
-        o.set_walls(smask)
-    o.set_particles(sX, sq)
-    o.step(warmup)
-    t0 = time.perf_counter()
-    o.step(steps)
-    dt = time.perf_counter() - t0
-    Ns = sp["nx"] * sp["ny"] * sp["nz"]
-    v = Ns * steps / dt / 1e6
+    v, n, dt = oracle_all_cores(sp, sX, sq, smask, warmup, steps)
+    sample = "%s, one copy per process in %d processes (one per host core) stepping together" % (sample, n)
     return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": ws,
             "steps": steps, "warmup": warmup, "ms_per_step": round(dt / steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded random packing, resting start)",
             "config": {"workload": desc, "sample": sample},
-            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
             "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -682,10 +808,14 @@ def main():
     out, (p, X, q, desc) = run_gpu(args, ws, rank, local)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
-            t = cpu_oracle_step_time(p, X, q, 1)
             N = p["nx"] * p["ny"] * p["nz"]
-            out["cpu_baseline"] = {"value": round(N / t / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                   "sample": "1 coupled step of the same workload (FP64 C oracle, 1 thread)"}
+            v, n, t = oracle_all_cores(p, X, q, None, 0, 1)
+            t1 = cpu_oracle_step_time(p, X, q, 1)
+            out["cpu_baseline"] = {
+                "value": round(v, 4), "unit": UNIT, "cores": n, "kind": "oracle",
+                "sample": "1 coupled step of the same workload in each of %d processes (the single-threaded FP64 C "
+                          "oracle, one process per host core, stepping together), %.1f s" % (n, t),
+                "cpu": cpu_model(), "single_core": {"value": round(N / t1 / 1e6, 4), "cores": 1}}
         print(json.dumps(out), flush=True)
 
 

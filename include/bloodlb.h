@@ -173,13 +173,15 @@ int bl_populations_set(bl_ctx *c, const double *pop);
 int bl_boundary_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count);
 int bl_contact_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count);
 
-/* The per-cell bounce-link lists that the step sums the link momentum of
-   Eq. (deltap) over and gives the moving-boundary term of Eq. (c) to, built
-   by the step's own kernel from the current owner map: (fluid node y,
-   direction r with y + c_r inside cell p, p) as int32 triples in (node, r)
-   order, i.e. the boundary links of bl_boundary_links_get whose owner is a
-   cell.  Writes min(count, cap) triples to the host array out and the full
-   count to *count; BL_EOVERFLOW if a list outgrew its capacity. */
+/* The bounce links of the last step's lattice sweep, as the step sums the
+   link momentum of Eq. (deltap) over them and gives them the moving-boundary
+   term of Eq. (c): the sweep writes, for every fluid node next to a cell, one
+   record per cell into that cell's list.  Read out as (fluid node y,
+   direction r with y + c_r inside cell p, p) int32 triples in (node, r)
+   order: the boundary links whose owner is a cell, of the owner map the
+   last step started from.  Empty before the first step after cells are set.
+   Writes min(count, cap) triples to the host array out and the full count to
+   *count; BL_EOVERFLOW if a list outgrew its capacity. */
 int bl_cell_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *count);
 
 /* Cell list of the current positions in canonical (bin, id) order:

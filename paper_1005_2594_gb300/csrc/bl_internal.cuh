@@ -75,9 +75,29 @@ struct LatticeView {
   int sweep;  // sweep variant (0 one node per thread, 1 / 2 FP32 pipeline over 4 / 8 planes)
   void *pop;       // 19 x N storage elements, slot r of node n at r * N + n
   int32_t *owner;  // N
-  float *rho_b;    // N: density of each fluid node with a cell link, written by the sweep
   uint32_t *nbm;   // N neighbour words of the current owner map (NB_* bits), written by the geometry pass
+  uint32_t *nbc;   // N neighbour-cell words (NBC_*), written with the neighbour words
+  // Cell links of the sweep.  A fluid node next to a cell writes one link
+  // record per cell into that cell's bucket, for the link-momentum sums.
+  // The moving-boundary term C of its bounced populations needs the cell's
+  // velocity of the half step, solved after the sweep: after the solve, the
+  // node's record of its first cell becomes pu[n] = (rho (V + W x d), mask of
+  // the bounced directions as the bits of .w), which the next sweep reads
+  // with the populations and adds as C = -(m_r / 6) c_r . u; the links to a
+  // second or third cell of one node get C in place right after the solve.
+  float4 *pu;              // N
+  float4 *rec;             // ncells x rec_cap records of 2 float4
+  int *rec_count;          // ncells
+  int rec_cap;
+  int *status;
 };
+
+// A link record: node n (bits of .x), direction mask (bits of .y: bit r =
+// the neighbour n + c_r belongs to the cell; bit 31 marks the links of a
+// node's second or third cell, whose C is given in place right after the
+// solve), density rho (.z) and sum over the mask of 2 f~*_r c_r (.w, then
+// .x, .y of the second float4).
+constexpr uint32_t REC_DIRECT = 1u << 31;
 
 // neighbour word of a node: bit 0 the node is fluid; bit r (1..18) the
 // neighbour x + c_r is solid; NB_WALL some solid neighbour is a wall node;
@@ -86,6 +106,12 @@ constexpr uint32_t NB_FLUID = 1u;
 constexpr uint32_t NB_SOLID = 0x7FFFEu;
 constexpr uint32_t NB_WALL = 1u << 19;
 constexpr uint32_t NB_CELL = 1u << 20;
+// neighbour-cell word of a fluid node next to a cell: the index of the cell
+// owning its first solid neighbour in direction order (low bits), and
+// NBC_MIXED when not every solid neighbour belongs to that cell (a wall or a
+// second cell among them: the sweep then reads the neighbours' owners)
+constexpr uint32_t NBC_MIXED = 1u << 31;
+constexpr uint32_t NBC_CELL = 0x7FFFFFFFu;
 
 // momentum given to each wall id by its bounce-back links: variable part in
 // FP64, constant part 2 alpha_r rho_bar c_r as exact integer sums of m_r c_r
@@ -94,10 +120,8 @@ struct WallAcc {
   long long *K;  // 8 x 3
 };
 
-// Cells.  Per-cell link list: the bounce links (fluid node y, direction r
-// from y into the cell) as packed coordinates, grouped by direction within
-// each warp's run, rebuilt by the geometry pass after every
-// re-discretisation; contact links enter as exact integer sums cK, cIT.
+// Cells.  Their bounce links come from the sweep's link records
+// (LatticeView::rec); contact links enter as exact integer sums cK, cIT.
 struct PartView {
   int n;
   double *X, *q, *V, *L, *Om;
@@ -106,9 +130,7 @@ struct PartView {
   float4 *kin;       // kinematics of the current step, 3 float4 per cell:
                      //   (f.x, f.y, f.z, Xi.x), (V, Xi.y), (W, Xi.z); X = Xi + f, Xi = rint(X)
   float4 *kin_next;  // kinematics written for the next step
-  unsigned long long *lk;  // n x lk_cap bounce links (pack_xyzr of the fluid node, r)
-  int *lk_count;     // n
-  int lk_cap;
+  int *rec_last;     // n: records of the last sweep (for the link read-out)
   int *cK, *cIT;     // n x 3 each: contact links, sum m_r c_r and sum m_r dI x c_r
   unsigned long long *touched;  // n x touched_cap nodes claimed or left in one re-discretisation (pack_xyzr)
   double *lsum;      // n x 27 link sums of one step: F, T (variable part), Zff 6, Zft 9, Ztt 6
@@ -176,10 +198,11 @@ void launch_links(const LatticeView &lv, int contact, int pass, int *block_count
 void launch_cell_list(const LatticeView &lv, const PartView &pv, const CellListView &cl, cudaStream_t st, int64_t *nl);
 void launch_forces(const LatticeView &lv, const PartView &pv, const CellListView &cl, const SurfBits &sb,
                    cudaStream_t st, int64_t *nl);
-// link sums and the implicit solve + leap-frog; then the link correction
-// (independent of the claims, which need only the solve)
+// link sums from the sweep's records and the implicit solve + leap-frog;
+// then the pending C of the records (independent of the claims, which need
+// only the solve)
 void launch_sums_solve(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st, int64_t *nl);
-void launch_link_correct(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st,
+void launch_link_pending(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st,
                          int64_t *nl);
 void launch_set_state(const LatticeView &lv, const PartView &pv, int mode, cudaStream_t st, int64_t *nl);
 void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const ChangeList &chg, int mode,
@@ -187,11 +210,14 @@ void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const 
 void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);
 // the geometry after a step's resolve, in two independent parts (together
 // the same result as launch_geometry): neighbour words around the changed
-// nodes (after resolve); link lists and contact sums cell by cell from the
-// current owner map and kinematics (at the start of the next step)
+// nodes (after resolve); contact sums cell by cell from the current owner
+// map and kinematics (at the start of the next step)
 void launch_nbm_update(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
                        int64_t *nl);
-void launch_cell_links(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);
+void launch_contacts(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);
+// the pending C of the last step into the stored populations (layout par),
+// before read-outs and state changes between steps
+void launch_flush_pending(int dtype, const LatticeView &lv, int par, cudaStream_t st, int64_t *nl);
 void launch_resolve_fill(int dtype, const LatticeView &lv, const PartView &pv, const CellListView &cl, int *claim,
                          const ChangeList &chg, int par_next, int impulses, cudaStream_t st, int64_t *nl);
 void launch_clear_cells(int dtype, const LatticeView &lv, int par, cudaStream_t st, int64_t *nl);

@@ -192,6 +192,16 @@ static int build_surface_bits(bl_ctx *c) {
   return BL_OK;
 }
 
+// The steps leave the moving-boundary term C of their last bounces off cells
+// pending (the next sweep adds it as it reads the populations): before the
+// populations are read out or the cells are set anew, it is given to the
+// stored populations here.
+static int flush_pending(bl_ctx *c) {
+  if (c->np == 0) return BL_OK;  // nothing pends without cells (a removal flushes first)
+  launch_flush_pending(c->dtype, c->lv, c->parity, c->stream, &c->launches);
+  return check_launch(c, "pending moving-boundary terms");
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 
@@ -262,9 +272,11 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
     launch_fill_int(c->claim, lv.N, INT_MAX, c->stream);
     c->launches += 2;
     if ((rc = check_launch(c, "init")) != BL_OK) break;
-    if (cudaMalloc(&lv.rho_b, sizeof(float) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "density buffer"); break; }
-    cudaMemsetAsync(lv.rho_b, 0, sizeof(float) * N, c->stream);
     if (cudaMalloc(&lv.nbm, sizeof(uint32_t) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "neighbour words"); break; }
+    if (cudaMalloc(&lv.nbc, sizeof(uint32_t) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "neighbour-cell words"); break; }
+    if (cudaMalloc(&lv.pu, sizeof(float4) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "pending velocities"); break; }
+    cudaMemsetAsync(lv.pu, 0, sizeof(float4) * N, c->stream);
+    lv.status = c->status;
     launch_geometry(lv, c->pv, c->stream, &c->launches);
     if ((rc = check_launch(c, "geometry")) != BL_OK) break;
     if ((rc = build_surface_bits(c)) != BL_OK) break;
@@ -299,12 +311,15 @@ extern "C" int bl_walls_set(bl_ctx *c, const uint8_t *mask) {
 
 static void free_particles(bl_ctx *c) {
   PartView &pv = c->pv;
-  void *ptrs[] = {pv.X, pv.q, pv.V, pv.L, pv.Om, pv.o, pv.oprev, pv.kin, pv.kin_next, pv.lk, pv.lk_count, pv.cK, pv.cIT,
+  void *ptrs[] = {pv.X, pv.q, pv.V, pv.L, pv.Om, pv.o, pv.oprev, pv.kin, pv.kin_next, pv.rec_last, pv.cK, pv.cIT,
                   pv.touched, pv.touched_count, pv.lsum, pv.lsum_i, pv.vw, pv.Fpot, pv.Tpot, pv.PF, pv.PT, pv.Flink, pv.Tlink, pv.Ftot,
                   pv.Ttot, pv.box, pv.stage, c->cl.bin_of, c->cl.count, c->cl.start, c->cl.cursor, c->cl.ids,
-                  c->chg.count, c->chg.items};
+                  c->chg.count, c->chg.items, c->lv.rec, c->lv.rec_count};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  c->lv.rec = nullptr;
+  c->lv.rec_count = nullptr;
+  c->lv.rec_cap = 0;
   {
     void *pp[] = {c->pb.pairs, c->pb.feat, c->pb.out, c->pb.count};
     for (void *p : pp)
@@ -347,18 +362,22 @@ static int alloc_particles(bl_ctx *c, int n) {
   CU(cudaMalloc(&pv.cIT, sizeof(int) * 3 * (size_t)n));
   CU(cudaMemsetAsync(pv.cK, 0, sizeof(int) * 3 * (size_t)n, c->stream));
   CU(cudaMemsetAsync(pv.cIT, 0, sizeof(int) * 3 * (size_t)n, c->stream));
-  // per-cell lists: bounce links (at most ~6 per node of a shell of radius
-  // max(R) + 1) and nodes touched by one re-discretisation (at most the box)
+  // per-cell lists: link records of the sweep (one per fluid node next to
+  // the cell: at most the nodes within one node of its surface, fewer than
+  // twice the area of a sphere of radius max(R) + 1) and nodes touched by
+  // one re-discretisation (at most the box)
   const double rmax = fmax(c->pp.R_par, c->pp.R_perp);
-  const double lk_cap = 6.0 * 4.0 * M_PI * (rmax + 1.0) * (rmax + 1.0) + 64.0;
+  const double rec_cap = 2.0 * 4.0 * M_PI * (rmax + 1.0) * (rmax + 1.0) + 64.0;
   const double box = 2.0 * rmax + 4.0;
   const double t_cap = box * box * box;
-  if (lk_cap * n > 2.0e9 || t_cap * n > 2.0e9 || n > 65535) return fail(c, BL_EINVAL, "cell lists too large");
-  pv.lk_cap = (int)lk_cap;
+  if (rec_cap * n > 2.0e9 || t_cap * n > 2.0e9 || n > 65535) return fail(c, BL_EINVAL, "cell lists too large");
+  c->lv.rec_cap = (int)rec_cap;
   pv.touched_cap = (int)t_cap;
-  CU(cudaMalloc(&pv.lk, sizeof(unsigned long long) * (size_t)pv.lk_cap * n));
-  CU(cudaMalloc(&pv.lk_count, sizeof(int) * (size_t)n));
-  CU(cudaMemsetAsync(pv.lk_count, 0, sizeof(int) * (size_t)n, c->stream));
+  CU(cudaMalloc(&c->lv.rec, sizeof(float4) * 2 * (size_t)c->lv.rec_cap * n));
+  CU(cudaMalloc(&c->lv.rec_count, sizeof(int) * (size_t)n));
+  CU(cudaMemsetAsync(c->lv.rec_count, 0, sizeof(int) * (size_t)n, c->stream));
+  CU(cudaMalloc(&pv.rec_last, sizeof(int) * (size_t)n));
+  CU(cudaMemsetAsync(pv.rec_last, 0, sizeof(int) * (size_t)n, c->stream));
   CU(cudaMalloc(&pv.touched, sizeof(unsigned long long) * (size_t)pv.touched_cap * n));
   CU(cudaMalloc(&pv.touched_count, sizeof(int) * (size_t)n));
   CU(cudaMemsetAsync(pv.touched_count, 0, sizeof(int) * (size_t)n, c->stream));
@@ -462,6 +481,7 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
       if (c->lv.per[k] && !((double)dims[k] >= 2.0 * rmax + 4.0))
         return fail(c, BL_EINVAL, "periodic length %d < 2 max(R) + 4", dims[k]);
   }
+  if (flush_pending(c)) return c->sticky;
   const bool first = n != c->np || c->np == 0;
   // the graphs hold the cell arrays' pointers and the cell constants by
   // value: they stay valid for a re-placement with the same arrays and
@@ -532,7 +552,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     cudaStreamWaitEvent(c->side2, c->ev_fork, 0);
     group_begin(c, 4, &slot, c->side2);
-    launch_cell_links(c->lv, c->pv, c->side2, &c->launches);
+    launch_contacts(c->lv, c->pv, c->side2, &c->launches);
     group_end(c, slot, c->side2);
     cudaEventRecord(c->ev_join3, c->side2);
     group_begin(c, 1, &slot, c->side);
@@ -556,7 +576,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     group_begin(c, 3, &slot, st);
     launch_sums_solve(c->dtype, c->lv, c->pv, c->parity, st, &c->launches);
     group_end(c, slot, st);
-    // the claims need only the solve: beside the link correction
+    // the claims need only the solve: beside the pending C of the records
     cudaEventRecord(c->ev_fork2, st);
     cudaStreamWaitEvent(c->side, c->ev_fork2, 0);
     group_begin(c, 3, &slot, c->side);
@@ -564,7 +584,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     group_end(c, slot, c->side);
     cudaEventRecord(c->ev_join2, c->side);
     group_begin(c, 3, &slot, st);
-    launch_link_correct(c->dtype, c->lv, c->pv, c->parity, st, &c->launches);
+    launch_link_pending(c->dtype, c->lv, c->pv, c->parity, st, &c->launches);
     group_end(c, slot, st);
     cudaStreamWaitEvent(st, c->ev_join2, 0);
     group_begin(c, 4, &slot, st);
@@ -703,6 +723,7 @@ extern "C" int bl_sync(bl_ctx *c) {
 extern "C" int bl_fields_get(bl_ctx *c, double *rho, double *u, int32_t *owner, int on_device) {
   if (!c) return BL_EINVAL;
   if (c->sticky) return c->sticky;
+  if (flush_pending(c)) return c->sticky;
   const size_t N = c->lv.N;
   if (on_device) {
     launch_fields(c->dtype, c->lv, c->parity, rho, u, owner, c->stream);
@@ -767,6 +788,7 @@ extern "C" int bl_wall_momentum_get(bl_ctx *c, double *wallmom) {
 extern "C" int bl_populations_get(bl_ctx *c, double *pop) {
   if (!c || !pop) return BL_EINVAL;
   if (c->sticky) return c->sticky;
+  if (flush_pending(c)) return c->sticky;
   const size_t bytes = sizeof(double) * bl::Q * (size_t)c->lv.N;
   if (ensure_scratch(c, bytes)) return c->sticky;
   launch_pop_io(c->dtype, c->lv, c->parity, c->scratch, 0, c->stream);
@@ -780,6 +802,7 @@ extern "C" int bl_populations_get(bl_ctx *c, double *pop) {
 extern "C" int bl_populations_set(bl_ctx *c, const double *pop) {
   if (!c || !pop) return BL_EINVAL;
   if (c->sticky) return c->sticky;
+  if (flush_pending(c)) return c->sticky;  // (the set overwrites them: nothing may pend after it)
   const size_t bytes = sizeof(double) * bl::Q * (size_t)c->lv.N;
   if (ensure_scratch(c, bytes)) return c->sticky;
   CU(cudaMemcpyAsync(c->scratch, pop, bytes, cudaMemcpyHostToDevice, c->stream));
@@ -837,29 +860,26 @@ extern "C" int bl_cell_links_get(bl_ctx *c, int32_t *out, int64_t cap, int64_t *
   if (c->sticky) return c->sticky;
   *count = 0;
   if (c->np == 0) return BL_OK;
-  // the lists the next step sums over, built by the step's own kernel from
-  // the current owner map and kinematics
-  launch_cell_links(c->lv, c->pv, c->stream, &c->launches);
-  if (check_launch(c, "cell links")) return c->sticky;
-  const int n = c->np, capl = c->pv.lk_cap;
+  // the link records of the last sweep, as the step's link sums read them
+  const int n = c->np, capr = c->lv.rec_cap;
   std::vector<int> cnt(n);
-  std::vector<unsigned long long> lk((size_t)n * capl);
-  CU(cudaMemcpyAsync(cnt.data(), c->pv.lk_count, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaMemcpyAsync(lk.data(), c->pv.lk, sizeof(unsigned long long) * lk.size(), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<float4> rec((size_t)n * capr * 2);
+  CU(cudaMemcpyAsync(cnt.data(), c->pv.rec_last, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(rec.data(), c->lv.rec, sizeof(float4) * rec.size(), cudaMemcpyDeviceToHost, c->stream));
   if (read_status(c)) return c->sticky;
   struct Link {
     long long node;
     int r, p;
   };
   std::vector<Link> links;
-  const long long nx = c->lv.nx, ny = c->lv.ny;
   for (int p = 0; p < n; ++p) {
-    if (cnt[p] > capl) return fail(c, BL_EOVERFLOW, "cell %d: link list overflow", p);
-    for (int i = 0; i < cnt[p]; ++i) {
-      const unsigned long long e = lk[(size_t)p * capl + i];
-      const long long x = (long long)((e >> 5) & 0xFFFFFull), y = (long long)((e >> 25) & 0xFFFFFull),
-                      z = (long long)(e >> 45);
-      links.push_back(Link{x + nx * (y + ny * z), (int)(e & 31ull), p});
+    for (int i = 0; i < cnt[p] && i < capr; ++i) {
+      const float4 r0 = rec[2 * ((size_t)p * capr + i)];
+      uint32_t node, mask;
+      memcpy(&node, &r0.x, 4);
+      memcpy(&mask, &r0.y, 4);
+      for (int r = 1; r < bl::Q; ++r)
+        if (mask & (1u << r)) links.push_back(Link{(long long)node, r, p});
     }
   }
   std::sort(links.begin(), links.end(), [](const Link &a, const Link &b) {
@@ -1184,8 +1204,8 @@ extern "C" void bl_destroy(bl_ctx *c) {
     if (e) cudaEventDestroy(e);
   if (c->side2) cudaStreamDestroy(c->side2);
   free_particles(c);
-  void *ptrs[] = {c->lv.pop, c->lv.owner, c->lv.rho_b, c->lv.nbm, c->claim, c->status, c->wacc.F, c->wacc.K,
-                  c->sbits.bits, c->scratch};
+  void *ptrs[] = {c->lv.pop, c->lv.owner, c->lv.nbm, c->lv.nbc, c->lv.pu, c->claim, c->status,
+                  c->wacc.F, c->wacc.K, c->sbits.bits, c->scratch};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);

@@ -6,9 +6,9 @@
 // Geometry pass.  After lb_init, walls_set and a first particles_set one
 // lattice-wide pass (k_geometry) writes each fluid node's neighbour word --
 // so the sweep reads one word per node instead of 18 neighbour owners --
-// and, at each cell node, appends the cell's bounce links and sums its
+// clears the pending moving-boundary terms and, at each cell node, sums its
 // contact links.  Inside the steps the same results come incrementally
-// (particle_kernels.cu: k_nbm_update, k_cell_links).
+// (particle_kernels.cu: k_nbm_update, k_contacts).
 #include "bl_internal.cuh"
 
 namespace bl {
@@ -16,17 +16,17 @@ namespace bl {
 // ---------------------------------------------------------------------------
 // geometry pass over the owner map (one thread per node, 128 along x)
 //
-//   fluid node  -> neighbour word (NB_* bits)
-//   cell node x of cell p, neighbour x + c_r fluid -> bounce link of p: the
-//                  fluid node y = x + c_r streams direction rbar into p
+//   fluid node  -> neighbour word (NB_* bits); no pending C (the pass runs
+//                  where none is pending: after lb_init, walls_set, and a
+//                  first particles_set, each of which gives pending C to the
+//                  populations first)
 //   cell node x of cell p, neighbour x + c_r another cell or a wall -> contact
 //                  link (Eqs. deltapppp, deltapppm): its constant momentum
 //                  -2 alpha_r rho_bar c_r goes into p's exact integer sums
 //                  cK = sum m_r c_r, cIT = sum m_r dI x c_r, dI = x - rint(X_p)
 //
-// A warp appends its links cell by cell with one atomic on the cell's count,
-// in direction order, so that the link kernels read consecutive nodes of one
-// direction.  The counts start at zero (the claims kernel clears them).
+// A warp adds its contact sums cell by cell with one atomic per value.  The
+// sums start at zero (the claims kernel clears them).
 __global__ void __launch_bounds__(128) k_geometry(LatticeView lv, PartView pv) {
   using D = D3Q19;
   const unsigned FULL = 0xffffffffu;
@@ -42,9 +42,12 @@ __global__ void __launch_bounds__(128) k_geometry(LatticeView lv, PartView pv) {
   const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
   const int zs[3] = {z == 0 ? lv.nz - 1 : z - 1, z, z == lv.nz - 1 ? 0 : z + 1};
   const int own = valid ? lv.owner[n] : -2;
-  unsigned lmask = 0, cmask = 0;
+  unsigned cmask = 0;
+  if (valid) reinterpret_cast<float *>(lv.pu + n)[3] = 0.f;  // no pending C
   if (own >= FLUID) {
     unsigned solid = 0, wall = 0, same = 0;
+    int first = -1;
+    bool mixed = false;
     sfor<1, Q>([&](auto R) {
       constexpr int r = decltype(R)::value;
       const unsigned nb = (unsigned)xs[1 + D::cx(r)] + (unsigned)nx * (unsigned)ys[1 + D::cy(r)] +
@@ -53,47 +56,22 @@ __global__ void __launch_bounds__(128) k_geometry(LatticeView lv, PartView pv) {
       solid |= (on != FLUID ? 1u : 0u) << r;
       wall |= (on <= -2 ? 1u : 0u) << r;
       same |= (on == own ? 1u : 0u) << r;
+      if (on != FLUID) {
+        if (first == -1) first = on;
+        else if (on != first) mixed = true;
+      }
     });
     if (own == FLUID) {
       lv.nbm[n] = NB_FLUID | solid | (wall ? NB_WALL : 0u) | ((solid & ~wall) ? NB_CELL : 0u);
+      lv.nbc[n] = (first >= 0 && !mixed) ? (uint32_t)first : NBC_MIXED;
     } else {
       lv.nbm[n] = 0u;
-      lmask = NB_SOLID & ~solid;  // fluid neighbours
-      cmask = solid & ~same;      // other cells and walls
+      cmask = solid & ~same;  // other cells and walls
     }
   } else if (valid) {
     lv.nbm[n] = 0u;
   }
-  if (pv.n == 0) return;  // no cell nodes: nothing to append (uniform per launch)
-
-  // bounce links, one group of lanes per cell
-  unsigned pend = __ballot_sync(FULL, lmask != 0u);
-  while (pend) {
-    const int leader = __ffs(pend) - 1;
-    const int cell = __shfl_sync(FULL, own, leader);
-    const bool mine = lmask != 0u && own == cell;
-    const unsigned grp = __ballot_sync(FULL, mine);
-    const int tot = __reduce_add_sync(FULL, mine ? __popc(lmask) : 0);
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&pv.lk_count[cell], tot);
-    base = __shfl_sync(FULL, base, leader);
-    if (base + tot > pv.lk_cap && lane == leader) atomicOr(pv.status, ST_OVERFLOW);
-    unsigned long long *lk = pv.lk + (size_t)cell * pv.lk_cap;
-    const unsigned below = (1u << lane) - 1u;
-    int run = base;
-    sfor<1, Q>([&](auto R) {
-      constexpr int r = decltype(R)::value;
-      const bool has = mine && ((lmask >> r) & 1u);
-      const unsigned b = __ballot_sync(FULL, has);
-      if (has) {
-        const int pos = run + __popc(b & below);
-        if (pos < pv.lk_cap)
-          lk[pos] = pack_xyzr(xs[1 + D::cx(r)], ys[1 + D::cy(r)], zs[1 + D::cz(r)], D::opp(r));
-      }
-      run += __popc(b);
-    });
-    pend &= ~grp;
-  }
+  if (pv.n == 0) return;  // no cell nodes: no contact links (uniform per launch)
 
   // contact links as exact integer sums
   int ci[6] = {0, 0, 0, 0, 0, 0};
@@ -114,7 +92,7 @@ __global__ void __launch_bounds__(128) k_geometry(LatticeView lv, PartView pv) {
       }
     });
   }
-  pend = __ballot_sync(FULL, cmask != 0u);
+  unsigned pend = __ballot_sync(FULL, cmask != 0u);
   while (pend) {
     const int leader = __ffs(pend) - 1;
     const int cell = __shfl_sync(FULL, own, leader);
@@ -317,14 +295,16 @@ __global__ void k_links(LatticeView lv, int contact, int pass, int *block_count,
 // host-side launchers
 
 // the sweep for each storage type (lb_sweep_f32.cu, lb_sweep_bf16.cu, lb_sweep_f16.cu)
-void launch_lb_step_f32(const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st);
-void launch_lb_step_bf16(const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st);
-void launch_lb_step_f16(const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st);
+void launch_lb_step_f32(const LatticeView &lv, int par, const WallAcc &wa, cudaStream_t st);
+void launch_lb_step_bf16(const LatticeView &lv, int par, const WallAcc &wa, cudaStream_t st);
+void launch_lb_step_f16(const LatticeView &lv, int par, const WallAcc &wa, cudaStream_t st);
 
-void launch_lb_step(int dtype, const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st) {
-  if (dtype == 0) launch_lb_step_f32(lv, par, wa, status, st);
-  else if (dtype == 1) launch_lb_step_bf16(lv, par, wa, status, st);
-  else launch_lb_step_f16(lv, par, wa, status, st);
+void launch_lb_step(int dtype, const LatticeView &lv0, int par, const WallAcc &wa, int *status, cudaStream_t st) {
+  LatticeView lv = lv0;
+  lv.status = status;
+  if (dtype == 0) launch_lb_step_f32(lv, par, wa, st);
+  else if (dtype == 1) launch_lb_step_bf16(lv, par, wa, st);
+  else launch_lb_step_f16(lv, par, wa, st);
 }
 
 static inline unsigned nblk(unsigned n, unsigned b) { return (n + b - 1) / b; }

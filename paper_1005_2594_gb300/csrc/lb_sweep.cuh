@@ -21,10 +21,14 @@
 //
 // Cells.  A population that meets a cell node is bounced here without the
 // moving-boundary term: the cell's velocity of the half step is not known
-// yet.  The sweep records the node's density; the cell kernels then sum the
-// cell's link momenta over its link list, solve for the half-step velocity
-// and add C to each of its bounced populations (reading Q3, implicit
-// coupling).
+// yet (reading Q3, implicit coupling).  The node writes one link record per
+// cell it borders (its direction mask, its density and the sum of 2 f~*_r c_r
+// over those links) into the cell's bucket, from which the link kernel sums
+// the cell's link momentum and drag matrices.  After the solve each node's
+// record of its first cell becomes its pending velocity pu = rho (V + W x d)
+// with the bounced directions; the next sweep reads pu with the
+// populations and adds C = -(m_r / 6) c_r . pu (Eq. c, at the link midpoint;
+// c_r . (W x c_r / 2) = 0) to those populations before the moments.
 // Walls move at a known velocity: their links get C here, and the wall's
 // momentum is summed per warp (constant part 2 alpha_r rho_bar c_r as exact
 // integers) before one atomic per wall and component.
@@ -38,6 +42,13 @@ namespace bl {
 // blocks of 128 threads resident per SM: 8 caps the sweep at 64 registers
 #ifndef BL_LB_MINB
 #define BL_LB_MINB 8
+#endif
+// the bulk-copy sweep: resident blocks per SM (its register cap) and stages
+#ifndef BL_BULK_MINB
+#define BL_BULK_MINB 6
+#endif
+#ifndef BL_BULK_TS
+#define BL_BULK_TS 3
 #endif
 
 // warp-level sum of the wall momenta, one atomic per wall and component
@@ -75,32 +86,133 @@ __device__ __forceinline__ unsigned src_slot(int r, unsigned N, unsigned n, cons
   return (unsigned)D::opp(r) * N + xo[1 - D::cx(r)] + yo[1 - D::cy(r)] + zo[1 - D::cz(r)];
 }
 
-// One fluid node of the sweep: moments, collision, streaming with
-// bounce-back and the wall momentum.  load(r, slot) gives the incoming
-// population of direction r (from the slot src_slot names).
+// the primary link record a node hands to the warp-level append (cell p < 0:
+// no cell link)
+struct CellLink {
+  int p;
+  uint32_t mask;
+  float rho, F[3];
+};
+
+// warp-level append of the lanes' primary link records to their cells'
+// buckets, one atomic per (warp, cell), in two halves so that the atomic's
+// round trip can overlap other work (a block barrier): reserve takes the
+// slots, write stores the records; all 32 lanes call both
+struct LinkSlot {
+  unsigned grp;
+  int base;
+};
+
+__device__ __forceinline__ LinkSlot reserve_links(const LatticeView &lv, const CellLink &cl) {
+  const unsigned FULL = 0xffffffffu;
+  LinkSlot sl{0u, 0};
+  if (!__ballot_sync(FULL, cl.p >= 0)) return sl;
+  sl.grp = __match_any_sync(FULL, cl.p);
+  if (cl.p >= 0 && (threadIdx.x & 31) == __ffs(sl.grp) - 1) sl.base = atomicAdd(&lv.rec_count[cl.p], __popc(sl.grp));
+  return sl;
+}
+
+__device__ __forceinline__ void write_links(const LatticeView &lv, const CellLink &cl, unsigned n, const LinkSlot &sl) {
+  if (cl.p < 0) return;
+  const int lane = threadIdx.x & 31;
+  const int base = __shfl_sync(sl.grp, sl.base, __ffs(sl.grp) - 1);
+  const int pos = base + __popc(sl.grp & ((1u << lane) - 1u));
+  if (pos < lv.rec_cap) {
+    float4 *r = lv.rec + 2 * ((size_t)cl.p * lv.rec_cap + pos);
+    r[0] = make_float4(__uint_as_float(n), __uint_as_float(cl.mask), cl.rho, cl.F[0]);
+    r[1] = make_float4(cl.F[1], cl.F[2], 0.f, 0.f);
+  } else {
+    atomicOr(lv.status, ST_OVERFLOW);
+  }
+}
+
+__device__ __forceinline__ void emit_links(const LatticeView &lv, const CellLink &cl, unsigned n) {
+  const LinkSlot sl = reserve_links(lv, cl);
+  write_links(lv, cl, n, sl);
+}
+
+// the neighbour n + c_r for a direction r known only at run time: the
+// components of c_r + 1 packed two bits per direction, the coordinate
+// chosen by selects (no indexing of the xo, yo, zo arrays)
+template <int A>
+__host__ __device__ constexpr unsigned long long packed_dirs() {
+  unsigned long long v = 0;
+  for (int r = 0; r < Q; ++r)
+    v |= (unsigned long long)((A == 0 ? D3Q19::cx(r) : (A == 1 ? D3Q19::cy(r) : D3Q19::cz(r))) + 1) << (2 * r);
+  return v;
+}
+__device__ __forceinline__ unsigned pick3(unsigned k, const unsigned v[3]) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); }
+__device__ __forceinline__ unsigned neighbour_rt(int r, const unsigned xo[3], const unsigned yo[3], const unsigned zo[3]) {
+  constexpr unsigned long long PX = packed_dirs<0>(), PY = packed_dirs<1>(), PZ = packed_dirs<2>();
+  return pick3((unsigned)(PX >> (2 * r)) & 3u, xo) + pick3((unsigned)(PY >> (2 * r)) & 3u, yo) +
+         pick3((unsigned)(PZ >> (2 * r)) & 3u, zo);
+}
+
+// the pending C of the last step's bounces off a cell: pu.xyz = rho (V + W x
+// d) of the cell at the node, pu.w the bounced directions (bit r); C_r =
+// -(m_r / 6) c_r . pu is added to the incoming population of direction rbar
+__device__ __forceinline__ void apply_pending(const float4 &pu, float (&f)[Q]) {
+  using D = D3Q19;
+  const uint32_t mask = __float_as_uint(pu.w);
+  sfor<1, Q>([&](auto R) {
+    constexpr int r = decltype(R)::value;
+    if (mask & (1u << r)) {
+      float cu = 0.f;
+      if constexpr (D::cx(r) != 0) cu += D::cx(r) * pu.x;
+      if constexpr (D::cy(r) != 0) cu += D::cy(r) * pu.y;
+      if constexpr (D::cz(r) != 0) cu += D::cz(r) * pu.z;
+      f[D::opp(r)] -= (D::m(r) / 6.0f) * cu;
+    }
+  });
+}
+
+// sum of 2 f~*_r c_r over the directions in mask
+__device__ __forceinline__ void link_sum(uint32_t mask, const float (&f)[Q], float (&F)[3]) {
+  using D = D3Q19;
+  float F0 = 0.f, F1 = 0.f, F2 = 0.f;
+  sfor<1, Q>([&](auto R) {
+    constexpr int r = decltype(R)::value;
+    if (mask & (1u << r)) {
+      if constexpr (D::cx(r) != 0) F0 += 2.0f * D::cx(r) * f[r];
+      if constexpr (D::cy(r) != 0) F1 += 2.0f * D::cy(r) * f[r];
+      if constexpr (D::cz(r) != 0) F2 += 2.0f * D::cz(r) * f[r];
+    }
+  });
+  F[0] = F0;
+  F[1] = F1;
+  F[2] = F2;
+}
+
+// one record appended to cell q's bucket by this thread alone
+__device__ __forceinline__ void append_link(const LatticeView &lv, unsigned n, int q, uint32_t mask, float rho,
+                                            float F0, float F1, float F2) {
+  const int pos = atomicAdd(&lv.rec_count[q], 1);
+  if (pos < lv.rec_cap) {
+    float4 *rr = lv.rec + 2 * ((size_t)q * lv.rec_cap + pos);
+    rr[0] = make_float4(__uint_as_float(n), __uint_as_float(mask), rho, F0);
+    rr[1] = make_float4(F1, F2, 0.f, 0.f);
+  } else {
+    atomicOr(lv.status, ST_OVERFLOW);
+  }
+}
+
+// One fluid node of the sweep: the pending C of its last bounces off a cell,
+// moments, collision, streaming with bounce-back, the wall momentum and its
+// cell links.  load(r, slot) gives the incoming population of direction r
+// (from the slot src_slot names); pu is the node's pending velocity.
 // FORCE: a body force is set (Guo forcing); TAU1: tau = 1, where the
 // relaxation gives the equilibrium itself
 template <class S, int PAR, bool FORCE, bool TAU1, class Load>
-__device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc &wa, int *status, unsigned n,
+__device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc &wa, unsigned n, const int xyz[3],
                                             const unsigned xo[3], const unsigned yo[3], const unsigned zo[3],
-                                            uint32_t nbw, Load load, int &wkey, float (&wF)[3], int (&wK)[3]) {
+                                            uint32_t nbw, uint32_t nbc, float4 pu, Load load, int &wkey,
+                                            float (&wF)[3], int (&wK)[3], CellLink &cl) {
   using D = D3Q19;
   const unsigned N = lv.N;
   S *pop = reinterpret_cast<S *>(lv.pop);
+  cl.p = -1;
   if (nbw & NB_FLUID) {
-    // neighbour classes from the geometry pass: solid = any non-fluid node;
-    // the wall subset is looked up only next to a wall
     const unsigned solid = nbw & NB_SOLID;
-    unsigned wall = 0;
-    if (nbw & NB_WALL) {
-      sfor<1, Q>([&](auto R) {
-        constexpr int r = decltype(R)::value;
-        if (solid & (1u << r)) {
-          const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
-          wall |= (lv.owner[nb] <= -2 ? 1u : 0u) << r;
-        }
-      });
-    }
     // incoming populations of this node (layout of the step's parity)
     float f[Q];
     sfor<0, Q>([&](auto R) {
@@ -113,6 +225,9 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
       }
       f[r] = load(r, src);
     });
+    // C of the last step's bounces off a cell (reading Q3)
+    const uint32_t pm = __float_as_uint(pu.w);
+    if (pm) apply_pending(pu, f);
     // moments (shifted: rho = rho_bar + sum f~, j = sum f~ c)
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
     sfor<0, Q>([&](auto R) {
@@ -132,7 +247,7 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
     }
     const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv, uz = (jz + 0.5f * Fz) * inv;
     const float uu = ux * ux + uy * uy + uz * uz;
-    if (!(rho > 0.f) || !(uu < 0.09f)) atomicOr(status, ST_UNSTABLE);
+    if (!(rho > 0.f) || !(uu < 0.09f)) atomicOr(lv.status, ST_UNSTABLE);
     const float om = lv.omega;
     const float src_w = 1.0f - 0.5f * om;
     const float uF = ux * Fx + uy * Fy + uz * Fz;
@@ -164,38 +279,95 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
       f[rb] = relax(f[rb], w, E - O, -cu, -cF);
     });
     Store<S>::st(pop + n, f[0]);
-    if (wall) {
-      // links into a wall (next to a wall only): the moving-wall term C for
-      // the population returning along rbar, 6 alpha_rbar rho c_rbar . v_wall,
-      // and the momentum the wall receives
-      sfor<1, Q>([&](auto R) {
-        constexpr int r = decltype(R)::value;
-        if (wall & (1u << r)) {
-          const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
-          const int w = -2 - lv.owner[nb];
-          const float C = -(D::m(r) / 6.0f) * rho *
-                          (D::cx(r) * lv.wall_vel[w][0] + D::cy(r) * lv.wall_vel[w][1] + D::cz(r) * lv.wall_vel[w][2]);
-          const float dp = 2.0f * f[r] + C;
-          if (wkey != w && wkey >= 0) {
-            // a node touching two different walls: flush the first one directly
-            for (int k = 0; k < 3; ++k) {
-              atomicAdd(&wa.F[3 * wkey + k], (double)wF[k]);
-              atomicAdd((unsigned long long *)&wa.K[3 * wkey + k], (unsigned long long)(long long)wK[k]);
-              wF[k] = 0.f;
-              wK[k] = 0;
-            }
-          }
-          wkey = w;
-          wF[0] += dp * D::cx(r);
-          wF[1] += dp * D::cy(r);
-          wF[2] += dp * D::cz(r);
-          wK[0] += D::m(r) * D::cx(r);
-          wK[1] += D::m(r) * D::cy(r);
-          wK[2] += D::m(r) * D::cz(r);
-          f[r] += C;
+    // neighbour classes from the geometry pass: solid = any non-fluid node;
+    // next to a wall or a cell the owners of the solid neighbours give the
+    // walls and the cells (in direction order: the first and a second cell
+    // each get a record and a pending C; a third, rare, its links one by one)
+    if (nbw & (NB_WALL | NB_CELL)) {
+      unsigned wall = 0, cmask = 0, cmask2 = 0, csec = 0;
+      int p1 = -1, p2 = -1;
+      // one cell and nothing else next to the node (the common case): its
+      // index from the neighbour-cell word, no owner to read
+      const bool one_cell = !(nbc & NBC_MIXED);
+      if (one_cell) {
+        p1 = (int)nbc;
+        cmask = solid;
+      }
+      for (unsigned m = one_cell ? 0u : solid; m; m &= m - 1u) {
+        const int r = __ffs(m) - 1;
+        const int ow = lv.owner[neighbour_rt(r, xo, yo, zo)];
+        if (ow <= -2) {
+          wall |= 1u << r;
+        } else if (p1 < 0 || ow == p1) {
+          p1 = ow;
+          cmask |= 1u << r;
+        } else if (p2 < 0 || ow == p2) {
+          p2 = ow;
+          cmask2 |= 1u << r;
+        } else {
+          csec |= 1u << r;
         }
-      });
+      }
+      if (wall) {
+        // links into a wall: the moving-wall term C for the population
+        // returning along rbar, 6 alpha_rbar rho c_rbar . v_wall, and the
+        // momentum the wall receives
+        sfor<1, Q>([&](auto R) {
+          constexpr int r = decltype(R)::value;
+          if (wall & (1u << r)) {
+            const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
+            const int w = -2 - lv.owner[nb];
+            const float C = -(D::m(r) / 6.0f) * rho *
+                            (D::cx(r) * lv.wall_vel[w][0] + D::cy(r) * lv.wall_vel[w][1] + D::cz(r) * lv.wall_vel[w][2]);
+            const float dp = 2.0f * f[r] + C;
+            if (wkey != w && wkey >= 0) {
+              // a node touching two different walls: flush the first one directly
+              for (int k = 0; k < 3; ++k) {
+                atomicAdd(&wa.F[3 * wkey + k], (double)wF[k]);
+                atomicAdd((unsigned long long *)&wa.K[3 * wkey + k], (unsigned long long)(long long)wK[k]);
+                wF[k] = 0.f;
+                wK[k] = 0;
+              }
+            }
+            wkey = w;
+            wF[0] += dp * D::cx(r);
+            wF[1] += dp * D::cy(r);
+            wF[2] += dp * D::cz(r);
+            wK[0] += D::m(r) * D::cx(r);
+            wK[1] += D::m(r) * D::cy(r);
+            wK[2] += D::m(r) * D::cz(r);
+            f[r] += C;
+          }
+        });
+      }
+      // cell links: the record of the first cell (sum of 2 f~*_r c_r over its
+      // directions) through the warp-level append; those of a second and a
+      // third cell, rarer, directly, marked for C in place after the solve
+      if (cmask) {
+        cl.p = p1;
+        cl.mask = cmask;
+        cl.rho = rho;
+        link_sum(cmask, f, cl.F);
+        if (cmask2) {
+          float F2[3];
+          link_sum(cmask2, f, F2);
+          append_link(lv, n, p2, cmask2 | REC_DIRECT, rho, F2[0], F2[1], F2[2]);
+        }
+        if (csec) {
+          sfor<1, Q>([&](auto R) {
+            constexpr int r = decltype(R)::value;
+            if (csec & (1u << r)) {
+              const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
+              append_link(lv, n, lv.owner[nb], (1u << r) | REC_DIRECT, rho, 2.0f * D::cx(r) * f[r],
+                          2.0f * D::cy(r) * f[r], 2.0f * D::cz(r) * f[r]);
+            }
+          });
+        }
+      }
     }
+    // a node whose C was pending and that has no first-cell record now: no
+    // pending C for the next sweep (a record's pu is written after the solve)
+    if (pm && cl.p < 0) reinterpret_cast<float *>(lv.pu + n)[3] = 0.f;
     // streaming, or bounce-back into the slot where the next step reads
     // direction rbar where the neighbour is solid: one store per direction,
     // its slot chosen without a branch (so that a warp mixing open and
@@ -210,12 +382,11 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
       const unsigned dst = (sol != (PAR == 1)) ? (unsigned)r * N + nb : (unsigned)rb * N + n;
       Store<S>::st(pop + dst, f[r]);
     });
-    if (nbw & NB_CELL) lv.rho_b[n] = rho;
   }
 }
 
 template <class S, int PAR, bool FORCE, bool TAU1>
-__global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, WallAcc wa, int *status) {
+__global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, WallAcc wa) {
   const int nx = lv.nx, ny = lv.ny;
   const int x0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
@@ -236,9 +407,15 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, Wal
   int wkey = -1;
   float wF[3] = {0.f, 0.f, 0.f};
   int wK[3] = {0, 0, 0};
-  if (nbw & NB_FLUID)
-    node_update<S, PAR, FORCE, TAU1>(lv, wa, status, n, xo, yo, zo, nbw,
-                                     [&](int, unsigned slot) { return Store<S>::ld(pop + slot); }, wkey, wF, wK);
+  CellLink cl;
+  cl.p = -1;
+  if (nbw & NB_FLUID) {
+    const int xyz[3] = {x, y, z};
+    node_update<S, PAR, FORCE, TAU1>(lv, wa, n, xyz, xo, yo, zo, nbw, lv.nbc[n], lv.pu[n],
+                                     [&](int, unsigned slot) { return Store<S>::ld(pop + slot); }, wkey, wF, wK,
+                                     cl);
+  }
+  emit_links(lv, cl, n);
   flush_wall_momentum(wa, wkey, wF, wK);
 }
 
@@ -264,7 +441,7 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 template <int PAR, bool FORCE, bool TAU1, int ZC>
-__global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv, WallAcc wa, int *status) {
+__global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv, WallAcc wa) {
   __shared__ float stage[PIPE_ST][Q][128];
   const int nx = lv.nx, ny = lv.ny, nz = lv.nz;
   const int tx = threadIdx.x;
@@ -314,12 +491,17 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv
     cp_async_commit();
     cp_async_wait<PIPE_ST - 1>();  // the copies of node z have landed
     const int b = i % PIPE_ST;
+    CellLink cl;
+    cl.p = -1;
+    unsigned zo[3];
+    zoff(z, zo);
     if (w[0] & NB_FLUID) {
-      unsigned zo[3];
-      zoff(z, zo);
-      node_update<float, PAR, FORCE, TAU1>(lv, wa, status, rowb + zo[1], xo, yo, zo, w[0],
-                                           [&](int r, unsigned) { return stage[b][r][tx]; }, wkey, wF, wK);
+      const int xyz[3] = {x, y, z};
+      node_update<float, PAR, FORCE, TAU1>(lv, wa, rowb + zo[1], xyz, xo, yo, zo, w[0], lv.nbc[rowb + zo[1]],
+                                           lv.pu[rowb + zo[1]],
+                                           [&](int r, unsigned) { return stage[b][r][tx]; }, wkey, wF, wK, cl);
     }
+    emit_links(lv, cl, rowb + zo[1]);
 #pragma unroll
     for (int k = 0; k < PIPE_ST - 1; ++k) w[k] = w[k + 1];
   }
@@ -370,10 +552,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 }
 
 template <class S, int PAR, bool FORCE, bool TAU1, int ZC, int TS>
-__global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc wa, int *status) {
+__global__ void __launch_bounds__(128, BL_BULK_MINB) k_lb_step_bulk(LatticeView lv, WallAcc wa) {
   using D = D3Q19;
   __shared__ alignas(128) S sb[TS][Q][128];        // [stage][array][x]
   __shared__ alignas(128) uint32_t sw[TS][128];    // [stage][x] neighbour words
+  __shared__ alignas(128) float4 spu[TS][128];     // [stage][x] pending velocities
+  __shared__ alignas(128) uint32_t sc[TS][128];    // [stage][x] neighbour-cell words
   __shared__ alignas(8) unsigned long long bar[TS];
   __shared__ int s_ok;
   const int nx = lv.nx, ny = lv.ny, nz = lv.nz;
@@ -402,7 +586,7 @@ __global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc
     unsigned zo[3];
     zoff(z, zo);
     const unsigned bytes = (unsigned)W * (unsigned)sizeof(S);
-    mbar_expect_tx(&bar[s], Q * bytes + (unsigned)W * 4u);
+    mbar_expect_tx(&bar[s], Q * bytes + (unsigned)W * 24u);
     sfor<0, Q>([&](auto R) {
       constexpr int r = decltype(R)::value;
       unsigned row;
@@ -411,6 +595,8 @@ __global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc
       bulk_g2s(&sb[s][r][0], pop + row + (unsigned)x0, bytes, &bar[s]);
     });
     bulk_g2s(&sw[s][0], lv.nbm + yo[1] + zo[1] + (unsigned)x0, (unsigned)W * 4u, &bar[s]);
+    bulk_g2s(&spu[s][0], lv.pu + yo[1] + zo[1] + (unsigned)x0, (unsigned)W * 16u, &bar[s]);
+    bulk_g2s(&sc[s][0], lv.nbc + yo[1] + zo[1] + (unsigned)x0, (unsigned)W * 4u, &bar[s]);
   };
   if (tx == 0) {
     for (int k = 0; k < TS; ++k) mbar_init(&bar[k], 1);
@@ -428,26 +614,32 @@ __global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc
     const int i = z - zb, s = i % TS;
     if (tx == 0) issue(z + TS - 1, (i + TS - 1) % TS);  // that stage was freed by the last barrier
     if (!mbar_wait(&bar[s], (unsigned)(i / TS) & 1u)) {
-      atomicOr(status, ST_BARRIER);
+      atomicOr(lv.status, ST_BARRIER);
       s_ok = 0;
     }
     __syncthreads();
     if (!s_ok) break;
     const uint32_t w = valid ? sw[s][tx] : 0u;
+    unsigned zo[3];
+    zoff(z, zo);
+    const unsigned n = (unsigned)x + yo[1] + zo[1];
+    CellLink cl;
+    cl.p = -1;
     if (w & NB_FLUID) {
-      unsigned zo[3];
-      zoff(z, zo);
+      const int xyz[3] = {x, y, z};
       node_update<S, PAR, FORCE, TAU1>(
-          lv, wa, status, (unsigned)x + yo[1] + zo[1], xo, yo, zo, w,
+          lv, wa, n, xyz, xo, yo, zo, w, sc[s][tx], spu[s][tx],
           [&](int r, unsigned slot) -> float {
             if (PAR == 0 || r == 0) return Store<S>::ld(&sb[s][r][tx]);
             int j = tx - D::cx(r);
             if (whole) j = j < 0 ? j + W : (j >= W ? j - W : j);
             return (j >= 0 && j < W) ? Store<S>::ld(&sb[s][r][j]) : Store<S>::ld(pop + slot);
           },
-          wkey, wF, wK);
+          wkey, wF, wK, cl);
     }
-    __syncthreads();  // stage s is read: free for refill
+    const LinkSlot sl = reserve_links(lv, cl);
+    __syncthreads();  // stage s is read: free for refill (the atomic's round trip overlaps it)
+    write_links(lv, cl, n, sl);
   }
   if (z < ze && tx == 0) {
     // gave up: let the copies still in flight land before the block exits
@@ -460,16 +652,15 @@ __global__ void __launch_bounds__(128, 6) k_lb_step_bulk(LatticeView lv, WallAcc
 // host-side launch of the sweep
 
 template <int PAR, bool FORCE, bool TAU1, int ZC>
-static void launch_pipe(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
-                        cudaStream_t st) {
+static void launch_pipe(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, cudaStream_t st) {
   const dim3 gp(grid.x, grid.y, (grid.z + ZC - 1) / ZC);
-  k_lb_step_pipe<PAR, FORCE, TAU1, ZC><<<gp, block, 0, st>>>(lv, wa, status);
+  k_lb_step_pipe<PAR, FORCE, TAU1, ZC><<<gp, block, 0, st>>>(lv, wa);
 }
 
 template <class S, int PAR, bool FORCE, bool TAU1, int ZC, int TS>
-static void launch_bulk(const LatticeView &lv, dim3 grid, const WallAcc &wa, int *status, cudaStream_t st) {
+static void launch_bulk(const LatticeView &lv, dim3 grid, const WallAcc &wa, cudaStream_t st) {
   const dim3 gp((lv.nx + 127) / 128, grid.y, (grid.z + ZC - 1) / ZC);
-  k_lb_step_bulk<S, PAR, FORCE, TAU1, ZC, TS><<<gp, 128, 0, st>>>(lv, wa, status);
+  k_lb_step_bulk<S, PAR, FORCE, TAU1, ZC, TS><<<gp, 128, 0, st>>>(lv, wa);
 }
 
 // row length for the bulk-copy sweep: 16-byte aligned rows of the storage type
@@ -479,37 +670,35 @@ __host__ __device__ inline bool bulk_rows_ok(int nx, int store_bytes) { return n
 // pipeline over 4 or 8 planes; 3, 4 the bulk-copy pipeline over 8 or 4 planes
 // with 3 stages (any storage type with 16-byte aligned rows, else variant 0)
 template <class S, int PAR, bool FORCE, bool TAU1>
-static void launch_lb_variant(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
-                              cudaStream_t st) {
+static void launch_lb_variant(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, cudaStream_t st) {
   if constexpr (std::is_same<S, float>::value) {
-    if (lv.sweep == 1) return launch_pipe<PAR, FORCE, TAU1, 4>(lv, grid, block, wa, status, st);
-    if (lv.sweep == 2) return launch_pipe<PAR, FORCE, TAU1, 8>(lv, grid, block, wa, status, st);
+    if (lv.sweep == 1) return launch_pipe<PAR, FORCE, TAU1, 4>(lv, grid, block, wa, st);
+    if (lv.sweep == 2) return launch_pipe<PAR, FORCE, TAU1, 8>(lv, grid, block, wa, st);
   }
   if (bulk_rows_ok(lv.nx, (int)sizeof(S))) {
-    if (lv.sweep == 3) return launch_bulk<S, PAR, FORCE, TAU1, 8, 3>(lv, grid, wa, status, st);
-    if (lv.sweep == 4) return launch_bulk<S, PAR, FORCE, TAU1, 4, 3>(lv, grid, wa, status, st);
+    if (lv.sweep == 3) return launch_bulk<S, PAR, FORCE, TAU1, 8, BL_BULK_TS>(lv, grid, wa, st);
+    if (lv.sweep == 4) return launch_bulk<S, PAR, FORCE, TAU1, 4, BL_BULK_TS>(lv, grid, wa, st);
   }
-  k_lb_step<S, PAR, FORCE, TAU1><<<grid, block, 0, st>>>(lv, wa, status);
+  k_lb_step<S, PAR, FORCE, TAU1><<<grid, block, 0, st>>>(lv, wa);
 }
 
 template <class S, int PAR, bool FORCE>
-static void launch_lb_tau(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, int *status,
-                          cudaStream_t st) {
-  if (lv.omega == 1.0f) launch_lb_variant<S, PAR, FORCE, true>(lv, grid, block, wa, status, st);
-  else launch_lb_variant<S, PAR, FORCE, false>(lv, grid, block, wa, status, st);
+static void launch_lb_tau(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, cudaStream_t st) {
+  if (lv.omega == 1.0f) launch_lb_variant<S, PAR, FORCE, true>(lv, grid, block, wa, st);
+  else launch_lb_variant<S, PAR, FORCE, false>(lv, grid, block, wa, st);
 }
 
 template <class S>
-static void launch_lb_typed(const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st) {
+static void launch_lb_typed(const LatticeView &lv, int par, const WallAcc &wa, cudaStream_t st) {
   const int bx = lv.nx >= 128 ? 128 : ((lv.nx + 31) / 32) * 32;
   dim3 block(bx, 1, 1);
   dim3 grid((lv.nx + bx - 1) / bx, lv.ny, lv.nz);
   if (par == 0) {
-    if (lv.has_force) launch_lb_tau<S, 0, true>(lv, grid, block, wa, status, st);
-    else launch_lb_tau<S, 0, false>(lv, grid, block, wa, status, st);
+    if (lv.has_force) launch_lb_tau<S, 0, true>(lv, grid, block, wa, st);
+    else launch_lb_tau<S, 0, false>(lv, grid, block, wa, st);
   } else {
-    if (lv.has_force) launch_lb_tau<S, 1, true>(lv, grid, block, wa, status, st);
-    else launch_lb_tau<S, 1, false>(lv, grid, block, wa, status, st);
+    if (lv.has_force) launch_lb_tau<S, 1, true>(lv, grid, block, wa, st);
+    else launch_lb_tau<S, 1, false>(lv, grid, block, wa, st);
   }
 }
 

@@ -3,8 +3,8 @@
 
 namespace bl {
 
-void launch_lb_step_f16(const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st) {
-  launch_lb_typed<__half>(lv, par, wa, status, st);
+void launch_lb_step_f16(const LatticeView &lv, int par, const WallAcc &wa, cudaStream_t st) {
+  launch_lb_typed<__half>(lv, par, wa, st);
 }
 
 }  // namespace bl

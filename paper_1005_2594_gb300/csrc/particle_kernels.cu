@@ -3,20 +3,23 @@
 //   cell list      count -> scan -> scatter -> per-bin sort, canonical (bin, id)
 //   potentials     Berne-Pechukas-scaled Hookean cell-cell pairs (Sec. III,
 //                  Eqs. phi, epsilon, sigma) and cell-wall spheres (Eq. sigmaw),
-//                  one block per cell, FP32 arithmetic, FP64 result
-//   link sums      per cell over its bounce-link list (Eq. deltap): link
-//                  momentum at the predictor and the drag matrices
+//                  one block per cell, FP64 contact geometry, FP32 forces,
+//                  FP64 result
+//   link sums      per cell over the link records the sweep wrote (Eq.
+//                  deltap): link momentum at the predictor and the drag
+//                  matrices
 //   solve          one thread per cell: velocities of the half step (reading
 //                  Q3), leap-frog on unit quaternions (reading Q4)
-//   link correct   the moving-boundary term C (Eq. c) on every bounced
-//                  population of the cell
+//   second links   the moving-boundary term C (Eq. c) on the rare links to a
+//                  node's second cell; the first cell's C is added by the
+//                  next sweep as it reads the bounced populations
 //   claims         one block per cell, one thread per lattice row: the nodes
 //                  the cell's new ellipsoid enters or leaves
 //   resolve        first-arrival owner rule (Sec. II single occupancy), then
 //                  fill/drain of every changed node with the momentum balance
 //                  given to the cells (Sec. II)
-// (the geometry pass that rebuilds the link lists from the new owner map is
-// a lattice-wide kernel in lb_kernels.cu)
+//   contacts       contact links of each cell as exact integer sums (Eqs.
+//                  deltapppp, deltapppm)
 //
 // Ownership.  claim[] holds INT_MAX ("free") on every node between steps.
 // A cell marks each fluid node its new ellipsoid enters with its index
@@ -27,9 +30,10 @@
 // is the first-arrival rule: an owner keeps a node while it covers it.
 //
 // FP64 is used only where the state needs it (positions, velocities, angular
-// momenta, the exact inside test near a surface); on this GPU a one-lane FP64
-// instruction costs a full warp slot of a narrow pipe, so sums, the 6 x 6
-// solve and the rotation increment are FP32 around FP64 reference values.
+// momenta, the exact inside test near a surface, the contact geometry of the
+// potentials); on this GPU a one-lane FP64 instruction costs a full warp
+// slot of a narrow pipe, so sums, the 6 x 6 solve and the rotation increment
+// are FP32 around FP64 reference values.
 #include <climits>
 
 #include "bl_internal.cuh"
@@ -133,6 +137,20 @@ __global__ void k_cl_sort(CellListView cl) {
 // shape function S, sigma and h are formed in FP64; the strength, its
 // derivatives and the force and torque, which multiply h without cancelling
 // it, in FP32.
+
+// FP32 test of a pair against its contact distance (Eq. sigma) with a
+// relative margin of 1e-4: false only for pairs certainly out of contact
+__device__ __forceinline__ bool near_contact(const float r[3], float r2, const float oi[3], const float oj[3],
+                                             const PartView &pv) {
+  if (!(r2 > 0.f)) return false;
+  const float ir = rsqrtf(r2);
+  const float a = (r[0] * oi[0] + r[1] * oi[1] + r[2] * oi[2]) * ir;
+  const float b = (r[0] * oj[0] + r[1] * oj[1] + r[2] * oj[2]) * ir;
+  const float c = oi[0] * oj[0] + oi[1] * oj[1] + oi[2] * oj[2];
+  const float chi = pv.chi, ap = a + b, am = a - b;
+  const float S = 1.0f - 0.5f * chi * (ap * ap / (1.0f + chi * c) + am * am / (1.0f - chi * c));
+  return r2 * S < pv.sigbar * pv.sigbar * 1.0002f;  // r < sigma_bar / sqrt(S) (1 + 1e-4)
+}
 
 // cell-cell pair, force and torque on i; r = X_j - X_i (Eqs. phi, epsilon,
 // sigma; the Gay-Berne factor eps2^mu of the variant)
@@ -393,6 +411,7 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
   const double Xd[3] = {pv.X[3 * i], pv.X[3 * i + 1], pv.X[3 * i + 2]};
   const double oid[3] = {pv.o[3 * i], pv.o[3 * i + 1], pv.o[3 * i + 2]};
   const double fd[3] = {Xd[0] - (double)Xi[0], Xd[1] - (double)Xi[1], Xd[2] - (double)Xi[2]};  // exact
+  const float oif[3] = {(float)oid[0], (float)oid[1], (float)oid[2]};
   const int dims[3] = {lv.nx, lv.ny, lv.nz};
   float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
   if (threadIdx.x < 27) {
@@ -419,9 +438,13 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
         float r[3];
         for (int m = 0; m < 3; ++m) r[m] = (float)imin_image(Xj[m] - Xi[m], dims[m], lv.per[m]) + (fj[m] - fi[m]);
         const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-        // no contact distance exceeds 2 max(sigma_perp, sigma_par): a pair
-        // farther than that in FP32, with margin, needs no FP64 geometry
+        // no contact distance exceeds 2 max(sigma_perp, sigma_par); nearer
+        // pairs first get the contact distance in FP32 (its error is ~1e-6
+        // relative, far inside the margin): only pairs at or within contact
+        // take the FP64 geometry
         if (r2 >= rc2 || r2 > smax2) continue;
+        const float oj[3] = {(float)pv.o[3 * j], (float)pv.o[3 * j + 1], (float)pv.o[3 * j + 2]};
+        if (!near_contact(r, r2, oif, oj, pv)) continue;
         double rd[3];
         for (int m = 0; m < 3; ++m) rd[m] = min_image_exact(__dsub_rn(pv.X[3 * j + m], Xd[m]), dims[m], lv.per[m]);
         const double ojd[3] = {pv.o[3 * j], pv.o[3 * j + 1], pv.o[3 * j + 2]};
@@ -448,6 +471,11 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
         if (lv.per[0]) x = wrapi(x, lv.nx);
         else if (x < 0 || x >= lv.nx) continue;
         if (!((row[x >> 5] >> (x & 31)) & 1u)) continue;
+        // FP32 test against the wall sphere's radius first (margin 1e-4)
+        const float rx = (float)dx - fi[0];
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        const float af = rx * oif[0] + ry * oif[1] + rz * oif[2];
+        if (!(r2 > 0.f) || (r2 - pv.chi_w * af * af) >= pv.sigbar_w * pv.sigbar_w * 1.0002f) continue;
         const double rd[3] = {(double)dx - fd[0], (double)oy - fd[1], (double)oz - fd[2]};
         bp_wall(rd, oid, pv, F, T);
       }
@@ -591,84 +619,139 @@ __device__ __forceinline__ void cell_geo(const PartView &pv, int p, CellGeo &g) 
 
 // ---------------------------------------------------------------------------
 // implicit coupling (reading Q3).  The sweep bounced each cell's links
-// without C and appended them to the cell's segment.  With the predictor
-// (Vp, Wp) = velocities of t-1/2 the link momentum is (2 f*_r + C(Vp, Wp)) c_r;
-// the link kernel sums it (variable part in FP32, 2 alpha_r rho_bar c_r as
-// exact integers) with the drag matrices Z = sum (m_r / 6) rho [c; a x c][c;
-// a x c]^T.  The half-step velocities V = Vp + dV, W = Wp + dW solve
+// without C and wrote one record per (fluid node, cell) into the cell's
+// bucket.  With the predictor (Vp, Wp) = velocities of t-1/2 the link
+// momentum is (2 f*_r + C(Vp, Wp)) c_r; the reduction sums it (variable part
+// in FP32, 2 alpha_r rho_bar c_r as exact integers) with the drag matrices
+// Z = sum (m_r / 6) rho [c; a x c][c; a x c]^T.  The half-step velocities
+// V = Vp + dV, W = Wp + dW solve
 //   (m + Zff) dV + Zft dW = F_tot(Vp, Wp) - m (Vp - V(t-1/2))
 //   Ztf dV + (I + Ztt) dW = T_tot(Vp, Wp) + L(t-1/2) - I Wp,
-// and the correction kernel gives each bounced population C(V, W), so the
-// fluid and the cell exchange the same momentum.
+// and the bounced populations get C(V, W) (the next sweep adds it as it
+// reads them), so the fluid and the cell exchange the same momentum.
 //
-// Link kernels run on a grid (chunk, cell): each block takes CB links of one
-// cell, reduces them, and adds the block's sums with one atomic per value.
+// All links of one node into a cell share d = y - X: the arm of link r is
+// a_r = d + c_r / 2 and a_r x c_r = d x c_r.  So a record (rho, mask, F_raw =
+// sum over the mask of 2 f~*_r c_r) gives
+//   F0 = F_raw - rho M v_p,  T0 = d x F0,  v_p = Vp + Wp x d,
+//   Zff = rho M,  Zft = rho M [d]x^T,  Ztt = [d]x rho M [d]x^T,
+// with M = sum over the mask of (m_r / 6) c_r c_r^T, and the constant parts
+// K = sum m_r c_r, IT = d_int x K with d_int = y - rint(X) exactly.
 
-constexpr int LT = 128;            // threads of a link-sum block
-constexpr int LPT = 8;             // links per thread
-constexpr int LCHUNK = LT * LPT;   // links per link-sum block
+constexpr int LT = 128;  // threads of a link-reduction block
 
-template <class S>
-__global__ void __launch_bounds__(LT) k_link_sums(LatticeView lv, PartView pv, int par) {
-  using D = D3Q19;
+// direction masks of the lattice (bit r), for the record sums by popcount
+template <class P>
+__host__ __device__ constexpr uint32_t dir_mask(P pred) {
+  uint32_t m = 0;
+  for (int r = 1; r < Q; ++r)
+    if (pred(r)) m |= 1u << r;
+  return m;
+}
+using D3 = D3Q19;
+constexpr int cxyz(int r, int a) { return a == 0 ? D3::cx(r) : (a == 1 ? D3::cy(r) : D3::cz(r)); }
+template <int A, int SGN>
+struct AxisDirs {  // axis vectors along A with sign SGN (m = 2)
+  static constexpr uint32_t v = dir_mask([](int r) { return r <= 6 && cxyz(r, A) == SGN; });
+};
+template <int A, int SGN>
+struct DiagDirs {  // diagonal vectors with c_A = SGN (m = 1)
+  static constexpr uint32_t v = dir_mask([](int r) { return r > 6 && cxyz(r, A) == SGN; });
+};
+template <int A, int B, int SGN>
+struct PairDirs {  // diagonal vectors with c_A c_B = SGN
+  static constexpr uint32_t v = dir_mask([](int r) { return r > 6 && cxyz(r, A) * cxyz(r, B) == SGN; });
+};
+
+__device__ __forceinline__ int popm(uint32_t m, uint32_t sel) { return __popc(m & sel); }
+
+__global__ void __launch_bounds__(LT) k_link_reduce(LatticeView lv, PartView pv) {
   __shared__ float shf[LT / 32][27];
   __shared__ int shi[LT / 32][6];
-  const int p = blockIdx.y;
-  const int nlk = min(pv.lk_count[p], pv.lk_cap);
-  const int first = blockIdx.x * LCHUNK;
-  if (first >= nlk) return;
+  const int p = blockIdx.x;
+  const int nrec = min(lv.rec_count[p], lv.rec_cap);
   const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
-  const S *pop = reinterpret_cast<const S *>(lv.pop);
-  const unsigned long long *lk = pv.lk + (size_t)p * pv.lk_cap;
+  const int Xi[3] = {(int)k0.w, (int)k1.w, (int)k2.w};
+  const unsigned nx = (unsigned)lv.nx, nxy = (unsigned)lv.nx * (unsigned)lv.ny;
   float v[27];
   int iv[6];
 #pragma unroll
   for (int k = 0; k < 27; ++k) v[k] = 0.f;
 #pragma unroll
   for (int k = 0; k < 6; ++k) iv[k] = 0;
-  const int last = min(first + LCHUNK, nlk);
-  for (int i = first + threadIdx.x; i < last; i += LT) {
-    int yc[3], r;
-    unpack_xyzr(lk[i], yc, r);
-    const unsigned y = node_of(lv, yc[0], yc[1], yc[2]);
-    const float fs = Store<S>::ld(pop + bounce_slot(lv, par, y, yc, r));
-    const float rho = lv.rho_b[y];
-    const int di[3] = {imin_image(yc[0] - (int)k0.w, lv.nx, lv.per[0]), imin_image(yc[1] - (int)k1.w, lv.ny, lv.per[1]),
-                       imin_image(yc[2] - (int)k2.w, lv.nz, lv.per[2])};
-    const float c[3] = {(float)D::cx(r), (float)D::cy(r), (float)D::cz(r)};
-    const int m = D::m(r);
-    const float a[3] = {(float)di[0] + 0.5f * c[0] - k0.x, (float)di[1] + 0.5f * c[1] - k0.y,
-                        (float)di[2] + 0.5f * c[2] - k0.z};
-    const float b[3] = {a[1] * c[2] - a[2] * c[1], a[2] * c[0] - a[0] * c[2], a[0] * c[1] - a[1] * c[0]};
-    const float vb = c[0] * k1.x + c[1] * k1.y + c[2] * k1.z + b[0] * k2.x + b[1] * k2.y + b[2] * k2.z;
-    const float w = (m / 6.0f) * rho;
-    const float dp = 2.0f * fs - w * vb;  // 2 f~*_r + C(Vp, Wp), C = -(m_r / 6) rho c.v_b
+  const float4 *rec = lv.rec + 2 * (size_t)p * lv.rec_cap;
+  for (int i = threadIdx.x; i < nrec; i += LT) {
+    const float4 r0 = rec[2 * i], r1 = rec[2 * i + 1];
+    const unsigned n = __float_as_uint(r0.x);
+    const uint32_t m = __float_as_uint(r0.y) & NB_SOLID;
+    const float rho = r0.z;
+    const unsigned z = n / nxy, rem = n - z * nxy, y = rem / nx, x = rem - y * nx;
+    const int di[3] = {imin_image((int)x - Xi[0], lv.nx, lv.per[0]), imin_image((int)y - Xi[1], lv.ny, lv.per[1]),
+                       imin_image((int)z - Xi[2], lv.nz, lv.per[2])};
+    const float d[3] = {(float)di[0] - k0.x, (float)di[1] - k0.y, (float)di[2] - k0.z};
+    // rho M and K from the mask
+    const float w6 = rho * (1.0f / 6.0f);
+    const float Axx = w6 * (float)(2 * popm(m, AxisDirs<0, 1>::v | AxisDirs<0, -1>::v) +
+                                   popm(m, DiagDirs<0, 1>::v | DiagDirs<0, -1>::v));
+    const float Ayy = w6 * (float)(2 * popm(m, AxisDirs<1, 1>::v | AxisDirs<1, -1>::v) +
+                                   popm(m, DiagDirs<1, 1>::v | DiagDirs<1, -1>::v));
+    const float Azz = w6 * (float)(2 * popm(m, AxisDirs<2, 1>::v | AxisDirs<2, -1>::v) +
+                                   popm(m, DiagDirs<2, 1>::v | DiagDirs<2, -1>::v));
+    const float Axy = w6 * (float)(popm(m, PairDirs<0, 1, 1>::v) - popm(m, PairDirs<0, 1, -1>::v));
+    const float Axz = w6 * (float)(popm(m, PairDirs<0, 2, 1>::v) - popm(m, PairDirs<0, 2, -1>::v));
+    const float Ayz = w6 * (float)(popm(m, PairDirs<1, 2, 1>::v) - popm(m, PairDirs<1, 2, -1>::v));
+    const int K[3] = {2 * (popm(m, AxisDirs<0, 1>::v) - popm(m, AxisDirs<0, -1>::v)) + popm(m, DiagDirs<0, 1>::v) -
+                          popm(m, DiagDirs<0, -1>::v),
+                      2 * (popm(m, AxisDirs<1, 1>::v) - popm(m, AxisDirs<1, -1>::v)) + popm(m, DiagDirs<1, 1>::v) -
+                          popm(m, DiagDirs<1, -1>::v),
+                      2 * (popm(m, AxisDirs<2, 1>::v) - popm(m, AxisDirs<2, -1>::v)) + popm(m, DiagDirs<2, 1>::v) -
+                          popm(m, DiagDirs<2, -1>::v)};
+    const float A[3][3] = {{Axx, Axy, Axz}, {Axy, Ayy, Ayz}, {Axz, Ayz, Azz}};
+    // predictor velocity at the node and the link momentum
+    const float vp[3] = {k1.x + (k2.y * d[2] - k2.z * d[1]), k1.y + (k2.z * d[0] - k2.x * d[2]),
+                         k1.z + (k2.x * d[1] - k2.y * d[0])};
+    float F[3];
+    F[0] = r0.w - (A[0][0] * vp[0] + A[0][1] * vp[1] + A[0][2] * vp[2]);
+    F[1] = r1.x - (A[1][0] * vp[0] + A[1][1] * vp[1] + A[1][2] * vp[2]);
+    F[2] = r1.y - (A[2][0] * vp[0] + A[2][1] * vp[1] + A[2][2] * vp[2]);
+    v[0] += F[0];
+    v[1] += F[1];
+    v[2] += F[2];
+    v[3] += d[1] * F[2] - d[2] * F[1];
+    v[4] += d[2] * F[0] - d[0] * F[2];
+    v[5] += d[0] * F[1] - d[1] * F[0];
+    v[6] += Axx;
+    v[7] += Axy;
+    v[8] += Axz;
+    v[9] += Ayy;
+    v[10] += Ayz;
+    v[11] += Azz;
+    // G = A [d]x^T (the Zft block), then Ztt = [d]x G
+    float G[3][3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      v[k] += dp * c[k];
-      v[3 + k] += dp * b[k];  // a x (dp c) = dp (a x c)
+    for (int a = 0; a < 3; ++a) {
+      G[a][0] = A[a][2] * d[1] - A[a][1] * d[2];
+      G[a][1] = A[a][0] * d[2] - A[a][2] * d[0];
+      G[a][2] = A[a][1] * d[0] - A[a][0] * d[1];
     }
-    int k = 6;
 #pragma unroll
-    for (int s2 = 0; s2 < 3; ++s2)
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int t = s2; t < 3; ++t) v[k++] += w * c[s2] * c[t];
-#pragma unroll
-    for (int s2 = 0; s2 < 3; ++s2)
-#pragma unroll
-      for (int t = 0; t < 3; ++t) v[k++] += w * c[s2] * b[t];
-#pragma unroll
-    for (int s2 = 0; s2 < 3; ++s2)
-#pragma unroll
-      for (int t = s2; t < 3; ++t) v[k++] += w * b[s2] * b[t];
-    iv[0] += m * D::cx(r);
-    iv[1] += m * D::cy(r);
-    iv[2] += m * D::cz(r);
-    iv[3] += m * (di[1] * D::cz(r) - di[2] * D::cy(r));
-    iv[4] += m * (di[2] * D::cx(r) - di[0] * D::cz(r));
-    iv[5] += m * (di[0] * D::cy(r) - di[1] * D::cx(r));
+      for (int b = 0; b < 3; ++b) v[12 + 3 * a + b] += G[a][b];
+    v[21] += G[2][0] * d[1] - G[1][0] * d[2];
+    v[22] += G[2][1] * d[1] - G[1][1] * d[2];
+    v[23] += G[2][2] * d[1] - G[1][2] * d[2];
+    v[24] += G[0][1] * d[2] - G[2][1] * d[0];
+    v[25] += G[0][2] * d[2] - G[2][2] * d[0];
+    v[26] += G[1][2] * d[0] - G[0][2] * d[1];
+    iv[0] += K[0];
+    iv[1] += K[1];
+    iv[2] += K[2];
+    iv[3] += di[1] * K[2] - di[2] * K[1];
+    iv[4] += di[2] * K[0] - di[0] * K[2];
+    iv[5] += di[0] * K[1] - di[1] * K[0];
   }
-  // warp sums, then one thread per value adds the warps and issues the atomic
+  // warp sums, then one thread per value adds the warps (FP64) and writes
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 27; ++k) {
@@ -682,13 +765,17 @@ __global__ void __launch_bounds__(LT) k_link_sums(LatticeView lv, PartView pv, i
   }
   __syncthreads();
   if (threadIdx.x < 27) {
-    float t = 0.f;
-    for (int w2 = 0; w2 < LT / 32; ++w2) t += shf[w2][threadIdx.x];
-    atomicAdd(&pv.lsum[27 * p + threadIdx.x], (double)t);
+    double t = 0.0;
+    for (int w2 = 0; w2 < LT / 32; ++w2) t += (double)shf[w2][threadIdx.x];
+    pv.lsum[27 * p + threadIdx.x] = t;
   } else if (threadIdx.x >= 32 && threadIdx.x < 38) {
     int t = 0;
     for (int w2 = 0; w2 < LT / 32; ++w2) t += shi[w2][threadIdx.x - 32];
-    atomicAdd(&pv.lsum_i[6 * p + threadIdx.x - 32], t);
+    pv.lsum_i[6 * p + threadIdx.x - 32] = t;
+  } else if (threadIdx.x == 64) {
+    // the bucket is read: keep its size for the link read-out, empty it for the next sweep
+    pv.rec_last[p] = nrec;
+    lv.rec_count[p] = 0;
   }
 }
 
@@ -714,16 +801,12 @@ __global__ void k_solve(LatticeView lv, PartView pv) {
   for (int k = 0; k < 27; ++k) {
     v[k] = (float)pv.lsum[27 * p + k];
     if (k < 6) vd[k] = pv.lsum[27 * p + k];
-    pv.lsum[27 * p + k] = 0.0;
   }
   double K[3], IT[3];
   for (int k = 0; k < 3; ++k) {
+    // (the link reduction and the contact kernel rewrite these every step)
     K[k] = (double)(pv.lsum_i[6 * p + k] + pv.cK[3 * p + k]);
     IT[k] = (double)(pv.lsum_i[6 * p + 3 + k] + pv.cIT[3 * p + k]);
-    pv.lsum_i[6 * p + k] = 0;
-    pv.lsum_i[6 * p + 3 + k] = 0;
-    pv.cK[3 * p + k] = 0;
-    pv.cIT[3 * p + k] = 0;
   }
   // link force at the predictor: variable part + exact constant part, with
   // f = X - rint(X) the fraction the sweep's lever arms used
@@ -837,30 +920,72 @@ __global__ void k_solve(LatticeView lv, PartView pv) {
   write_kin(pv, p, X, V, W);
 }
 
-// C(V, W) on every bounced population of a cell
+// The pending moving-boundary term of each record, right after the solve
+// (one block per cell, beside the claims).  A record of a node's first cell
+// becomes the node's pending velocity pu = rho (V + W x d) with its bounced
+// directions, which the next sweep adds as C = -(m_r / 6) c_r . pu to the
+// populations it reads; the records of a second or third cell of one node
+// (marked REC_DIRECT) get their C in place.  V, W: the cell's half-step
+// velocities of the solve; d: node minus the cell's position of this step.
+// Every link is one cell's, so no two blocks touch the same slot.
 template <class S>
-__global__ void __launch_bounds__(CB) k_link_correct(LatticeView lv, PartView pv, int par) {
+__global__ void __launch_bounds__(LT) k_link_pending(LatticeView lv, PartView pv, int par) {
   using D = D3Q19;
-  const int p = blockIdx.y;
-  const int nlk = min(pv.lk_count[p], pv.lk_cap);
-  const int i = blockIdx.x * CB + threadIdx.x;
-  if (i >= nlk) return;
+  const int p = blockIdx.x;
+  const int nrec = min(pv.rec_last[p], lv.rec_cap);
   const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
+  const int Xi[3] = {(int)k0.w, (int)k1.w, (int)k2.w};
   const float *vw = pv.vw + 6 * p;
+  const float V[3] = {vw[0], vw[1], vw[2]}, W[3] = {vw[3], vw[4], vw[5]};
   S *pop = reinterpret_cast<S *>(lv.pop);
-  int yc[3], r;
-  unpack_xyzr(pv.lk[(size_t)p * pv.lk_cap + i], yc, r);
-  const unsigned y = node_of(lv, yc[0], yc[1], yc[2]);
-  const unsigned slot = bounce_slot(lv, par, y, yc, r);
-  const float c[3] = {(float)D::cx(r), (float)D::cy(r), (float)D::cz(r)};
-  const float a[3] = {(float)imin_image(yc[0] - (int)k0.w, lv.nx, lv.per[0]) + 0.5f * c[0] - k0.x,
-                      (float)imin_image(yc[1] - (int)k1.w, lv.ny, lv.per[1]) + 0.5f * c[1] - k0.y,
-                      (float)imin_image(yc[2] - (int)k2.w, lv.nz, lv.per[2]) + 0.5f * c[2] - k0.z};
-  const float vbx = vw[0] + (vw[4] * a[2] - vw[5] * a[1]);
-  const float vby = vw[1] + (vw[5] * a[0] - vw[3] * a[2]);
-  const float vbz = vw[2] + (vw[3] * a[1] - vw[4] * a[0]);
-  const float C = -(D::m(r) / 6.0f) * lv.rho_b[y] * (c[0] * vbx + c[1] * vby + c[2] * vbz);
-  Store<S>::st(pop + slot, Store<S>::ld(pop + slot) + C);
+  const float4 *rec = lv.rec + 2 * (size_t)p * lv.rec_cap;
+  for (int i = threadIdx.x; i < nrec; i += LT) {
+    const float4 r0 = rec[2 * i];
+    const unsigned n = __float_as_uint(r0.x);
+    const uint32_t mb = __float_as_uint(r0.y);
+    int yc[3];
+    node_xyz(lv, n, yc);
+    const float d[3] = {(float)imin_image(yc[0] - Xi[0], lv.nx, lv.per[0]) - k0.x,
+                        (float)imin_image(yc[1] - Xi[1], lv.ny, lv.per[1]) - k0.y,
+                        (float)imin_image(yc[2] - Xi[2], lv.nz, lv.per[2]) - k0.z};
+    const float u[3] = {r0.z * (V[0] + (W[1] * d[2] - W[2] * d[1])), r0.z * (V[1] + (W[2] * d[0] - W[0] * d[2])),
+                        r0.z * (V[2] + (W[0] * d[1] - W[1] * d[0]))};
+    const uint32_t mask = mb & NB_SOLID;
+    if (!(mb & REC_DIRECT)) {
+      lv.pu[n] = make_float4(u[0], u[1], u[2], __uint_as_float(mask));
+    } else {
+      for (uint32_t m = mask; m; m &= m - 1u) {
+        const int r = __ffs(m) - 1;
+        const float C = -(D::m(r) / 6.0f) * (D::cx(r) * u[0] + D::cy(r) * u[1] + D::cz(r) * u[2]);
+        const unsigned slot = bounce_slot(lv, par, n, yc, r);
+        Store<S>::st(pop + slot, Store<S>::ld(pop + slot) + C);
+      }
+    }
+  }
+}
+
+// The pending C of the last step given to the stored populations, for
+// read-outs and state changes between steps (the sweep's arithmetic); par is
+// the layout of the stored populations (the next step's parity).
+template <class S>
+__global__ void k_flush_pending(LatticeView lv, int par) {
+  using D = D3Q19;
+  S *pop = reinterpret_cast<S *>(lv.pop);
+  for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < lv.N; n += gridDim.x * blockDim.x) {
+    const float4 pu = lv.pu[n];
+    const uint32_t pm = __float_as_uint(pu.w);
+    if (!pm) continue;
+    int yc[3];
+    node_xyz(lv, n, yc);
+    for (uint32_t m = pm; m; m &= m - 1u) {
+      const int r = __ffs(m) - 1;
+      const float C = -(D::m(r) / 6.0f) * (D::cx(r) * pu.x + D::cy(r) * pu.y + D::cz(r) * pu.z);
+      // the slot from which node n reads direction rbar in layout par
+      const unsigned slot = bounce_slot(lv, par ^ 1, n, yc, r);
+      Store<S>::st(pop + slot, Store<S>::ld(pop + slot) + C);
+    }
+    reinterpret_cast<float *>(lv.pu + n)[3] = 0.f;
+  }
 }
 
 // particles_set: the state comes from the stage.  mode 1: first set (the
@@ -988,7 +1113,6 @@ __global__ void __launch_bounds__(PB) k_claims(LatticeView lv, PartView pv, int 
   if (threadIdx.x == 0) {
     sh_len = 0;
     if (mode != 0) {
-      pv.lk_count[p] = 0;
       for (int k = 0; k < 3; ++k) {
         pv.cK[3 * p + k] = 0;
         pv.cIT[3 * p + k] = 0;
@@ -1228,7 +1352,13 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
     if (nw >= 0)
       for (int k = 0; k < 3; ++k) arm_n[k] = min_image_exact((double)xyz[k] - pv.X[3 * nw + k], dims[k], lv.per[k]);
     if (old == FLUID && nw >= 0) {
-      // covered: the fluid is deleted, its momentum goes to the new owner
+      // covered: the fluid is deleted, its momentum goes to the new owner;
+      // its populations bounced off a cell in this step still owe their C
+      // (the next sweep would have added it): C_r enters direction rbar,
+      // momentum -C_r c_r, with the velocity of this step's half step at
+      // the link's cell at its position of this step
+      const float4 pu = lv.pu[idx];
+      const uint32_t pm = __float_as_uint(pu.w);
       if (impulses) {
         float mf[3] = {0.f, 0.f, 0.f};
         for (int r = 0; r < Q; ++r) {
@@ -1237,12 +1367,22 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
           mf[1] += v * D::cy(r);
           mf[2] += v * D::cz(r);
         }
+        // C_r owed to direction rbar: momentum -C_r c_r (the links to a second
+        // or third cell got theirs in place)
+        for (uint32_t m = pm; m; m &= m - 1u) {
+          const int r = __ffs(m) - 1;
+          const float C = -(D::m(r) / 6.0f) * (D::cx(r) * pu.x + D::cy(r) * pu.y + D::cz(r) * pu.z);
+          mf[0] -= C * D::cx(r);
+          mf[1] -= C * D::cy(r);
+          mf[2] -= C * D::cz(r);
+        }
         const double mom[3] = {mf[0], mf[1], mf[2]};
         const double tq[3] = {arm_n[1] * mom[2] - arm_n[2] * mom[1], arm_n[2] * mom[0] - arm_n[0] * mom[2],
                               arm_n[0] * mom[1] - arm_n[1] * mom[0]};
         atomic_add3(pv.PF + 3 * nw, mom);
         atomic_add3(pv.PT + 3 * nw, tq);
       }
+      if (pm) reinterpret_cast<float *>(lv.pu + idx)[3] = 0.f;
     } else if (old >= 0) {
       const double mom[3] = {pv.rho0 * u_o[0], pv.rho0 * u_o[1], pv.rho0 * u_o[2]};
       const double tq[3] = {arm_o[1] * mom[2] - arm_o[2] * mom[1], arm_o[2] * mom[0] - arm_o[0] * mom[2],
@@ -1282,20 +1422,28 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
 // neighbour word of node (x, y, z) from the owner map: bit 0 fluid, bit r
 // neighbour x + c_r solid, NB_WALL / NB_CELL some solid neighbour is a wall /
 // a cell; zero for solid nodes
-__device__ __forceinline__ uint32_t node_word(const LatticeView &lv, int x, int y, int z) {
+__device__ __forceinline__ uint32_t node_word(const LatticeView &lv, int x, int y, int z, uint32_t &cellw) {
   using D = D3Q19;
   const unsigned nx = (unsigned)lv.nx, nxy = (unsigned)lv.nx * (unsigned)lv.ny;
+  cellw = NBC_MIXED;
   if (lv.owner[(unsigned)x + nx * (unsigned)y + nxy * (unsigned)z] != FLUID) return 0u;
   const int xs[3] = {x == 0 ? lv.nx - 1 : x - 1, x, x == lv.nx - 1 ? 0 : x + 1};
   const int ys[3] = {y == 0 ? lv.ny - 1 : y - 1, y, y == lv.ny - 1 ? 0 : y + 1};
   const int zs[3] = {z == 0 ? lv.nz - 1 : z - 1, z, z == lv.nz - 1 ? 0 : z + 1};
   unsigned solid = 0, wall = 0;
+  int first = -1;
+  bool mixed = false;
   sfor<1, Q>([&](auto R) {
     constexpr int r = decltype(R)::value;
     const int on = lv.owner[(unsigned)xs[1 + D::cx(r)] + nx * (unsigned)ys[1 + D::cy(r)] + nxy * (unsigned)zs[1 + D::cz(r)]];
     solid |= (on != FLUID ? 1u : 0u) << r;
     wall |= (on <= -2 ? 1u : 0u) << r;
+    if (on != FLUID) {
+      if (first == -1) first = on;
+      else if (on != first) mixed = true;
+    }
   });
+  if (first >= 0 && !mixed) cellw = (uint32_t)first;
   return NB_FLUID | solid | (wall ? NB_WALL : 0u) | ((solid & ~wall) ? NB_CELL : 0u);
 }
 
@@ -1318,28 +1466,26 @@ __global__ void k_nbm_update(LatticeView lv, ChangeList chg) {
       xyz[1] = wrapi(xyz[1] - D::cy(r), lv.ny);
       xyz[2] = wrapi(xyz[2] - D::cz(r), lv.nz);
     }
-    lv.nbm[node_of(lv, xyz[0], xyz[1], xyz[2])] = node_word(lv, xyz[0], xyz[1], xyz[2]);
+    uint32_t cw;
+    const unsigned nn = node_of(lv, xyz[0], xyz[1], xyz[2]);
+    lv.nbm[nn] = node_word(lv, xyz[0], xyz[1], xyz[2], cw);
+    lv.nbc[nn] = cw;
   }
 }
 
-// link list and contact sums of one cell (one block per cell): the rows of
-// the cell's box, each cut to the outer interval of its ellipsoid at X(t+1),
-// flattened over the block; every node the cell owns appends the links from
-// its fluid neighbours (grouped by direction within a warp, so that the link
-// kernels read slots of one direction together) and adds its contact links
-// to exact integer sums
-constexpr int LB = 128;  // threads of a link-list block (8 blocks fit an SM)
+// contact sums of one cell (one block per cell, Eqs. deltapppp,
+// deltapppm): the rows of the cell's box, each cut to the outer interval of
+// its ellipsoid at its current position, flattened over the block; every
+// node the cell owns adds its links into another cell or a wall to exact
+// integer sums (the cell's bounce links come from the sweep's records)
+constexpr int LB = 128;  // threads of a contact block (8 blocks fit an SM)
 
-__global__ void __launch_bounds__(LB) k_cell_links(LatticeView lv, PartView pv) {
+__global__ void __launch_bounds__(LB) k_contacts(LatticeView lv, PartView pv) {
   using D = D3Q19;
-  const unsigned FULL = 0xffffffffu;
   __shared__ int sh_w[LB / 32 + 1];
   __shared__ int s_off[LB + 1], s_x0[LB], s_y[LB], s_z[LB];
-  __shared__ int s_len;
   __shared__ int s_ci[LB / 32][6];
   const int p = blockIdx.x;
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) s_len = 0;
   const int lo1 = pv.box[6 * p + 1], lo2 = pv.box[6 * p + 2];
   const int by = pv.box[6 * p + 4] - lo1 + 1, bz = pv.box[6 * p + 5] - lo2 + 1;
   const int rows = (by > 0 && bz > 0) ? by * bz : 0;
@@ -1350,8 +1496,6 @@ __global__ void __launch_bounds__(LB) k_cell_links(LatticeView lv, PartView pv) 
   const int imax = lv.per[0] ? imin + lv.nx - 1 : lv.nx - 1 - g.Xi[0];
   const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
   const int Xk[3] = {(int)k0.w, (int)k1.w, (int)k2.w};
-  unsigned long long *lk = pv.lk + (size_t)p * pv.lk_cap;
-  const unsigned below = (1u << lane) - 1u;
   const unsigned nx = (unsigned)lv.nx, nxy = (unsigned)lv.nx * (unsigned)lv.ny;
   int ci[6] = {0, 0, 0, 0, 0, 0};
   for (int r0 = 0; r0 < rows; r0 += LB) {
@@ -1377,62 +1521,31 @@ __global__ void __launch_bounds__(LB) k_cell_links(LatticeView lv, PartView pv) 
     s_y[threadIdx.x] = y;
     s_z[threadIdx.x] = z;
     __syncthreads();
-    for (int kb = 0; kb < tot; kb += LB) {
-      const int k = kb + threadIdx.x;
-      unsigned lmask = 0u, cmask = 0u;
-      int xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
-      if (k < tot) {
-        // the row holding flattened node k: the last row starting at or before k
-        int lo = 0, hi = LB - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (s_off[mid] <= k) lo = mid;
-          else hi = mid - 1;
-        }
-        int x = g.Xi[0] + s_x0[lo] + (k - s_off[lo]);
-        if (lv.per[0]) x = wrapi(x, lv.nx);
-        const int yy = s_y[lo], zz = s_z[lo];
-        xs[0] = x == 0 ? lv.nx - 1 : x - 1;
-        xs[1] = x;
-        xs[2] = x == lv.nx - 1 ? 0 : x + 1;
-        ys[0] = yy == 0 ? lv.ny - 1 : yy - 1;
-        ys[1] = yy;
-        ys[2] = yy == lv.ny - 1 ? 0 : yy + 1;
-        zs[0] = zz == 0 ? lv.nz - 1 : zz - 1;
-        zs[1] = zz;
-        zs[2] = zz == lv.nz - 1 ? 0 : zz + 1;
-        if (lv.owner[(unsigned)x + nx * (unsigned)yy + nxy * (unsigned)zz] == p) {
-          unsigned solid = 0, same = 0;
-          sfor<1, Q>([&](auto R) {
-            constexpr int r = decltype(R)::value;
-            const int on =
-                lv.owner[(unsigned)xs[1 + D::cx(r)] + nx * (unsigned)ys[1 + D::cy(r)] + nxy * (unsigned)zs[1 + D::cz(r)]];
-            solid |= (on != FLUID ? 1u : 0u) << r;
-            same |= (on == p ? 1u : 0u) << r;
-          });
-          lmask = NB_SOLID & ~solid;  // fluid neighbours
-          cmask = solid & ~same;      // other cells and walls
-        }
+    for (int k = threadIdx.x; k < tot; k += LB) {
+      // the row holding flattened node k: the last row starting at or before k
+      int lo = 0, hi = LB - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= k) lo = mid;
+        else hi = mid - 1;
       }
-      const int wtot = __reduce_add_sync(FULL, __popc(lmask));
-      if (wtot) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&s_len, wtot);
-        int run = __shfl_sync(FULL, base, 0);
-        sfor<1, Q>([&](auto R) {
-          constexpr int r = decltype(R)::value;
-          const bool has = (lmask >> r) & 1u;
-          const unsigned b = __ballot_sync(FULL, has);
-          if (has) {
-            const int pos = run + __popc(b & below);
-            if (pos < pv.lk_cap) lk[pos] = pack_xyzr(xs[1 + D::cx(r)], ys[1 + D::cy(r)], zs[1 + D::cz(r)], D::opp(r));
-          }
-          run += __popc(b);
-        });
-      }
+      int x = g.Xi[0] + s_x0[lo] + (k - s_off[lo]);
+      if (lv.per[0]) x = wrapi(x, lv.nx);
+      const int yy = s_y[lo], zz = s_z[lo];
+      if (lv.owner[(unsigned)x + nx * (unsigned)yy + nxy * (unsigned)zz] != p) continue;
+      const int xs[3] = {x == 0 ? lv.nx - 1 : x - 1, x, x == lv.nx - 1 ? 0 : x + 1};
+      const int ys[3] = {yy == 0 ? lv.ny - 1 : yy - 1, yy, yy == lv.ny - 1 ? 0 : yy + 1};
+      const int zs[3] = {zz == 0 ? lv.nz - 1 : zz - 1, zz, zz == lv.nz - 1 ? 0 : zz + 1};
+      unsigned cmask = 0;
+      sfor<1, Q>([&](auto R) {
+        constexpr int r = decltype(R)::value;
+        const int on =
+            lv.owner[(unsigned)xs[1 + D::cx(r)] + nx * (unsigned)ys[1 + D::cy(r)] + nxy * (unsigned)zs[1 + D::cz(r)]];
+        cmask |= (on != FLUID && on != p ? 1u : 0u) << r;  // another cell or a wall
+      });
       if (cmask) {
-        const int di[3] = {imin_image(xs[1] - Xk[0], lv.nx, lv.per[0]), imin_image(ys[1] - Xk[1], lv.ny, lv.per[1]),
-                           imin_image(zs[1] - Xk[2], lv.nz, lv.per[2])};
+        const int di[3] = {imin_image(x - Xk[0], lv.nx, lv.per[0]), imin_image(yy - Xk[1], lv.ny, lv.per[1]),
+                           imin_image(zz - Xk[2], lv.nz, lv.per[2])};
         sfor<1, Q>([&](auto R) {
           constexpr int r = decltype(R)::value;
           constexpr int m = D::m(r);
@@ -1450,14 +1563,11 @@ __global__ void __launch_bounds__(LB) k_cell_links(LatticeView lv, PartView pv) 
     __syncthreads();  // the row tables are rewritten by the next chunk
   }
   block_sum_i<6, LB>(ci, s_ci);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0)
     for (int k = 0; k < 3; ++k) {
       pv.cK[3 * p + k] = ci[k];
       pv.cIT[3 * p + k] = ci[3 + k];
     }
-    pv.lk_count[p] = s_len;
-    if (s_len > pv.lk_cap) atomicOr(pv.status, ST_OVERFLOW);
-  }
 }
 
 // owners >= 0 become resting fluid (first particles_set), layout of parity par
@@ -1607,30 +1717,29 @@ void launch_forces(const LatticeView &lv, const PartView &pv, const CellListView
   *nl += 1;
 }
 
-static unsigned link_chunks(const PartView &pv) { return (unsigned)((pv.lk_cap + CB - 1) / CB); }
-
-template <class S>
-static void sums_solve_typed(const LatticeView &lv, const PartView &pv, int par, cudaStream_t st) {
-  const dim3 grid_sum((unsigned)((pv.lk_cap + LCHUNK - 1) / LCHUNK), pv.n);
-  k_link_sums<S><<<grid_sum, LT, 0, st>>>(lv, pv, par);
-  k_solve<<<nblk(pv.n, 32), 32, 0, st>>>(lv, pv);
-}
-
 void launch_sums_solve(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st, int64_t *nl) {
+  (void)dtype;
+  (void)par;
   if (pv.n == 0) return;
-  if (dtype == 0) sums_solve_typed<float>(lv, pv, par, st);
-  else if (dtype == 1) sums_solve_typed<__nv_bfloat16>(lv, pv, par, st);
-  else sums_solve_typed<__half>(lv, pv, par, st);
+  k_link_reduce<<<pv.n, LT, 0, st>>>(lv, pv);
+  k_solve<<<nblk(pv.n, 32), 32, 0, st>>>(lv, pv);
   *nl += 2;
 }
 
-void launch_link_correct(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st,
+void launch_link_pending(int dtype, const LatticeView &lv, const PartView &pv, int par, cudaStream_t st,
                          int64_t *nl) {
   if (pv.n == 0) return;
-  const dim3 grid(link_chunks(pv), pv.n);
-  if (dtype == 0) k_link_correct<float><<<grid, CB, 0, st>>>(lv, pv, par);
-  else if (dtype == 1) k_link_correct<__nv_bfloat16><<<grid, CB, 0, st>>>(lv, pv, par);
-  else k_link_correct<__half><<<grid, CB, 0, st>>>(lv, pv, par);
+  if (dtype == 0) k_link_pending<float><<<pv.n, LT, 0, st>>>(lv, pv, par);
+  else if (dtype == 1) k_link_pending<__nv_bfloat16><<<pv.n, LT, 0, st>>>(lv, pv, par);
+  else k_link_pending<__half><<<pv.n, LT, 0, st>>>(lv, pv, par);
+  *nl += 1;
+}
+
+void launch_flush_pending(int dtype, const LatticeView &lv, int par, cudaStream_t st, int64_t *nl) {
+  const unsigned b = 256, g = nblk(lv.N, b) < 4u * 152u ? nblk(lv.N, b) : 4u * 152u;
+  if (dtype == 0) k_flush_pending<float><<<g, b, 0, st>>>(lv, par);
+  else if (dtype == 1) k_flush_pending<__nv_bfloat16><<<g, b, 0, st>>>(lv, par);
+  else k_flush_pending<__half><<<g, b, 0, st>>>(lv, par);
   *nl += 1;
 }
 
@@ -1670,9 +1779,9 @@ void launch_nbm_update(const LatticeView &lv, const PartView &pv, const ChangeLi
   *nl += 1;
 }
 
-void launch_cell_links(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl) {
+void launch_contacts(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  k_cell_links<<<pv.n, LB, 0, st>>>(lv, pv);
+  k_contacts<<<pv.n, LB, 0, st>>>(lv, pv);
   *nl += 1;
 }
 

@@ -40,3 +40,29 @@ def test_reference_sample_is_a_bounded_sub_box():
     # the cost model of the sample (12 s per 128^3 step with 1022 cells) fits the budget
     assert 12.0 * frac * frac * 20 <= 150.0 or (sp["nx"], sp["ny"]) == (16, 16)
     assert abs(len(sX) - len(X) * frac) <= 1
+
+
+def test_oracle_on_all_cores_aggregates_processes():
+    """the all-core CPU baseline: spawned processes, each stepping its own
+    copy, their site updates summed over the slowest one's time"""
+    from paper_1005_2594_gb300 import workloads
+
+    p, X, q = workloads.small_shear()
+    v, n, t = bench.oracle_all_cores(p, X, q, None, 0, 1, procs=2)
+    assert n == 2 and t > 0
+    assert abs(v - 2 * 32 ** 3 / t / 1e6) < 1e-9
+    assert 1 <= bench.host_cores(32 ** 3) <= (os.cpu_count() or 1)
+
+
+def test_sweep_kernel_label_follows_the_default_variant():
+    assert "k_lb_step_bulk" in bench.sweep_kernel(128, 0) and "FP32" in bench.sweep_kernel(128, 0)
+    assert "k_lb_step_bulk" in bench.sweep_kernel(256, 1) and "BF16" in bench.sweep_kernel(256, 1)
+    assert "k_lb_step_pipe" in bench.sweep_kernel(30, 0)
+    assert bench.sweep_kernel(36, 2).startswith("k_lb_step ") and "FP16" in bench.sweep_kernel(36, 2)
+
+
+def test_clock_sampler_reports_without_a_gpu():
+    c = bench.ClockSampler(0)
+    c.start()
+    out = c.stop()
+    assert "samples" in out and "reasons" in out

@@ -233,15 +233,29 @@ def make_workload(name):
 SWEEP_TRAFFIC = {"sha": "ad506e7e2729c60d", "config": "shear128", "store": 0, "bytes": 271938944}
 
 
-def sweep_kernel(nx, store):
-    """the sweep kernel the library runs by default for this row length and
-    storage type (the bulk-copy pipeline needs 16-byte aligned rows)"""
+SWEEP_KERNELS = {
+    0: "k_lb_step (fused collide/stream/bounce-back, one node per thread, %s store)",
+    1: "k_lb_step_pipe (fused collide/stream/bounce-back, per-thread copy pipeline over 4 planes, %s store)",
+    2: "k_lb_step_pipe (fused collide/stream/bounce-back, per-thread copy pipeline over 8 planes, %s store)",
+    3: "k_lb_step_bulk (fused collide/stream/bounce-back, bulk-copy pipeline over 8 planes, %s store)",
+    4: "k_lb_step_bulk (fused collide/stream/bounce-back, bulk-copy pipeline over 4 planes, %s store)",
+    5: "k_lb_step_rows (fused collide/stream/bounce-back, persistent bulk-copy row pipeline, %s store)",
+}
+
+
+def sweep_kernel(nx, store, variant=None, cells=True):
+    """the sweep kernel the library runs for this row length, storage type
+    and variant (None: the context's own choice, one node per thread with
+    cells, else the bulk-copy pipeline where rows are 16-byte aligned); the
+    bulk-copy variants need 16-byte aligned rows and the per-thread pipeline
+    FP32, else the library runs one node per thread"""
     name = {0: "FP32", 1: "BF16", 2: "FP16"}[store]
-    if nx % (4 if store == 0 else 8) == 0:
-        return "k_lb_step_bulk (fused collide/stream/bounce-back, bulk-copy pipeline over 8 planes, %s store)" % name
-    if store == 0:
-        return "k_lb_step_pipe (fused collide/stream/bounce-back, per-thread copy pipeline, FP32 store)"
-    return "k_lb_step (fused collide/stream/bounce-back, one node per thread, %s store)" % name
+    aligned = nx % (4 if store == 0 else 8) == 0
+    if variant is None:
+        variant = 0 if cells else (3 if aligned else (1 if store == 0 else 0))
+    if (variant in (3, 4, 5) and not aligned) or (variant in (1, 2) and store != 0):
+        variant = 0
+    return SWEEP_KERNELS[variant] % name
 
 
 def sweep_traffic(config, store):
@@ -282,6 +296,8 @@ def run_gpu(args, ws, rank, local):
     N = p["nx"] * p["ny"] * p["nz"]
     dsize = {0: 4, 1: 2, 2: 2}[args.store]
     sim = bl.Simulation(p, store_dtype=args.store, stream=stream.cuda_stream, wall_mask=mask)
+    if args.sweep is not None:
+        sim.sweep_variant(args.sweep)
     sim.set_particles(X, q)
     sim.step(args.warmup)
     sim.sync()
@@ -338,7 +354,7 @@ def run_gpu(args, ws, rank, local):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
                      "traffic": sweep_traffic(args.config, args.store), "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
-                     else "fallback 6.8 TB/s", "kernel": sweep_kernel(p["nx"], args.store),
+                     else "fallback 6.8 TB/s", "kernel": sweep_kernel(p["nx"], args.store, args.sweep),
                      "bytes_per_launch": bytes_per, "launch_ms": round(k1_ms / max(k1_n, 1), 5),
                      # the coupled step as a whole: the same algorithmic bytes (the
                      # link, contact, potential and fill/drain work adds none when
@@ -787,6 +803,8 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--config", default="shear128", choices=["shear128", "small32", "duct256", "ensemble64", "tube512", "tube_rheology"])
     ap.add_argument("--store", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--sweep", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
+                    help="sweep variant (default: the library's choice for the row length and storage)")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision-steps", type=int, default=1000,

@@ -213,13 +213,18 @@ int bl_cell_list_build_static(const double *X, int n, const int32_t dims[3], dou
    pipeline that walks 4 or 8 z planes per thread block and copies the next
    node's populations into shared memory while the current one is collided;
    3, 4 (any storage) a pipeline over 8 or 4 z planes whose row segments are
-   fetched by bulk asynchronous copies (TMA) two planes ahead, for rows of a
-   multiple of 16 bytes (nx a multiple of 4 in FP32, of 8 in BF16 / FP16;
-   otherwise they run as variant 0).  Contexts start with 3 where the rows
-   allow it, else FP32 with 1 and 16-bit storage with 0.  bl_sweep_variant
-   sets one (BL_EINVAL for an unknown variant, or variant 1 or 2 with 16-bit
-   storage).  A bounded wait for the bulk
-   copies that gives up makes the next bl_sync return BL_EBARRIER.
+   fetched by bulk asynchronous copies (TMA) two planes ahead; 5 (any
+   storage) a persistent grid of as many blocks as the device holds, each
+   walking its share of the rows through one bulk-copy pipeline.  3 to 5
+   need rows of a multiple of 16 bytes (nx a multiple of 4 in FP32, of 8 in
+   BF16 / FP16; otherwise they run as variant 0).  A context that was given
+   no variant chooses: with cells, 0 (the boundary work of a suspension
+   falls unevenly on the warps, and the block-wide barriers of 1 to 5 make
+   every warp wait for the slowest); without cells, 3 where the rows allow
+   it, else FP32 with 1 and 16-bit storage with 0.  bl_sweep_variant sets
+   one and keeps it (BL_EINVAL for an unknown variant, or variant 1 or 2
+   with 16-bit storage).  A bounded wait for the bulk copies that gives up
+   makes the next bl_sync return BL_EBARRIER.
    bl_autotune times every variant the storage type allows over trial_steps
    steps (>= 2; the context advances by those steps, so call it before the
    steps that count), keeps the fastest and writes its number to *choice

@@ -72,7 +72,9 @@ struct LatticeView {
   float rho0;
   float g[3];
   int has_force;
-  int sweep;  // sweep variant (0 one node per thread, 1 / 2 FP32 pipeline over 4 / 8 planes)
+  int sweep;  // sweep variant (0 one node per thread, 1 / 2 FP32 pipeline over 4 / 8 planes,
+             // 3 / 4 bulk-copy pipeline over 8 / 4 planes, 5 persistent bulk-copy rows)
+  int rows_grid[8];  // grid of the persistent row sweep per (parity, force, tau = 1)
   void *pop;       // 19 x N storage elements, slot r of node n at r * N + n
   int32_t *owner;  // N
   uint32_t *nbm;   // N neighbour words of the current owner map (NB_* bits), written by the geometry pass
@@ -92,11 +94,14 @@ struct LatticeView {
   int *status;
 };
 
-// A link record: node n (bits of .x), direction mask (bits of .y: bit r =
-// the neighbour n + c_r belongs to the cell; bit 31 marks the links of a
-// node's second or third cell, whose C is given in place right after the
-// solve), density rho (.z) and sum over the mask of 2 f~*_r c_r (.w, then
-// .x, .y of the second float4).
+// A link record (two float4): node n (bits of .x), direction mask (bits of
+// .y: bit r = the neighbour n + c_r belongs to the cell; bit 31 marks the
+// links of a node's second or third cell, whose C is given in place right
+// after the solve), the density deviation drho = rho - rho_bar (.z), then
+// at tau = 1 the node's velocity u (.w, second .x, .y), uu (second .z) and
+// u . F (second .w), from which the link sums rebuild the bounced
+// populations; at any other tau the sum over the mask of 2 f~*_r c_r (.w,
+// second .x, .y).
 constexpr uint32_t REC_DIRECT = 1u << 31;
 
 // neighbour word of a node: bit 0 the node is fluid; bit r (1..18) the
@@ -185,6 +190,8 @@ struct ChangeList {
 // launchers (each adds the number of kernels it launched to *nl where given)
 
 void launch_lb_step(int dtype, const LatticeView &lv, int par, const WallAcc &wa, int *status, cudaStream_t st);
+// the persistent row sweep's grid per instantiation (LatticeView::rows_grid)
+void lb_rows_grids(int dtype, int out[8]);
 void launch_fields(int dtype, const LatticeView &lv, int par, double *rho, double *u, int32_t *owner,
                    cudaStream_t st);
 void launch_pop_io(int dtype, const LatticeView &lv, int par, double *buf, int to_storage, cudaStream_t st);
@@ -290,6 +297,62 @@ __device__ __forceinline__ void unpack_xyzr(unsigned long long e, int xyz[3], in
   xyz[0] = (int)((e >> 5) & 0xFFFFFull);
   xyz[1] = (int)((e >> 25) & 0xFFFFFull);
   xyz[2] = (int)(e >> 45);
+}
+
+// direction masks of the lattice (bit r), for the record sums by popcount
+template <class P>
+__host__ __device__ constexpr uint32_t dir_mask(P pred) {
+  uint32_t m = 0;
+  for (int r = 1; r < Q; ++r)
+    if (pred(r)) m |= 1u << r;
+  return m;
+}
+using D3 = D3Q19;
+constexpr int cxyz(int r, int a) { return a == 0 ? D3::cx(r) : (a == 1 ? D3::cy(r) : D3::cz(r)); }
+template <int A, int SGN>
+struct AxisDirs {  // axis vectors along A with sign SGN (m = 2)
+  static constexpr uint32_t v = dir_mask([](int r) { return r <= 6 && cxyz(r, A) == SGN; });
+};
+template <int A, int SGN>
+struct DiagDirs {  // diagonal vectors with c_A = SGN (m = 1)
+  static constexpr uint32_t v = dir_mask([](int r) { return r > 6 && cxyz(r, A) == SGN; });
+};
+template <int A, int B, int SGN>
+struct PairDirs {  // diagonal vectors with c_A c_B = SGN
+  static constexpr uint32_t v = dir_mask([](int r) { return r > 6 && cxyz(r, A) * cxyz(r, B) == SGN; });
+};
+
+__device__ __forceinline__ int popm(uint32_t m, uint32_t sel) { return __popc(m & sel); }
+
+// sums over the directions of a mask (bit r) by popcount: component A of
+// K = sum m_r c_r, and the entries A A and A B of M = sum m_r c_r c_r^T
+template <int A>
+__device__ __forceinline__ int mask_K(uint32_t m) {
+  return 2 * (popm(m, AxisDirs<A, 1>::v) - popm(m, AxisDirs<A, -1>::v)) + popm(m, DiagDirs<A, 1>::v) -
+         popm(m, DiagDirs<A, -1>::v);
+}
+template <int A>
+__device__ __forceinline__ int mask_Maa(uint32_t m) {
+  return 2 * popm(m, AxisDirs<A, 1>::v | AxisDirs<A, -1>::v) + popm(m, DiagDirs<A, 1>::v | DiagDirs<A, -1>::v);
+}
+template <int A, int B>
+__device__ __forceinline__ int mask_Mab(uint32_t m) {
+  return popm(m, PairDirs<A, B, 1>::v) - popm(m, PairDirs<A, B, -1>::v);
+}
+
+// post-collision shifted population at tau = 1: the third-order equilibrium
+// w (drho + rho t), t = 4.5 cu^2 - 1.5 uu + cu (3 - 4.5 uu + 4.5 cu^2), with
+// rho t taken as rho_bar t + drho t (exact for small drho in FP32), plus the
+// Guo source src_w w (3 (cF - uF) + 9 cu cF) when a force acts; the sweep and
+// the link sums evaluate this same function, so the bounced populations the
+// fluid keeps and those the cell's momentum counts agree
+__device__ __forceinline__ float post_tau1(float w, float drho, float rho0, float cu, float uu, bool force, float cF,
+                                           float uF, float src_w) {
+  const float q = 4.5f * cu * cu;
+  const float t = (q - 1.5f * uu) + cu * ((3.0f - 4.5f * uu) + q);
+  float fs = w * (drho + fmaf(drho, t, rho0 * t));
+  if (force) fs += src_w * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
+  return fs;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -82,6 +82,7 @@ struct bl_ctx {
   size_t scratch_bytes;
   // timing
   int timing;
+  int sweep_fixed;  // the sweep variant was set (bl_sweep_variant, bl_autotune), not chosen here
   std::vector<cudaEvent_t> ev;  // pairs
   std::vector<int> ev_group;
   int ev_used;
@@ -117,6 +118,18 @@ static int check_launch(bl_ctx *c, const char *what) {
 }
 
 static size_t elem_size(int dtype) { return dtype == BL_STORE_F32 ? 4 : 2; }
+
+// the sweep variant of a context that was given none.  With cells, one node
+// per thread: the boundary work of a suspension falls unevenly on the warps,
+// and hiding its latency by occupancy beats a block-wide copy pipeline whose
+// barriers make every warp wait for the slowest.  Without cells, the
+// bulk-copy pipeline over 8 planes where rows are 16-byte aligned, else the
+// FP32 per-thread copy pipeline or one node per thread.
+static int auto_sweep(const bl_ctx *c) {
+  if (c->np > 0) return 0;
+  if (c->lv.nx % (c->dtype == BL_STORE_F32 ? 4 : 8) == 0) return 3;
+  return c->dtype == BL_STORE_F32 ? 1 : 0;
+}
 
 static int ensure_scratch(bl_ctx *c, size_t bytes) {
   if (c->scratch_bytes >= bytes) return BL_OK;
@@ -237,11 +250,13 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
   lv.omega = (float)(1.0 / p->tau);
   lv.rho0 = (float)p->rho0;
   lv.has_force = 0;
-  // the bulk-copy pipeline over 8 planes where rows are 16-byte aligned (nx a
-  // multiple of 4 in FP32, of 8 in BF16 / FP16); else FP32 takes the pipeline
-  // over 4 planes and 16-bit storage one node per thread
+  // (no cells yet: the bulk-copy pipeline over 8 planes where rows are
+  // 16-byte aligned, nx a multiple of 4 in FP32, of 8 in BF16 / FP16; else
+  // FP32 takes the pipeline over 4 planes and 16-bit storage one node per
+  // thread; auto_sweep changes it when cells come)
   if (p->store_dtype == BL_STORE_F32) lv.sweep = p->nx % 4 == 0 ? 3 : 1;
   else lv.sweep = p->nx % 8 == 0 ? 3 : 0;
+  bl::lb_rows_grids(p->store_dtype, lv.rows_grid);
   for (int k = 0; k < 3; ++k) {
     lv.g[k] = (float)p->g[k];
     if (p->g[k] != 0.0) lv.has_force = 1;
@@ -494,6 +509,7 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
     CU(cudaStreamSynchronize(c->stream));
     free_particles(c);
     c->pp = *pp;
+    if (!c->sweep_fixed) c->lv.sweep = auto_sweep(c);
     if (n == 0) {
       launch_geometry(c->lv, c->pv, c->stream, &c->launches);
       if (check_launch(c, "geometry")) return c->sticky;
@@ -501,6 +517,7 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
       return BL_OK;
     }
     if (alloc_particles(c, n)) return c->sticky;
+    if (!c->sweep_fixed) c->lv.sweep = auto_sweep(c);
     if (c->mlp && alloc_pairbuf(c)) return c->sticky;
   } else {
     c->pp = *pp;
@@ -974,7 +991,7 @@ extern "C" int bl_autotune(bl_ctx *c, int trial_steps, int *choice) {
   if (c->sticky) return c->sticky;
   if (c->timing) return fail(c, BL_ESTATE, "bl_autotune with timing enabled");
   // candidate variants the storage type and the row length allow
-  int cand[5], nvar = 0;
+  int cand[6], nvar = 0;
   cand[nvar++] = 0;
   if (c->dtype == BL_STORE_F32) {
     cand[nvar++] = 1;
@@ -983,6 +1000,7 @@ extern "C" int bl_autotune(bl_ctx *c, int trial_steps, int *choice) {
   if (c->lv.nx % (c->dtype == BL_STORE_F32 ? 4 : 8) == 0) {
     cand[nvar++] = 3;
     cand[nvar++] = 4;
+    cand[nvar++] = 5;
   }
   int best = 0;
   float best_ms = 0.f;
@@ -1013,17 +1031,19 @@ extern "C" int bl_autotune(bl_ctx *c, int trial_steps, int *choice) {
   cudaEventDestroy(b);
   drop_graph(c);
   c->lv.sweep = best;
+  c->sweep_fixed = 1;
   if (choice) *choice = best;
   if (rc != BL_OK) return rc;
   return read_status(c);
 }
 
 extern "C" int bl_sweep_variant(bl_ctx *c, int variant) {
-  if (!c || variant < 0 || variant > 4) return BL_EINVAL;
+  if (!c || variant < 0 || variant > 5) return BL_EINVAL;
   if (c->sticky) return c->sticky;
   if ((variant == 1 || variant == 2) && c->dtype != BL_STORE_F32) return BL_EINVAL;
   drop_graph(c);
   c->lv.sweep = variant;
+  c->sweep_fixed = 1;
   return BL_OK;
 }
 

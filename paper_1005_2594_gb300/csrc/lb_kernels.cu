@@ -299,6 +299,16 @@ void launch_lb_step_f32(const LatticeView &lv, int par, const WallAcc &wa, cudaS
 void launch_lb_step_bf16(const LatticeView &lv, int par, const WallAcc &wa, cudaStream_t st);
 void launch_lb_step_f16(const LatticeView &lv, int par, const WallAcc &wa, cudaStream_t st);
 
+void lb_rows_grids_f32(int out[8]);
+void lb_rows_grids_bf16(int out[8]);
+void lb_rows_grids_f16(int out[8]);
+
+void lb_rows_grids(int dtype, int out[8]) {
+  if (dtype == 0) lb_rows_grids_f32(out);
+  else if (dtype == 1) lb_rows_grids_bf16(out);
+  else lb_rows_grids_f16(out);
+}
+
 void launch_lb_step(int dtype, const LatticeView &lv0, int par, const WallAcc &wa, int *status, cudaStream_t st) {
   LatticeView lv = lv0;
   lv.status = status;

@@ -22,13 +22,16 @@
 // Cells.  A population that meets a cell node is bounced here without the
 // moving-boundary term: the cell's velocity of the half step is not known
 // yet (reading Q3, implicit coupling).  The node writes one link record per
-// cell it borders (its direction mask, its density and the sum of 2 f~*_r c_r
-// over those links) into the cell's bucket, from which the link kernel sums
-// the cell's link momentum and drag matrices.  After the solve each node's
-// record of its first cell becomes its pending velocity pu = rho (V + W x d)
-// with the bounced directions; the next sweep reads pu with the
-// populations and adds C = -(m_r / 6) c_r . pu (Eq. c, at the link midpoint;
-// c_r . (W x c_r / 2) = 0) to those populations before the moments.
+// cell it borders (its direction mask, its density and, at tau = 1, its
+// velocity moments, else the sum of 2 f~*_r c_r over those links) into the
+// cell's bucket, from which the link kernel sums the cell's link momentum
+// and drag matrices.  After the solve each node's record of its first cell
+// becomes its pending velocity pu = rho (V + W x d) with the bounced
+// directions; the next sweep reads pu with the populations and adds
+// C = -(m_r / 6) c_r . pu (Eq. c, at the link midpoint; c_r . (W x c_r / 2)
+// = 0) to those populations before the moments.  At tau = 1 the collision
+// keeps only the moments of what it reads, so C enters as the change of
+// rho and j it makes, summed over the bounced directions by popcount.
 // Walls move at a known velocity: their links get C here, and the wall's
 // momentum is summed per warp (constant part 2 alpha_r rho_bar c_r as exact
 // integers) before one atomic per wall and component.
@@ -87,11 +90,14 @@ __device__ __forceinline__ unsigned src_slot(int r, unsigned N, unsigned n, cons
 }
 
 // the primary link record a node hands to the warp-level append (cell p < 0:
-// no cell link)
+// no cell link): its direction mask and the six values of the record, the
+// density deviation drho and, at tau = 1, the node's u, uu and u . F, from
+// which the link sums rebuild the bounced populations, else the sum of
+// 2 f~*_r c_r over the mask (two zeros after it)
 struct CellLink {
   int p;
   uint32_t mask;
-  float rho, F[3];
+  float e[6];
 };
 
 // warp-level append of the lanes' primary link records to their cells'
@@ -119,8 +125,8 @@ __device__ __forceinline__ void write_links(const LatticeView &lv, const CellLin
   const int pos = base + __popc(sl.grp & ((1u << lane) - 1u));
   if (pos < lv.rec_cap) {
     float4 *r = lv.rec + 2 * ((size_t)cl.p * lv.rec_cap + pos);
-    r[0] = make_float4(__uint_as_float(n), __uint_as_float(cl.mask), cl.rho, cl.F[0]);
-    r[1] = make_float4(cl.F[1], cl.F[2], 0.f, 0.f);
+    r[0] = make_float4(__uint_as_float(n), __uint_as_float(cl.mask), cl.e[0], cl.e[1]);
+    r[1] = make_float4(cl.e[2], cl.e[3], cl.e[4], cl.e[5]);
   } else {
     atomicOr(lv.status, ST_OVERFLOW);
   }
@@ -151,32 +157,44 @@ __device__ __forceinline__ unsigned neighbour_rt(int r, const unsigned xo[3], co
 // the pending C of the last step's bounces off a cell: pu.xyz = rho (V + W x
 // d) of the cell at the node, pu.w the bounced directions (bit r); C_r =
 // -(m_r / 6) c_r . pu is added to the incoming population of direction rbar
+// (every direction computed, the masked ones kept: no branch per direction)
 __device__ __forceinline__ void apply_pending(const float4 &pu, float (&f)[Q]) {
   using D = D3Q19;
   const uint32_t mask = __float_as_uint(pu.w);
   sfor<1, Q>([&](auto R) {
     constexpr int r = decltype(R)::value;
-    if (mask & (1u << r)) {
-      float cu = 0.f;
-      if constexpr (D::cx(r) != 0) cu += D::cx(r) * pu.x;
-      if constexpr (D::cy(r) != 0) cu += D::cy(r) * pu.y;
-      if constexpr (D::cz(r) != 0) cu += D::cz(r) * pu.z;
-      f[D::opp(r)] -= (D::m(r) / 6.0f) * cu;
-    }
+    float cu = 0.f;
+    if constexpr (D::cx(r) != 0) cu += D::cx(r) * pu.x;
+    if constexpr (D::cy(r) != 0) cu += D::cy(r) * pu.y;
+    if constexpr (D::cz(r) != 0) cu += D::cz(r) * pu.z;
+    f[D::opp(r)] -= ((mask >> r) & 1u) ? (D::m(r) / 6.0f) * cu : 0.0f;
   });
 }
 
-// sum of 2 f~*_r c_r over the directions in mask
+// the same C taken into the moments alone (enough at tau = 1, where the
+// collision keeps nothing of a population but its moments):
+// drho -= K . pu / 6, j += M pu / 6, K = sum m_r c_r, M = sum m_r c_r c_r^T
+// over the bounced directions
+__device__ __forceinline__ void pending_moments(const float4 &pu, float &drho, float &jx, float &jy, float &jz) {
+  const uint32_t m = __float_as_uint(pu.w);
+  const float s = 1.0f / 6.0f;
+  drho -= s * ((float)mask_K<0>(m) * pu.x + (float)mask_K<1>(m) * pu.y + (float)mask_K<2>(m) * pu.z);
+  const float mxy = (float)mask_Mab<0, 1>(m), mxz = (float)mask_Mab<0, 2>(m), myz = (float)mask_Mab<1, 2>(m);
+  jx += s * ((float)mask_Maa<0>(m) * pu.x + mxy * pu.y + mxz * pu.z);
+  jy += s * (mxy * pu.x + (float)mask_Maa<1>(m) * pu.y + myz * pu.z);
+  jz += s * (mxz * pu.x + myz * pu.y + (float)mask_Maa<2>(m) * pu.z);
+}
+
+// sum of 2 f~*_r c_r over the directions in mask (no branch per direction)
 __device__ __forceinline__ void link_sum(uint32_t mask, const float (&f)[Q], float (&F)[3]) {
   using D = D3Q19;
   float F0 = 0.f, F1 = 0.f, F2 = 0.f;
   sfor<1, Q>([&](auto R) {
     constexpr int r = decltype(R)::value;
-    if (mask & (1u << r)) {
-      if constexpr (D::cx(r) != 0) F0 += 2.0f * D::cx(r) * f[r];
-      if constexpr (D::cy(r) != 0) F1 += 2.0f * D::cy(r) * f[r];
-      if constexpr (D::cz(r) != 0) F2 += 2.0f * D::cz(r) * f[r];
-    }
+    const float v = ((mask >> r) & 1u) ? 2.0f * f[r] : 0.0f;
+    if constexpr (D::cx(r) != 0) F0 += D::cx(r) * v;
+    if constexpr (D::cy(r) != 0) F1 += D::cy(r) * v;
+    if constexpr (D::cz(r) != 0) F2 += D::cz(r) * v;
   });
   F[0] = F0;
   F[1] = F1;
@@ -184,13 +202,13 @@ __device__ __forceinline__ void link_sum(uint32_t mask, const float (&f)[Q], flo
 }
 
 // one record appended to cell q's bucket by this thread alone
-__device__ __forceinline__ void append_link(const LatticeView &lv, unsigned n, int q, uint32_t mask, float rho,
-                                            float F0, float F1, float F2) {
+__device__ __forceinline__ void append_link(const LatticeView &lv, unsigned n, int q, uint32_t mask,
+                                            const float (&e)[6]) {
   const int pos = atomicAdd(&lv.rec_count[q], 1);
   if (pos < lv.rec_cap) {
     float4 *rr = lv.rec + 2 * ((size_t)q * lv.rec_cap + pos);
-    rr[0] = make_float4(__uint_as_float(n), __uint_as_float(mask), rho, F0);
-    rr[1] = make_float4(F1, F2, 0.f, 0.f);
+    rr[0] = make_float4(__uint_as_float(n), __uint_as_float(mask), e[0], e[1]);
+    rr[1] = make_float4(e[2], e[3], e[4], e[5]);
   } else {
     atomicOr(lv.status, ST_OVERFLOW);
   }
@@ -225,9 +243,12 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
       }
       f[r] = load(r, src);
     });
-    // C of the last step's bounces off a cell (reading Q3)
+    // C of the last step's bounces off a cell (reading Q3): into the
+    // populations, or at tau = 1 into the moments
     const uint32_t pm = __float_as_uint(pu.w);
-    if (pm) apply_pending(pu, f);
+    if constexpr (!TAU1) {
+      if (pm) apply_pending(pu, f);
+    }
     // moments (shifted: rho = rho_bar + sum f~, j = sum f~ c)
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
     sfor<0, Q>([&](auto R) {
@@ -237,6 +258,9 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
       if constexpr (D::cy(r) != 0) jy += D::cy(r) * f[r];
       if constexpr (D::cz(r) != 0) jz += D::cz(r) * f[r];
     });
+    if constexpr (TAU1) {
+      if (pm) pending_moments(pu, drho, jx, jy, jz);
+    }
     const float rho = lv.rho0 + drho;
     const float inv = 1.0f / rho;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
@@ -340,26 +364,52 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
           }
         });
       }
-      // cell links: the record of the first cell (sum of 2 f~*_r c_r over its
-      // directions) through the warp-level append; those of a second and a
-      // third cell, rarer, directly, marked for C in place after the solve
+      // cell links: the record of the first cell through the warp-level
+      // append; those of a second and a third cell, rarer, directly, marked
+      // for C in place after the solve.  At tau = 1 a record holds the
+      // node's moments (the same for every cell of the node), else the sum
+      // of 2 f~*_r c_r over its directions
       if (cmask) {
         cl.p = p1;
         cl.mask = cmask;
-        cl.rho = rho;
-        link_sum(cmask, f, cl.F);
+        cl.e[0] = drho;
+        if constexpr (TAU1) {
+          cl.e[1] = ux;
+          cl.e[2] = uy;
+          cl.e[3] = uz;
+          cl.e[4] = uu;
+          cl.e[5] = uF;
+        } else {
+          float F[3];
+          link_sum(cmask, f, F);
+          cl.e[1] = F[0];
+          cl.e[2] = F[1];
+          cl.e[3] = F[2];
+          cl.e[4] = cl.e[5] = 0.f;
+        }
         if (cmask2) {
-          float F2[3];
-          link_sum(cmask2, f, F2);
-          append_link(lv, n, p2, cmask2 | REC_DIRECT, rho, F2[0], F2[1], F2[2]);
+          float e[6] = {drho, cl.e[1], cl.e[2], cl.e[3], cl.e[4], cl.e[5]};
+          if constexpr (!TAU1) {
+            float F[3];
+            link_sum(cmask2, f, F);
+            e[1] = F[0];
+            e[2] = F[1];
+            e[3] = F[2];
+          }
+          append_link(lv, n, p2, cmask2 | REC_DIRECT, e);
         }
         if (csec) {
           sfor<1, Q>([&](auto R) {
             constexpr int r = decltype(R)::value;
             if (csec & (1u << r)) {
               const unsigned nb = xo[1 + D::cx(r)] + yo[1 + D::cy(r)] + zo[1 + D::cz(r)];
-              append_link(lv, n, lv.owner[nb], (1u << r) | REC_DIRECT, rho, 2.0f * D::cx(r) * f[r],
-                          2.0f * D::cy(r) * f[r], 2.0f * D::cz(r) * f[r]);
+              float e[6] = {drho, cl.e[1], cl.e[2], cl.e[3], cl.e[4], cl.e[5]};
+              if constexpr (!TAU1) {
+                e[1] = 2.0f * D::cx(r) * f[r];
+                e[2] = 2.0f * D::cy(r) * f[r];
+                e[3] = 2.0f * D::cz(r) * f[r];
+              }
+              append_link(lv, n, lv.owner[nb], (1u << r) | REC_DIRECT, e);
             }
           });
         }
@@ -663,12 +713,200 @@ static void launch_bulk(const LatticeView &lv, dim3 grid, const WallAcc &wa, cud
   k_lb_step_bulk<S, PAR, FORCE, TAU1, ZC, TS><<<gp, 128, 0, st>>>(lv, wa);
 }
 
+// The persistent row sweep: a grid of as many blocks as the device holds at
+// once, block b taking the rows (segment, y, z) numbered b, b + G, b + 2G,
+// ... (G blocks, segments of 128 nodes fastest) in one bulk-copy pipeline
+// TS - 1 rows ahead, so that no tail wave and no pipeline restart remain.
+// The link records of a row wait in shared memory until the next row is
+// collided, by when the bucket atomic that gave them their slots has
+// returned; one barrier per row frees its stage.  Row and wait rules as in
+// k_lb_step_bulk.
+#ifndef BL_ROWS_MINB
+#define BL_ROWS_MINB 5
+#endif
+#ifndef BL_ROWS_TS
+#define BL_ROWS_TS 3
+#endif
+
+struct RowGeo {
+  int x0, W, y, z;
+};
+
+// the staged record of this lane, written to the slot reserved one row before
+__device__ __forceinline__ void write_staged(const LatticeView &lv, int p, unsigned grp, int base0, const float4 &r0,
+                                             const float4 &r1) {
+  if (p < 0) return;
+  const int lane = threadIdx.x & 31;
+  const int base = __shfl_sync(grp, base0, __ffs(grp) - 1);
+  const int pos = base + __popc(grp & ((1u << lane) - 1u));
+  if (pos < lv.rec_cap) {
+    float4 *r = lv.rec + 2 * ((size_t)p * lv.rec_cap + pos);
+    r[0] = r0;
+    r[1] = r1;
+  } else {
+    atomicOr(lv.status, ST_OVERFLOW);
+  }
+}
+
+template <class S, int PAR, bool FORCE, bool TAU1, int TS>
+__global__ void __launch_bounds__(128, BL_ROWS_MINB) k_lb_step_rows(LatticeView lv, WallAcc wa) {
+  using D = D3Q19;
+  __shared__ alignas(128) S sb[TS][Q][128];      // [stage][array][x]
+  __shared__ alignas(128) uint32_t sw[TS][128];  // [stage][x] neighbour words
+  __shared__ alignas(128) float4 spu[TS][128];   // [stage][x] pending velocities
+  __shared__ alignas(128) uint32_t sc[TS][128];  // [stage][x] neighbour-cell words
+  __shared__ alignas(128) float4 srec[2][128];   // the last row's link record of each thread
+  __shared__ alignas(8) unsigned long long bar[TS];
+  const int nx = lv.nx, ny = lv.ny, nz = lv.nz;
+  const int tx = threadIdx.x;
+  const int nseg = (nx + 127) >> 7;
+  const int nitems = nseg * ny * nz;
+  const int G = gridDim.x;
+  const int kmax = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;
+  const unsigned N = lv.N;
+  const unsigned nxy = (unsigned)nx * (unsigned)ny;
+  const S *pop = reinterpret_cast<const S *>(lv.pop);
+  auto geo = [&](int k) {
+    const int it = (int)blockIdx.x + k * G;
+    const int seg = it % nseg, t = it / nseg;
+    RowGeo g;
+    g.x0 = seg << 7;
+    g.W = min(128, nx - g.x0);
+    g.y = t % ny;
+    g.z = t / ny;
+    return g;
+  };
+  auto yzo = [&](const RowGeo &g, unsigned yo[3], unsigned zo[3]) {
+    yo[0] = (unsigned)(g.y == 0 ? ny - 1 : g.y - 1) * nx;
+    yo[1] = (unsigned)g.y * nx;
+    yo[2] = (unsigned)(g.y == ny - 1 ? 0 : g.y + 1) * nx;
+    zo[0] = (unsigned)(g.z == 0 ? nz - 1 : g.z - 1) * nxy;
+    zo[1] = (unsigned)g.z * nxy;
+    zo[2] = (unsigned)(g.z == nz - 1 ? 0 : g.z + 1) * nxy;
+  };
+  // one thread: the copies of row k into stage s
+  auto issue = [&](int k, int s) {
+    const RowGeo g = geo(k);
+    unsigned yo[3], zo[3];
+    yzo(g, yo, zo);
+    const unsigned bytes = (unsigned)g.W * (unsigned)sizeof(S);
+    mbar_expect_tx(&bar[s], Q * bytes + (unsigned)g.W * 24u);
+    sfor<0, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      unsigned row;
+      if constexpr (PAR == 0 || r == 0) row = (unsigned)r * N + yo[1] + zo[1];
+      else row = (unsigned)D::opp(r) * N + yo[1 - D::cy(r)] + zo[1 - D::cz(r)];
+      bulk_g2s(&sb[s][r][0], pop + row + (unsigned)g.x0, bytes, &bar[s]);
+    });
+    const unsigned o = yo[1] + zo[1] + (unsigned)g.x0;
+    bulk_g2s(&sw[s][0], lv.nbm + o, (unsigned)g.W * 4u, &bar[s]);
+    bulk_g2s(&spu[s][0], lv.pu + o, (unsigned)g.W * 16u, &bar[s]);
+    bulk_g2s(&sc[s][0], lv.nbc + o, (unsigned)g.W * 4u, &bar[s]);
+  };
+  if (tx == 0) {
+    for (int k = 0; k < TS; ++k) mbar_init(&bar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (tx == 0)
+    for (int k = 0; k < TS - 1 && k < kmax; ++k) issue(k, k);
+  int wkey = -1;
+  float wF[3] = {0.f, 0.f, 0.f};
+  int wK[3] = {0, 0, 0};
+  // the slot of this thread's record of the last row: cell, lane group, base
+  int lp = -1;
+  unsigned lgrp = 0u;
+  int lbase = 0;
+  bool failed = false;
+  for (int k = 0; k < kmax; ++k) {
+    const int s = k % TS;
+    if (tx == 0 && k + TS - 1 < kmax) issue(k + TS - 1, (k + TS - 1) % TS);  // freed by the last barrier
+    const bool ok = mbar_wait(&bar[s], (unsigned)(k / TS) & 1u);
+    if (!ok) atomicOr(lv.status, ST_BARRIER);
+    const RowGeo g = geo(k);
+    const bool whole = g.W == nx;
+    const bool valid = tx < g.W;
+    const int x = g.x0 + (valid ? tx : g.W - 1);
+    const unsigned xo[3] = {(unsigned)(x == 0 ? nx - 1 : x - 1), (unsigned)x, (unsigned)(x == nx - 1 ? 0 : x + 1)};
+    unsigned yo[3], zo[3];
+    yzo(g, yo, zo);
+    const uint32_t w = (valid && ok) ? sw[s][tx] : 0u;
+    const unsigned n = (unsigned)x + yo[1] + zo[1];
+    CellLink cl;
+    cl.p = -1;
+    if (w & NB_FLUID) {
+      const int xyz[3] = {x, g.y, g.z};
+      const int W = g.W;
+      node_update<S, PAR, FORCE, TAU1>(
+          lv, wa, n, xyz, xo, yo, zo, w, sc[s][tx], spu[s][tx],
+          [&](int r, unsigned slot) -> float {
+            if (PAR == 0 || r == 0) return Store<S>::ld(&sb[s][r][tx]);
+            int j = tx - D::cx(r);
+            if (whole) j = j < 0 ? j + W : (j >= W ? j - W : j);
+            return (j >= 0 && j < W) ? Store<S>::ld(&sb[s][r][j]) : Store<S>::ld(pop + slot);
+          },
+          wkey, wF, wK, cl);
+    }
+    // the last row's records to the slots reserved then; this row's slots
+    // reserved now, its records staged
+    write_staged(lv, lp, lgrp, lbase, srec[0][tx], srec[1][tx]);
+    const LinkSlot sl = reserve_links(lv, cl);
+    if (cl.p >= 0) {
+      srec[0][tx] = make_float4(__uint_as_float(n), __uint_as_float(cl.mask), cl.e[0], cl.e[1]);
+      srec[1][tx] = make_float4(cl.e[2], cl.e[3], cl.e[4], cl.e[5]);
+    }
+    lp = cl.p;
+    lgrp = sl.grp;
+    lbase = sl.base;
+    if (__syncthreads_or(!ok)) {  // stage s is read: free for refill
+      failed = true;
+      break;
+    }
+  }
+  write_staged(lv, lp, lgrp, lbase, srec[0][tx], srec[1][tx]);
+  if (failed && tx == 0) {
+    // gave up: let the copies still in flight land before the block exits
+    for (int k = 0; k < TS; ++k) mbar_wait(&bar[k], 0u), mbar_wait(&bar[k], 1u);
+  }
+  flush_wall_momentum(wa, wkey, wF, wK);
+}
+
+template <class S, int PAR, bool FORCE, bool TAU1>
+static void launch_rows(const LatticeView &lv, const WallAcc &wa, cudaStream_t st) {
+  const int nitems = ((lv.nx + 127) / 128) * lv.ny * lv.nz;
+  const int g = lv.rows_grid[PAR * 4 + (FORCE ? 2 : 0) + (TAU1 ? 1 : 0)];
+  k_lb_step_rows<S, PAR, FORCE, TAU1, BL_ROWS_TS><<<min(g > 0 ? g : 1, nitems), 128, 0, st>>>(lv, wa);
+}
+
+// the persistent sweep's grid for each instantiation (index PAR * 4 + FORCE
+// * 2 + TAU1): SMs x resident blocks per SM
+template <class S>
+static void rows_grids(int out[8]) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void *k[8] = {(const void *)k_lb_step_rows<S, 0, false, false, BL_ROWS_TS>,
+                      (const void *)k_lb_step_rows<S, 0, false, true, BL_ROWS_TS>,
+                      (const void *)k_lb_step_rows<S, 0, true, false, BL_ROWS_TS>,
+                      (const void *)k_lb_step_rows<S, 0, true, true, BL_ROWS_TS>,
+                      (const void *)k_lb_step_rows<S, 1, false, false, BL_ROWS_TS>,
+                      (const void *)k_lb_step_rows<S, 1, false, true, BL_ROWS_TS>,
+                      (const void *)k_lb_step_rows<S, 1, true, false, BL_ROWS_TS>,
+                      (const void *)k_lb_step_rows<S, 1, true, true, BL_ROWS_TS>};
+  for (int i = 0; i < 8; ++i) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k[i], 128, 0) != cudaSuccess || b < 1) b = 1;
+    out[i] = (sms > 0 ? sms : 1) * b;
+  }
+}
+
 // row length for the bulk-copy sweep: 16-byte aligned rows of the storage type
 __host__ __device__ inline bool bulk_rows_ok(int nx, int store_bytes) { return nx % (16 / store_bytes) == 0; }
 
 // sweep variants (LatticeView::sweep): 0 one node per thread; 1, 2 the FP32
 // pipeline over 4 or 8 planes; 3, 4 the bulk-copy pipeline over 8 or 4 planes
-// with 3 stages (any storage type with 16-byte aligned rows, else variant 0)
+// with 3 stages; 5 the persistent bulk-copy row sweep (3 to 5: any storage
+// type with 16-byte aligned rows, else variant 0)
 template <class S, int PAR, bool FORCE, bool TAU1>
 static void launch_lb_variant(const LatticeView &lv, dim3 grid, dim3 block, const WallAcc &wa, cudaStream_t st) {
   if constexpr (std::is_same<S, float>::value) {
@@ -678,6 +916,7 @@ static void launch_lb_variant(const LatticeView &lv, dim3 grid, dim3 block, cons
   if (bulk_rows_ok(lv.nx, (int)sizeof(S))) {
     if (lv.sweep == 3) return launch_bulk<S, PAR, FORCE, TAU1, 8, BL_BULK_TS>(lv, grid, wa, st);
     if (lv.sweep == 4) return launch_bulk<S, PAR, FORCE, TAU1, 4, BL_BULK_TS>(lv, grid, wa, st);
+    if (lv.sweep == 5) return launch_rows<S, PAR, FORCE, TAU1>(lv, wa, st);
   }
   k_lb_step<S, PAR, FORCE, TAU1><<<grid, block, 0, st>>>(lv, wa);
 }

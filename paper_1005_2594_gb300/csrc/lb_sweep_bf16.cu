@@ -7,4 +7,6 @@ void launch_lb_step_bf16(const LatticeView &lv, int par, const WallAcc &wa, cuda
   launch_lb_typed<__nv_bfloat16>(lv, par, wa, st);
 }
 
+void lb_rows_grids_bf16(int out[8]) { rows_grids<__nv_bfloat16>(out); }
+
 }  // namespace bl

@@ -7,4 +7,6 @@ void launch_lb_step_f16(const LatticeView &lv, int par, const WallAcc &wa, cudaS
   launch_lb_typed<__half>(lv, par, wa, st);
 }
 
+void lb_rows_grids_f16(int out[8]) { rows_grids<__half>(out); }
+
 }  // namespace bl

@@ -7,4 +7,6 @@ void launch_lb_step_f32(const LatticeView &lv, int par, const WallAcc &wa, cudaS
   launch_lb_typed<float>(lv, par, wa, st);
 }
 
+void lb_rows_grids_f32(int out[8]) { rows_grids<float>(out); }
+
 }  // namespace bl

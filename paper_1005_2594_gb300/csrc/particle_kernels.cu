@@ -636,39 +636,28 @@ __device__ __forceinline__ void cell_geo(const PartView &pv, int p, CellGeo &g) 
 //   F0 = F_raw - rho M v_p,  T0 = d x F0,  v_p = Vp + Wp x d,
 //   Zff = rho M,  Zft = rho M [d]x^T,  Ztt = [d]x rho M [d]x^T,
 // with M = sum over the mask of (m_r / 6) c_r c_r^T, and the constant parts
-// K = sum m_r c_r, IT = d_int x K with d_int = y - rint(X) exactly.
+// K = sum m_r c_r, IT = d_int x K with d_int = y - rint(X) exactly.  At
+// tau = 1 the record holds the node's moments instead of F_raw, and the
+// bounced populations f~*_r are evaluated again here by the function the
+// sweep collides with.
 
 constexpr int LT = 128;  // threads of a link-reduction block
-
-// direction masks of the lattice (bit r), for the record sums by popcount
-template <class P>
-__host__ __device__ constexpr uint32_t dir_mask(P pred) {
-  uint32_t m = 0;
-  for (int r = 1; r < Q; ++r)
-    if (pred(r)) m |= 1u << r;
-  return m;
-}
-using D3 = D3Q19;
-constexpr int cxyz(int r, int a) { return a == 0 ? D3::cx(r) : (a == 1 ? D3::cy(r) : D3::cz(r)); }
-template <int A, int SGN>
-struct AxisDirs {  // axis vectors along A with sign SGN (m = 2)
-  static constexpr uint32_t v = dir_mask([](int r) { return r <= 6 && cxyz(r, A) == SGN; });
-};
-template <int A, int SGN>
-struct DiagDirs {  // diagonal vectors with c_A = SGN (m = 1)
-  static constexpr uint32_t v = dir_mask([](int r) { return r > 6 && cxyz(r, A) == SGN; });
-};
-template <int A, int B, int SGN>
-struct PairDirs {  // diagonal vectors with c_A c_B = SGN
-  static constexpr uint32_t v = dir_mask([](int r) { return r > 6 && cxyz(r, A) * cxyz(r, B) == SGN; });
-};
-
-__device__ __forceinline__ int popm(uint32_t m, uint32_t sel) { return __popc(m & sel); }
+// threads of a block of the cell solve (one thread per cell): few, so that
+// the FP64 work of the cells spreads over many SMs
+#ifndef BL_SOLVE_TB
+#define BL_SOLVE_TB 32
+#endif
 
 __global__ void __launch_bounds__(LT) k_link_reduce(LatticeView lv, PartView pv) {
   __shared__ float shf[LT / 32][27];
   __shared__ int shi[LT / 32][6];
+  __shared__ float4 cw[Q];  // (c_x, c_y, c_z, w_r) of each direction, for the masks' bits
   const int p = blockIdx.x;
+  if (threadIdx.x < Q) {
+    const int r = threadIdx.x;
+    cw[r] = make_float4((float)D3::cx(r), (float)D3::cy(r), (float)D3::cz(r), (float)D3::m(r) / 36.0f);
+  }
+  __syncthreads();
   const int nrec = min(lv.rec_count[p], lv.rec_cap);
   const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
   const int Xi[3] = {(int)k0.w, (int)k1.w, (int)k2.w};
@@ -680,40 +669,52 @@ __global__ void __launch_bounds__(LT) k_link_reduce(LatticeView lv, PartView pv)
 #pragma unroll
   for (int k = 0; k < 6; ++k) iv[k] = 0;
   const float4 *rec = lv.rec + 2 * (size_t)p * lv.rec_cap;
+  const bool tau1 = lv.omega == 1.0f;  // the sweep's records hold moments (tau = 1) or link sums
   for (int i = threadIdx.x; i < nrec; i += LT) {
     const float4 r0 = rec[2 * i], r1 = rec[2 * i + 1];
     const unsigned n = __float_as_uint(r0.x);
     const uint32_t m = __float_as_uint(r0.y) & NB_SOLID;
-    const float rho = r0.z;
+    const float rho = lv.rho0 + r0.z;
     const unsigned z = n / nxy, rem = n - z * nxy, y = rem / nx, x = rem - y * nx;
     const int di[3] = {imin_image((int)x - Xi[0], lv.nx, lv.per[0]), imin_image((int)y - Xi[1], lv.ny, lv.per[1]),
                        imin_image((int)z - Xi[2], lv.nz, lv.per[2])};
     const float d[3] = {(float)di[0] - k0.x, (float)di[1] - k0.y, (float)di[2] - k0.z};
     // rho M and K from the mask
     const float w6 = rho * (1.0f / 6.0f);
-    const float Axx = w6 * (float)(2 * popm(m, AxisDirs<0, 1>::v | AxisDirs<0, -1>::v) +
-                                   popm(m, DiagDirs<0, 1>::v | DiagDirs<0, -1>::v));
-    const float Ayy = w6 * (float)(2 * popm(m, AxisDirs<1, 1>::v | AxisDirs<1, -1>::v) +
-                                   popm(m, DiagDirs<1, 1>::v | DiagDirs<1, -1>::v));
-    const float Azz = w6 * (float)(2 * popm(m, AxisDirs<2, 1>::v | AxisDirs<2, -1>::v) +
-                                   popm(m, DiagDirs<2, 1>::v | DiagDirs<2, -1>::v));
-    const float Axy = w6 * (float)(popm(m, PairDirs<0, 1, 1>::v) - popm(m, PairDirs<0, 1, -1>::v));
-    const float Axz = w6 * (float)(popm(m, PairDirs<0, 2, 1>::v) - popm(m, PairDirs<0, 2, -1>::v));
-    const float Ayz = w6 * (float)(popm(m, PairDirs<1, 2, 1>::v) - popm(m, PairDirs<1, 2, -1>::v));
-    const int K[3] = {2 * (popm(m, AxisDirs<0, 1>::v) - popm(m, AxisDirs<0, -1>::v)) + popm(m, DiagDirs<0, 1>::v) -
-                          popm(m, DiagDirs<0, -1>::v),
-                      2 * (popm(m, AxisDirs<1, 1>::v) - popm(m, AxisDirs<1, -1>::v)) + popm(m, DiagDirs<1, 1>::v) -
-                          popm(m, DiagDirs<1, -1>::v),
-                      2 * (popm(m, AxisDirs<2, 1>::v) - popm(m, AxisDirs<2, -1>::v)) + popm(m, DiagDirs<2, 1>::v) -
-                          popm(m, DiagDirs<2, -1>::v)};
+    const float Axx = w6 * (float)mask_Maa<0>(m), Ayy = w6 * (float)mask_Maa<1>(m), Azz = w6 * (float)mask_Maa<2>(m);
+    const float Axy = w6 * (float)mask_Mab<0, 1>(m), Axz = w6 * (float)mask_Mab<0, 2>(m),
+                Ayz = w6 * (float)mask_Mab<1, 2>(m);
+    const int K[3] = {mask_K<0>(m), mask_K<1>(m), mask_K<2>(m)};
+    // the sum of 2 f~*_r c_r over the mask: at tau = 1 the bounced populations
+    // again from the node's moments (drho, u, uu, uF), else the sweep's sums
+    float Fr[3];
+    if (tau1) {
+      const float ux = r0.w, uy = r1.x, uz = r1.y, uu = r1.z, uF = r1.w;
+      const float Fx = lv.has_force ? rho * lv.g[0] : 0.f, Fy = lv.has_force ? rho * lv.g[1] : 0.f,
+                  Fz = lv.has_force ? rho * lv.g[2] : 0.f;
+      Fr[0] = Fr[1] = Fr[2] = 0.f;
+      for (uint32_t mm = m; mm; mm &= mm - 1u) {
+        const float4 c = cw[__ffs(mm) - 1];
+        const float cu = c.x * ux + c.y * uy + c.z * uz;
+        const float cF = c.x * Fx + c.y * Fy + c.z * Fz;
+        const float fs2 = 2.0f * post_tau1(c.w, r0.z, lv.rho0, cu, uu, lv.has_force != 0, cF, uF, 0.5f);
+        Fr[0] += c.x * fs2;
+        Fr[1] += c.y * fs2;
+        Fr[2] += c.z * fs2;
+      }
+    } else {
+      Fr[0] = r0.w;
+      Fr[1] = r1.x;
+      Fr[2] = r1.y;
+    }
     const float A[3][3] = {{Axx, Axy, Axz}, {Axy, Ayy, Ayz}, {Axz, Ayz, Azz}};
     // predictor velocity at the node and the link momentum
     const float vp[3] = {k1.x + (k2.y * d[2] - k2.z * d[1]), k1.y + (k2.z * d[0] - k2.x * d[2]),
                          k1.z + (k2.x * d[1] - k2.y * d[0])};
     float F[3];
-    F[0] = r0.w - (A[0][0] * vp[0] + A[0][1] * vp[1] + A[0][2] * vp[2]);
-    F[1] = r1.x - (A[1][0] * vp[0] + A[1][1] * vp[1] + A[1][2] * vp[2]);
-    F[2] = r1.y - (A[2][0] * vp[0] + A[2][1] * vp[1] + A[2][2] * vp[2]);
+    F[0] = Fr[0] - (A[0][0] * vp[0] + A[0][1] * vp[1] + A[0][2] * vp[2]);
+    F[1] = Fr[1] - (A[1][0] * vp[0] + A[1][1] * vp[1] + A[1][2] * vp[2]);
+    F[2] = Fr[2] - (A[2][0] * vp[0] + A[2][1] * vp[1] + A[2][2] * vp[2]);
     v[0] += F[0];
     v[1] += F[1];
     v[2] += F[2];
@@ -948,8 +949,9 @@ __global__ void __launch_bounds__(LT) k_link_pending(LatticeView lv, PartView pv
     const float d[3] = {(float)imin_image(yc[0] - Xi[0], lv.nx, lv.per[0]) - k0.x,
                         (float)imin_image(yc[1] - Xi[1], lv.ny, lv.per[1]) - k0.y,
                         (float)imin_image(yc[2] - Xi[2], lv.nz, lv.per[2]) - k0.z};
-    const float u[3] = {r0.z * (V[0] + (W[1] * d[2] - W[2] * d[1])), r0.z * (V[1] + (W[2] * d[0] - W[0] * d[2])),
-                        r0.z * (V[2] + (W[0] * d[1] - W[1] * d[0]))};
+    const float rho = lv.rho0 + r0.z;
+    const float u[3] = {rho * (V[0] + (W[1] * d[2] - W[2] * d[1])), rho * (V[1] + (W[2] * d[0] - W[0] * d[2])),
+                        rho * (V[2] + (W[0] * d[1] - W[1] * d[0]))};
     const uint32_t mask = mb & NB_SOLID;
     if (!(mb & REC_DIRECT)) {
       lv.pu[n] = make_float4(u[0], u[1], u[2], __uint_as_float(mask));
@@ -1722,7 +1724,7 @@ void launch_sums_solve(int dtype, const LatticeView &lv, const PartView &pv, int
   (void)par;
   if (pv.n == 0) return;
   k_link_reduce<<<pv.n, LT, 0, st>>>(lv, pv);
-  k_solve<<<nblk(pv.n, 32), 32, 0, st>>>(lv, pv);
+  k_solve<<<nblk(pv.n, BL_SOLVE_TB), BL_SOLVE_TB, 0, st>>>(lv, pv);
   *nl += 2;
 }
 

@@ -55,10 +55,17 @@ def test_oracle_on_all_cores_aggregates_processes():
 
 
 def test_sweep_kernel_label_follows_the_default_variant():
-    assert "k_lb_step_bulk" in bench.sweep_kernel(128, 0) and "FP32" in bench.sweep_kernel(128, 0)
-    assert "k_lb_step_bulk" in bench.sweep_kernel(256, 1) and "BF16" in bench.sweep_kernel(256, 1)
-    assert "k_lb_step_pipe" in bench.sweep_kernel(30, 0)
-    assert bench.sweep_kernel(36, 2).startswith("k_lb_step ") and "FP16" in bench.sweep_kernel(36, 2)
+    # with cells one node per thread; without, the bulk-copy pipeline where rows allow it
+    assert bench.sweep_kernel(128, 0).startswith("k_lb_step ") and "FP32" in bench.sweep_kernel(128, 0)
+    assert "k_lb_step_bulk" in bench.sweep_kernel(128, 0, cells=False)
+    assert "k_lb_step_bulk" in bench.sweep_kernel(256, 1, cells=False) and "BF16" in bench.sweep_kernel(256, 1, cells=False)
+    assert "k_lb_step_pipe" in bench.sweep_kernel(30, 0, cells=False)
+    assert bench.sweep_kernel(36, 2, cells=False).startswith("k_lb_step ") and "FP16" in bench.sweep_kernel(36, 2)
+    # an explicit variant: its kernel where the rows and the storage allow it
+    assert bench.sweep_kernel(128, 0, 5).startswith("k_lb_step_rows ")
+    assert "4 planes" in bench.sweep_kernel(128, 1, 4)
+    assert bench.sweep_kernel(36, 2, 5).startswith("k_lb_step ")
+    assert bench.sweep_kernel(64, 1, 2).startswith("k_lb_step ")
 
 
 def test_clock_sampler_reports_without_a_gpu():

@@ -401,12 +401,13 @@ def test_graph_replay_matches_single_steps():
 
 def test_sweep_variants_agree():
     """The thread mappings of the FP32 sweep (one node per thread, the two
-    pipelines with per-thread copies, the two bulk-copy pipelines) compute
-    the same step; here each row is one whole periodic segment."""
+    pipelines with per-thread copies, the two bulk-copy pipelines over z
+    planes, the persistent bulk-copy row sweep) compute the same step; here
+    each row is one whole periodic segment."""
     oracle, bl, workloads = _mods()
     p, X, q, V, L = _coupled(0.0, seed=1021)
     sims = []
-    for v in (0, 1, 2, 3, 4):
+    for v in (0, 1, 2, 3, 4, 5):
         s = bl.Simulation(p)
         s.sweep_variant(v)
         s.set_particles(X, q, V, L)
@@ -435,7 +436,7 @@ def test_bulk_sweep_with_16bit_storage():
     for dtype, tol in ((1, 2.0 ** -8), (2, 2.0 ** -11)):
         for cells in (False, True):
             sims = []
-            for v in (0, 3):
+            for v in (0, 3, 5):
                 s = bl.Simulation(p, store_dtype=dtype)
                 s.sweep_variant(v)
                 if cells:
@@ -443,13 +444,14 @@ def test_bulk_sweep_with_16bit_storage():
                 s.step(12)
                 s.sync()
                 sims.append(s)
-            np.testing.assert_array_equal(sims[1].owner(), sims[0].owner())
-            u1, u0 = sims[1].fields()[1], sims[0].fields()[1]
-            if cells:
-                assert rel(sims[1].particles()["X"], sims[0].particles()["X"]) < 1e-6
-                assert rel(u1, u0) < tol, (dtype, rel(u1, u0))
-            else:
-                assert rel(u1, u0) < 1e-6, (dtype, rel(u1, u0))
+            for sv in sims[1:]:
+                np.testing.assert_array_equal(sv.owner(), sims[0].owner())
+                u1, u0 = sv.fields()[1], sims[0].fields()[1]
+                if cells:
+                    assert rel(sv.particles()["X"], sims[0].particles()["X"]) < 1e-6
+                    assert rel(u1, u0) < tol, (dtype, rel(u1, u0))
+                else:
+                    assert rel(u1, u0) < 1e-6, (dtype, rel(u1, u0))
             for s in sims:
                 s.close()
 
@@ -466,7 +468,7 @@ def test_bulk_sweep_on_split_rows_with_forcing():
         p["tau"] = 0.8
         X, q, _ = workloads.pack_cells(p, 12, 5)
         sims = []
-        for v in (0, 3, 4):
+        for v in (0, 3, 4, 5):
             s = bl.Simulation(p)
             s.sweep_variant(v)
             s.set_particles(X, q)
@@ -513,7 +515,7 @@ def test_autotune_keeps_a_valid_variant():
     s = bl.Simulation(p)
     s.set_particles(X, q, V, L)
     choice = s.autotune(6)
-    assert choice in (0, 1, 2, 3, 4)
+    assert choice in (0, 1, 2, 3, 4, 5)
     s.step(4)
     s.sync()
 
@@ -553,7 +555,8 @@ def test_ensemble_members_match_oracle():
     ens.close()
 
 
-def test_split_rows_with_cells_100_steps():
+@pytest.mark.parametrize("variant", [3, 5])
+def test_split_rows_with_cells_100_steps(variant):
     """Rows of 136 nodes: the bulk-copy sweep takes them as a 128-node and an
     8-node segment whose edge nodes read their shifted neighbours from global
     memory (the path of the 256^3 workloads), here with cells and a body
@@ -564,7 +567,7 @@ def test_split_rows_with_cells_100_steps():
                               wall_vel={4: (-0.01, 0.0, 0.0), 5: (0.01, 0.0, 0.0)})
     X, q, _ = workloads.pack_cells(p, 14, 29)
     orc, sim = oracle.Oracle(p), bl.Simulation(p)
-    sim.sweep_variant(3)
+    sim.sweep_variant(variant)
     orc.set_particles(X, q)
     sim.set_particles(X, q)
     for block in range(4):

@@ -63,10 +63,30 @@ struct Store<__half> {
   static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v * 1024.0f); }
 };
 
+// division by a lattice extent through a multiply-high: with
+// m = floor((2^64 - 1) / d) + 1, floor(n / d) is the high 64 bits of n m for
+// every 32-bit n and 2 <= d < 2^32 (m = floor(2^64 / d) + 1, or 2^64 / d when
+// d divides 2^64; the error of n m / 2^64 against n / d is below n / 2^64 <
+// 2^-32 <= 1 / d, and frac(n / d) <= 1 - 1 / d); d = 1 is passed through
+struct FastDiv {
+  unsigned long long m;
+  unsigned d;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d;
+  f.m = d > 1u ? ~0ull / d + 1ull : 0ull;
+  return f;
+}
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f) {
+  return f.d == 1u ? n : (unsigned)__umul64hi((unsigned long long)n, f.m);
+}
+
 struct LatticeView {
   int nx, ny, nz;
   int per[3];
   unsigned N;  // nodes; 19 N < 2^32 is checked on the host
+  FastDiv dnx, dnxy;  // division by nx and by nx ny (node index -> coordinates)
   float wall_vel[NWALL][3];
   float omega;  // 1 / tau
   float rho0;
@@ -323,6 +343,29 @@ struct PairDirs {  // diagonal vectors with c_A c_B = SGN
 };
 
 __device__ __forceinline__ int popm(uint32_t m, uint32_t sel) { return __popc(m & sel); }
+
+// the components of c_r for a direction r known only at run time: c + 1
+// packed two bits per direction in a 64-bit constant
+template <int A>
+__host__ __device__ constexpr unsigned long long packed_dirs() {
+  unsigned long long v = 0;
+  for (int r = 0; r < Q; ++r) v |= (unsigned long long)(cxyz(r, A) + 1) << (2 * r);
+  return v;
+}
+template <int A>
+__device__ __forceinline__ int rt_c(int r) {
+  return (int)((packed_dirs<A>() >> (2 * r)) & 3ull) - 1;
+}
+__device__ __forceinline__ int rt_m(int r) { return r == 0 ? 12 : (r <= 6 ? 2 : 1); }
+__device__ __forceinline__ int rt_opp(int r) { return r == 0 ? 0 : ((r & 1) ? r + 1 : r - 1); }
+
+// node index -> coordinates
+__device__ __forceinline__ void node_xyz(const LatticeView &lv, unsigned n, int xyz[3]) {
+  const unsigned z = fdiv(n, lv.dnxy), rem = n - z * lv.dnxy.d, y = fdiv(rem, lv.dnx);
+  xyz[0] = (int)(rem - y * lv.dnx.d);
+  xyz[1] = (int)y;
+  xyz[2] = (int)z;
+}
 
 // sums over the directions of a mask (bit r) by popcount: component A of
 // K = sum m_r c_r, and the entries A A and A B of M = sum m_r c_r c_r^T

@@ -245,6 +245,8 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
   lv.nz = p->nz;
   for (int k = 0; k < 3; ++k) lv.per[k] = p->periodic[k] ? 1 : 0;
   lv.N = (unsigned)N;
+  lv.dnx = bl::make_fastdiv((unsigned)p->nx);
+  lv.dnxy = bl::make_fastdiv((unsigned)p->nx * (unsigned)p->ny);
   for (int w = 0; w < bl::NWALL; ++w)
     for (int k = 0; k < 3; ++k) lv.wall_vel[w][k] = (float)p->wall_vel[w][k];
   lv.omega = (float)(1.0 / p->tau);

@@ -138,15 +138,8 @@ __device__ __forceinline__ void emit_links(const LatticeView &lv, const CellLink
 }
 
 // the neighbour n + c_r for a direction r known only at run time: the
-// components of c_r + 1 packed two bits per direction, the coordinate
-// chosen by selects (no indexing of the xo, yo, zo arrays)
-template <int A>
-__host__ __device__ constexpr unsigned long long packed_dirs() {
-  unsigned long long v = 0;
-  for (int r = 0; r < Q; ++r)
-    v |= (unsigned long long)((A == 0 ? D3Q19::cx(r) : (A == 1 ? D3Q19::cy(r) : D3Q19::cz(r))) + 1) << (2 * r);
-  return v;
-}
+// components of c_r + 1 from their packed form, the coordinate chosen by
+// selects (no indexing of the xo, yo, zo arrays)
 __device__ __forceinline__ unsigned pick3(unsigned k, const unsigned v[3]) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); }
 __device__ __forceinline__ unsigned neighbour_rt(int r, const unsigned xo[3], const unsigned yo[3], const unsigned zo[3]) {
   constexpr unsigned long long PX = packed_dirs<0>(), PY = packed_dirs<1>(), PZ = packed_dirs<2>();

@@ -339,12 +339,6 @@ __device__ __forceinline__ int warp_append(int cnt, int *sh_len) {
   return base + inc - cnt;
 }
 
-__device__ __forceinline__ void node_xyz(const LatticeView &lv, unsigned n, int xyz[3]) {
-  xyz[0] = n % lv.nx;
-  xyz[1] = (n / lv.nx) % lv.ny;
-  xyz[2] = n / ((unsigned)lv.nx * lv.ny);
-}
-
 __device__ __forceinline__ unsigned node_of(const LatticeView &lv, int x, int y, int z) {
   return (unsigned)x + (unsigned)lv.nx * ((unsigned)y + (unsigned)lv.ny * z);
 }
@@ -387,13 +381,12 @@ struct BoxIter {
 
 // slot where the sweep of parity par bounced direction r of fluid node y
 __device__ __forceinline__ unsigned bounce_slot(const LatticeView &lv, int par, unsigned y, const int yc[3], int r) {
-  using D = D3Q19;
   if (par == 0) {
-    const unsigned nb = node_of(lv, wrapi(yc[0] + D::cx(r), lv.nx), wrapi(yc[1] + D::cy(r), lv.ny),
-                                wrapi(yc[2] + D::cz(r), lv.nz));
+    const unsigned nb = node_of(lv, wrapi(yc[0] + rt_c<0>(r), lv.nx), wrapi(yc[1] + rt_c<1>(r), lv.ny),
+                                wrapi(yc[2] + rt_c<2>(r), lv.nz));
     return (unsigned)r * lv.N + nb;
   }
-  return (unsigned)D::opp(r) * lv.N + y;
+  return (unsigned)rt_opp(r) * lv.N + y;
 }
 
 // ---------------------------------------------------------------------------
@@ -661,7 +654,6 @@ __global__ void __launch_bounds__(LT) k_link_reduce(LatticeView lv, PartView pv)
   const int nrec = min(lv.rec_count[p], lv.rec_cap);
   const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
   const int Xi[3] = {(int)k0.w, (int)k1.w, (int)k2.w};
-  const unsigned nx = (unsigned)lv.nx, nxy = (unsigned)lv.nx * (unsigned)lv.ny;
   float v[27];
   int iv[6];
 #pragma unroll
@@ -675,9 +667,10 @@ __global__ void __launch_bounds__(LT) k_link_reduce(LatticeView lv, PartView pv)
     const unsigned n = __float_as_uint(r0.x);
     const uint32_t m = __float_as_uint(r0.y) & NB_SOLID;
     const float rho = lv.rho0 + r0.z;
-    const unsigned z = n / nxy, rem = n - z * nxy, y = rem / nx, x = rem - y * nx;
-    const int di[3] = {imin_image((int)x - Xi[0], lv.nx, lv.per[0]), imin_image((int)y - Xi[1], lv.ny, lv.per[1]),
-                       imin_image((int)z - Xi[2], lv.nz, lv.per[2])};
+    int yc[3];
+    node_xyz(lv, n, yc);
+    const int di[3] = {imin_image(yc[0] - Xi[0], lv.nx, lv.per[0]), imin_image(yc[1] - Xi[1], lv.ny, lv.per[1]),
+                       imin_image(yc[2] - Xi[2], lv.nz, lv.per[2])};
     const float d[3] = {(float)di[0] - k0.x, (float)di[1] - k0.y, (float)di[2] - k0.z};
     // rho M and K from the mask
     const float w6 = rho * (1.0f / 6.0f);
@@ -931,8 +924,12 @@ __global__ void k_solve(LatticeView lv, PartView pv) {
 // Every link is one cell's, so no two blocks touch the same slot.
 template <class S>
 __global__ void __launch_bounds__(LT) k_link_pending(LatticeView lv, PartView pv, int par) {
-  using D = D3Q19;
+  constexpr int PQ = 512;  // queue of a block's second- and third-cell records
+  __shared__ int s_nq;
+  __shared__ int s_q[PQ];
   const int p = blockIdx.x;
+  if (threadIdx.x == 0) s_nq = 0;
+  __syncthreads();
   const int nrec = min(pv.rec_last[p], lv.rec_cap);
   const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
   const int Xi[3] = {(int)k0.w, (int)k1.w, (int)k2.w};
@@ -940,30 +937,55 @@ __global__ void __launch_bounds__(LT) k_link_pending(LatticeView lv, PartView pv
   const float V[3] = {vw[0], vw[1], vw[2]}, W[3] = {vw[3], vw[4], vw[5]};
   S *pop = reinterpret_cast<S *>(lv.pop);
   const float4 *rec = lv.rec + 2 * (size_t)p * lv.rec_cap;
-  for (int i = threadIdx.x; i < nrec; i += LT) {
+  // rho (V + W x d) of record i's node, its coordinates and its mask word
+  auto node_u = [&](int i, unsigned &n, uint32_t &mb, int yc[3], float u[3]) {
     const float4 r0 = rec[2 * i];
-    const unsigned n = __float_as_uint(r0.x);
-    const uint32_t mb = __float_as_uint(r0.y);
-    int yc[3];
+    n = __float_as_uint(r0.x);
+    mb = __float_as_uint(r0.y);
     node_xyz(lv, n, yc);
     const float d[3] = {(float)imin_image(yc[0] - Xi[0], lv.nx, lv.per[0]) - k0.x,
                         (float)imin_image(yc[1] - Xi[1], lv.ny, lv.per[1]) - k0.y,
                         (float)imin_image(yc[2] - Xi[2], lv.nz, lv.per[2]) - k0.z};
     const float rho = lv.rho0 + r0.z;
-    const float u[3] = {rho * (V[0] + (W[1] * d[2] - W[2] * d[1])), rho * (V[1] + (W[2] * d[0] - W[0] * d[2])),
-                        rho * (V[2] + (W[0] * d[1] - W[1] * d[0]))};
-    const uint32_t mask = mb & NB_SOLID;
-    if (!(mb & REC_DIRECT)) {
-      lv.pu[n] = make_float4(u[0], u[1], u[2], __uint_as_float(mask));
-    } else {
-      for (uint32_t m = mask; m; m &= m - 1u) {
-        const int r = __ffs(m) - 1;
-        const float C = -(D::m(r) / 6.0f) * (D::cx(r) * u[0] + D::cy(r) * u[1] + D::cz(r) * u[2]);
-        const unsigned slot = bounce_slot(lv, par, n, yc, r);
-        Store<S>::st(pop + slot, Store<S>::ld(pop + slot) + C);
-      }
+    u[0] = rho * (V[0] + (W[1] * d[2] - W[2] * d[1]));
+    u[1] = rho * (V[1] + (W[2] * d[0] - W[0] * d[2]));
+    u[2] = rho * (V[2] + (W[0] * d[1] - W[1] * d[0]));
+  };
+  // C in place for the directions of a second- or third-cell record
+  auto direct = [&](int i) {
+    unsigned n;
+    uint32_t mb;
+    int yc[3];
+    float u[3];
+    node_u(i, n, mb, yc, u);
+    for (uint32_t m = mb & NB_SOLID; m; m &= m - 1u) {
+      const int r = __ffs(m) - 1;
+      const float C = -((float)rt_m(r) / 6.0f) * ((float)rt_c<0>(r) * u[0] + (float)rt_c<1>(r) * u[1] +
+                                                  (float)rt_c<2>(r) * u[2]);
+      const unsigned slot = bounce_slot(lv, par, n, yc, r);
+      Store<S>::st(pop + slot, Store<S>::ld(pop + slot) + C);
     }
+  };
+  for (int i = threadIdx.x; i < nrec; i += LT) {
+    const uint32_t mb = __float_as_uint(rec[2 * i].y);
+    if (mb & REC_DIRECT) {
+      const int k = atomicAdd(&s_nq, 1);
+      if (k < PQ) s_q[k] = i;
+      else direct(i);
+      continue;
+    }
+    unsigned n;
+    uint32_t mb2;
+    int yc[3];
+    float u[3];
+    node_u(i, n, mb2, yc, u);
+    lv.pu[n] = make_float4(u[0], u[1], u[2], __uint_as_float(mb2 & NB_SOLID));
   }
+  // the records of a node's second or third cell, gathered so that the
+  // warps take their per-direction loops with full lanes
+  __syncthreads();
+  const int nq = min(s_nq, PQ);
+  for (int k = threadIdx.x; k < nq; k += LT) direct(s_q[k]);
 }
 
 // The pending C of the last step given to the stored populations, for

@@ -635,13 +635,21 @@ __device__ __forceinline__ void cell_geo(const PartView &pv, int p, CellGeo &g) 
 // sweep collides with.
 
 constexpr int LT = 128;  // threads of a link-reduction block
+// blocks of the link reduction and of the claims resident per SM: enough
+// that one wave holds a thousand cells (the register cap this sets)
+#ifndef BL_REDUCE_MINB
+#define BL_REDUCE_MINB 7
+#endif
+#ifndef BL_CLAIMS_MINB
+#define BL_CLAIMS_MINB 7
+#endif
 // threads of a block of the cell solve (one thread per cell): few, so that
 // the FP64 work of the cells spreads over many SMs
 #ifndef BL_SOLVE_TB
 #define BL_SOLVE_TB 32
 #endif
 
-__global__ void __launch_bounds__(LT) k_link_reduce(LatticeView lv, PartView pv) {
+__global__ void __launch_bounds__(LT, BL_REDUCE_MINB) k_link_reduce(LatticeView lv, PartView pv) {
   __shared__ float shf[LT / 32][27];
   __shared__ int shi[LT / 32][6];
   __shared__ float4 cw[Q];  // (c_x, c_y, c_z, w_r) of each direction, for the masks' bits
@@ -1131,7 +1139,7 @@ constexpr int PB = 128;  // threads of the claims and resolve blocks (8 blocks f
 // contact sums for the lattice-wide geometry pass, which adds to them; in a
 // step (mode 0) the link correction may still be reading them, and the
 // step's geometry rewrites them.
-__global__ void __launch_bounds__(PB) k_claims(LatticeView lv, PartView pv, int *claim, ChangeList chg, int mode) {
+__global__ void __launch_bounds__(PB, BL_CLAIMS_MINB) k_claims(LatticeView lv, PartView pv, int *claim, ChangeList chg, int mode) {
   __shared__ int sh_len;
   const int p = blockIdx.x;
   if (threadIdx.x == 0) {

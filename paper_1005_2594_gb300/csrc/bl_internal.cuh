@@ -189,6 +189,7 @@ struct CellListView {
 struct SurfBits {
   uint32_t *bits;  // ny nz nxw words, or null when there is no surface wall node
   int nxw;
+  uint32_t *rows;  // one bit per lattice row (y, z): the row holds a surface wall node
 };
 
 // close pairs of the learned correction: pairs (i, j), their features
@@ -219,6 +220,7 @@ void launch_init(int dtype, const LatticeView &lv, cudaStream_t st);
 void launch_fill_int(int *a, unsigned n, int v, cudaStream_t st);
 void launch_apply_wall_mask(const LatticeView &lv, const uint8_t *mask, cudaStream_t st);
 void launch_surface_bits(const LatticeView &lv, const SurfBits &sb, int *count, cudaStream_t st);
+void launch_surface_rows(const LatticeView &lv, const SurfBits &sb, cudaStream_t st);
 unsigned links_blocks(const LatticeView &lv);
 void launch_links(const LatticeView &lv, int contact, int pass, int *block_count, const int *block_off, int32_t *out,
                   long long cap, cudaStream_t st);

@@ -186,12 +186,17 @@ static int build_surface_bits(bl_ctx *c) {
   const size_t words = (size_t)c->sbits.nxw * c->lv.ny * c->lv.nz;
   uint32_t *bits = c->sbits.bits;
   if (!bits) CU(cudaMalloc(&bits, sizeof(uint32_t) * words));
+  const size_t rwords = ((size_t)c->lv.ny * c->lv.nz + 31) / 32;
+  uint32_t *rows = c->sbits.rows;
+  if (!rows) CU(cudaMalloc(&rows, sizeof(uint32_t) * rwords));
   int *cnt = nullptr;
   CU(cudaMalloc(&cnt, sizeof(int)));
   CU(cudaMemsetAsync(cnt, 0, sizeof(int), c->stream));
-  SurfBits sb = {bits, c->sbits.nxw};
+  SurfBits sb = {bits, c->sbits.nxw, rows};
   launch_surface_bits(c->lv, sb, cnt, c->stream);
-  c->launches++;
+  CU(cudaMemsetAsync(rows, 0, sizeof(uint32_t) * rwords, c->stream));
+  launch_surface_rows(c->lv, sb, c->stream);
+  c->launches += 2;
   int h = 0;
   CU(cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -199,9 +204,12 @@ static int build_surface_bits(bl_ctx *c) {
   if (check_launch(c, "surface bits")) return c->sticky;
   if (h == 0) {
     cudaFree(bits);  // no walls: the wall potential is skipped
+    cudaFree(rows);
     bits = nullptr;
+    rows = nullptr;
   }
   c->sbits.bits = bits;
+  c->sbits.rows = rows;
   return BL_OK;
 }
 
@@ -269,13 +277,19 @@ extern "C" int bl_lb_init(bl_ctx **out, const bl_lb_params *p, void *cuda_stream
     if (cudaMalloc(&lv.owner, sizeof(int32_t) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "owner map"); break; }
     if (cudaMalloc(&c->claim, sizeof(int) * N) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "claim map"); break; }
     if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess) { rc = fail(c, BL_ENOMEM, "status"); break; }
-    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+    // the side streams run the cell list, the potentials, the contact sums
+    // and the claims beside the sweep and the pending C: at the highest
+    // priority, so that their few blocks are not queued behind the sweep's
+    // thousands (the step waits for them before the link sums)
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming) != cudaSuccess) {
       rc = fail(c, BL_ECUDA, "streams");
       break;
@@ -1227,7 +1241,7 @@ extern "C" void bl_destroy(bl_ctx *c) {
   if (c->side2) cudaStreamDestroy(c->side2);
   free_particles(c);
   void *ptrs[] = {c->lv.pop, c->lv.owner, c->lv.nbm, c->lv.nbc, c->lv.pu, c->claim, c->status,
-                  c->wacc.F, c->wacc.K, c->sbits.bits, c->scratch};
+                  c->wacc.F, c->wacc.K, c->sbits.bits, c->sbits.rows, c->scratch};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);

@@ -229,6 +229,15 @@ __global__ void k_surface_bits(LatticeView lv, SurfBits sb, int *count) {
   if (word) atomicAdd(count, __popc(word));
 }
 
+// the row bits: row (y, z) holds a surface wall node (rows cleared before)
+__global__ void k_surface_rows(LatticeView lv, SurfBits sb) {
+  const unsigned row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= (unsigned)lv.ny * lv.nz) return;
+  uint32_t any = 0;
+  for (int w = 0; w < sb.nxw; ++w) any |= sb.bits[(size_t)row * sb.nxw + w];
+  if (any) atomicOr(&sb.rows[row >> 5], 1u << (row & 31));
+}
+
 // ---------------------------------------------------------------------------
 // link lists by warp-level stream compaction in node order:
 // pass 0 counts per block, pass 1 writes at the block's scanned offset, each
@@ -359,6 +368,11 @@ void launch_apply_wall_mask(const LatticeView &lv, const uint8_t *mask, cudaStre
 void launch_surface_bits(const LatticeView &lv, const SurfBits &sb, int *count, cudaStream_t st) {
   const unsigned words = (unsigned)sb.nxw * lv.ny * lv.nz;
   k_surface_bits<<<nblk(words, 128), 128, 0, st>>>(lv, sb, count);
+}
+
+void launch_surface_rows(const LatticeView &lv, const SurfBits &sb, cudaStream_t st) {
+  const unsigned rows = (unsigned)lv.ny * lv.nz;
+  k_surface_rows<<<nblk(rows, 128), 128, 0, st>>>(lv, sb);
 }
 
 unsigned links_blocks(const LatticeView &lv) { return nblk(lv.N, 256); }

@@ -89,15 +89,20 @@ __device__ __forceinline__ unsigned src_slot(int r, unsigned N, unsigned n, cons
   return (unsigned)D::opp(r) * N + xo[1 - D::cx(r)] + yo[1 - D::cy(r)] + zo[1 - D::cz(r)];
 }
 
-// the primary link record a node hands to the warp-level append (cell p < 0:
-// no cell link): its direction mask and the six values of the record, the
-// density deviation drho and, at tau = 1, the node's u, uu and u . F, from
-// which the link sums rebuild the bounced populations, else the sum of
-// 2 f~*_r c_r over the mask (two zeros after it)
+// the link records a node hands to the warp-level append: that of its first
+// cell p (p < 0: no cell link) with its direction mask and the six values of
+// the record, the density deviation drho and, at tau = 1, the node's u, uu
+// and u . F, from which the link sums rebuild the bounced populations, else
+// the sum of 2 f~*_r c_r over the mask (two zeros after it); and that of a
+// second cell p2 (p2 < 0: none), with its own mask and, at tau != 1, its own
+// sums f2 (at tau = 1 it shares the values)
 struct CellLink {
   int p;
   uint32_t mask;
   float e[6];
+  int p2;
+  uint32_t mask2;
+  float f2[3];
 };
 
 // warp-level append of the lanes' primary link records to their cells'
@@ -109,13 +114,16 @@ struct LinkSlot {
   int base;
 };
 
-__device__ __forceinline__ LinkSlot reserve_links(const LatticeView &lv, const CellLink &cl) {
+__device__ __forceinline__ LinkSlot reserve_slots(const LatticeView &lv, int p) {
   const unsigned FULL = 0xffffffffu;
   LinkSlot sl{0u, 0};
-  if (!__ballot_sync(FULL, cl.p >= 0)) return sl;
-  sl.grp = __match_any_sync(FULL, cl.p);
-  if (cl.p >= 0 && (threadIdx.x & 31) == __ffs(sl.grp) - 1) sl.base = atomicAdd(&lv.rec_count[cl.p], __popc(sl.grp));
+  if (!__ballot_sync(FULL, p >= 0)) return sl;
+  sl.grp = __match_any_sync(FULL, p);
+  if (p >= 0 && (threadIdx.x & 31) == __ffs(sl.grp) - 1) sl.base = atomicAdd(&lv.rec_count[p], __popc(sl.grp));
   return sl;
+}
+__device__ __forceinline__ LinkSlot reserve_links(const LatticeView &lv, const CellLink &cl) {
+  return reserve_slots(lv, cl.p);
 }
 
 __device__ __forceinline__ void write_links(const LatticeView &lv, const CellLink &cl, unsigned n, const LinkSlot &sl) {
@@ -132,9 +140,44 @@ __device__ __forceinline__ void write_links(const LatticeView &lv, const CellLin
   }
 }
 
+// the second-cell record of this lane to its reserved slot, marked for C in
+// place after the solve
+template <bool TAU1>
+__device__ __forceinline__ void write_second(const LatticeView &lv, const CellLink &cl, unsigned n,
+                                             const LinkSlot &sl) {
+  if (cl.p2 < 0) return;
+  const int lane = threadIdx.x & 31;
+  const int base = __shfl_sync(sl.grp, sl.base, __ffs(sl.grp) - 1);
+  const int pos = base + __popc(sl.grp & ((1u << lane) - 1u));
+  if (pos < lv.rec_cap) {
+    float4 *r = lv.rec + 2 * ((size_t)cl.p2 * lv.rec_cap + pos);
+    if constexpr (TAU1) {
+      r[0] = make_float4(__uint_as_float(n), __uint_as_float(cl.mask2 | REC_DIRECT), cl.e[0], cl.e[1]);
+      r[1] = make_float4(cl.e[2], cl.e[3], cl.e[4], cl.e[5]);
+    } else {
+      r[0] = make_float4(__uint_as_float(n), __uint_as_float(cl.mask2 | REC_DIRECT), cl.e[0], cl.f2[0]);
+      r[1] = make_float4(cl.f2[1], cl.f2[2], 0.f, 0.f);
+    }
+  } else {
+    atomicOr(lv.status, ST_OVERFLOW);
+  }
+}
+
+// both records of the lanes (all 32 lanes call it): the two warp-level
+// reservations in flight together, then the writes
+template <bool TAU1>
 __device__ __forceinline__ void emit_links(const LatticeView &lv, const CellLink &cl, unsigned n) {
-  const LinkSlot sl = reserve_links(lv, cl);
+  const LinkSlot sl = reserve_slots(lv, cl.p);
+  const LinkSlot sl2 = reserve_slots(lv, cl.p2);
   write_links(lv, cl, n, sl);
+  write_second<TAU1>(lv, cl, n, sl2);
+}
+
+// the second-cell records alone (kernels that write the first ones later)
+template <bool TAU1>
+__device__ __forceinline__ void emit_second(const LatticeView &lv, const CellLink &cl, unsigned n) {
+  const LinkSlot sl2 = reserve_slots(lv, cl.p2);
+  write_second<TAU1>(lv, cl, n, sl2);
 }
 
 // the neighbour n + c_r for a direction r known only at run time: the
@@ -222,6 +265,7 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
   const unsigned N = lv.N;
   S *pop = reinterpret_cast<S *>(lv.pop);
   cl.p = -1;
+  cl.p2 = -1;
   if (nbw & NB_FLUID) {
     const unsigned solid = nbw & NB_SOLID;
     // incoming populations of this node (layout of the step's parity)
@@ -381,15 +425,9 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
           cl.e[4] = cl.e[5] = 0.f;
         }
         if (cmask2) {
-          float e[6] = {drho, cl.e[1], cl.e[2], cl.e[3], cl.e[4], cl.e[5]};
-          if constexpr (!TAU1) {
-            float F[3];
-            link_sum(cmask2, f, F);
-            e[1] = F[0];
-            e[2] = F[1];
-            e[3] = F[2];
-          }
-          append_link(lv, n, p2, cmask2 | REC_DIRECT, e);
+          cl.p2 = p2;
+          cl.mask2 = cmask2;
+          if constexpr (!TAU1) link_sum(cmask2, f, cl.f2);
         }
         if (csec) {
           sfor<1, Q>([&](auto R) {
@@ -452,13 +490,14 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, Wal
   int wK[3] = {0, 0, 0};
   CellLink cl;
   cl.p = -1;
+  cl.p2 = -1;
   if (nbw & NB_FLUID) {
     const int xyz[3] = {x, y, z};
     node_update<S, PAR, FORCE, TAU1>(lv, wa, n, xyz, xo, yo, zo, nbw, lv.nbc[n], lv.pu[n],
                                      [&](int, unsigned slot) { return Store<S>::ld(pop + slot); }, wkey, wF, wK,
                                      cl);
   }
-  emit_links(lv, cl, n);
+  emit_links<TAU1>(lv, cl, n);
   flush_wall_momentum(wa, wkey, wF, wK);
 }
 
@@ -536,6 +575,7 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv
     const int b = i % PIPE_ST;
     CellLink cl;
     cl.p = -1;
+    cl.p2 = -1;
     unsigned zo[3];
     zoff(z, zo);
     if (w[0] & NB_FLUID) {
@@ -544,7 +584,7 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv
                                            lv.pu[rowb + zo[1]],
                                            [&](int r, unsigned) { return stage[b][r][tx]; }, wkey, wF, wK, cl);
     }
-    emit_links(lv, cl, rowb + zo[1]);
+    emit_links<TAU1>(lv, cl, rowb + zo[1]);
 #pragma unroll
     for (int k = 0; k < PIPE_ST - 1; ++k) w[k] = w[k + 1];
   }
@@ -668,6 +708,7 @@ __global__ void __launch_bounds__(128, BL_BULK_MINB) k_lb_step_bulk(LatticeView 
     const unsigned n = (unsigned)x + yo[1] + zo[1];
     CellLink cl;
     cl.p = -1;
+    cl.p2 = -1;
     if (w & NB_FLUID) {
       const int xyz[3] = {x, y, z};
       node_update<S, PAR, FORCE, TAU1>(
@@ -681,8 +722,10 @@ __global__ void __launch_bounds__(128, BL_BULK_MINB) k_lb_step_bulk(LatticeView 
           wkey, wF, wK, cl);
     }
     const LinkSlot sl = reserve_links(lv, cl);
-    __syncthreads();  // stage s is read: free for refill (the atomic's round trip overlaps it)
+    const LinkSlot sl2 = reserve_slots(lv, cl.p2);
+    __syncthreads();  // stage s is read: free for refill (the atomics' round trip overlaps it)
     write_links(lv, cl, n, sl);
+    write_second<TAU1>(lv, cl, n, sl2);
   }
   if (z < ze && tx == 0) {
     // gave up: let the copies still in flight land before the block exits
@@ -827,6 +870,7 @@ __global__ void __launch_bounds__(128, BL_ROWS_MINB) k_lb_step_rows(LatticeView 
     const unsigned n = (unsigned)x + yo[1] + zo[1];
     CellLink cl;
     cl.p = -1;
+    cl.p2 = -1;
     if (w & NB_FLUID) {
       const int xyz[3] = {x, g.y, g.z};
       const int W = g.W;
@@ -843,6 +887,7 @@ __global__ void __launch_bounds__(128, BL_ROWS_MINB) k_lb_step_rows(LatticeView 
     // the last row's records to the slots reserved then; this row's slots
     // reserved now, its records staged
     write_staged(lv, lp, lgrp, lbase, srec[0][tx], srec[1][tx]);
+    emit_second<TAU1>(lv, cl, n);
     const LinkSlot sl = reserve_links(lv, cl);
     if (cl.p >= 0) {
       srec[0][tx] = make_float4(__uint_as_float(n), __uint_as_float(cl.mask), cl.e[0], cl.e[1]);

@@ -260,8 +260,8 @@ __device__ __forceinline__ int bin_offsets(int nb, int per, int b, int out[3]) {
 
 constexpr int CB = 256;
 
-// sums v over the block; the result is valid in thread 0
-template <int K>
+// sums v over a block of NT threads; the result is valid in thread 0
+template <int K, int NT = CB>
 __device__ __forceinline__ void block_sum(float (&v)[K], float (*sh)[K]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -271,7 +271,7 @@ __device__ __forceinline__ void block_sum(float (&v)[K], float (*sh)[K]) {
     for (int k = 0; k < K; ++k) sh[wid][k] = v[k];
   __syncthreads();
   if (threadIdx.x == 0)
-    for (int w = 1; w < CB / 32; ++w)
+    for (int w = 1; w < NT / 32; ++w)
 #pragma unroll
       for (int k = 0; k < K; ++k) v[k] += sh[w][k];
   __syncthreads();
@@ -394,9 +394,29 @@ __device__ __forceinline__ unsigned bounce_slot(const LatticeView &lv, int par, 
 // neighbouring bin), all threads take the rows (y, z) of the wall-sphere
 // range around the cell.
 
-__global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, CellListView cl, SurfBits sb) {
-  __shared__ float sh[CB / 32][6];
+constexpr int FB = 128;        // threads of a potentials block
+constexpr int FQ_PAIR = 128;   // per-cell queue of pairs within contact reach
+constexpr int FQ_WALL = 1024;  // per-cell queue of surface wall nodes within reach
+
+// One block per cell.  The search runs in FP32 and queues what can be in
+// contact: the cells j of the 27 bins around cell i within the largest
+// contact distance (one thread per bin), and the surface wall nodes within
+// the wall sphere's radius (rows without a surface wall node skipped by
+// their row bit).  The queued pairs and wall nodes then get the FP64 contact
+// geometry with one queue entry per thread, so that the few contacts of a
+// cell share the FP64 instructions instead of each taking a pass of its own.
+// A full queue evaluates the rest where they are found.
+__global__ void __launch_bounds__(FB, 7) k_forces(LatticeView lv, PartView pv, CellListView cl, SurfBits sb) {
+  __shared__ float sh[FB / 32][6];
+  __shared__ int s_np, s_nw;
+  __shared__ int s_pair[FQ_PAIR];
+  __shared__ unsigned s_wall[FQ_WALL];
   const int i = blockIdx.x;
+  if (threadIdx.x == 0) {
+    s_np = 0;
+    s_nw = 0;
+  }
+  __syncthreads();
   const float4 a0 = pv.kin[3 * i], a1 = pv.kin[3 * i + 1], a2 = pv.kin[3 * i + 2];
   const int Xi[3] = {(int)a0.w, (int)a1.w, (int)a2.w};
   const float fi[3] = {a0.x, a0.y, a0.z};
@@ -407,6 +427,18 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
   const float oif[3] = {(float)oid[0], (float)oid[1], (float)oid[2]};
   const int dims[3] = {lv.nx, lv.ny, lv.nz};
   float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+  auto pair_force = [&](int j) {
+    double rd[3];
+    for (int m = 0; m < 3; ++m) rd[m] = min_image_exact(__dsub_rn(pv.X[3 * j + m], Xd[m]), dims[m], lv.per[m]);
+    const double ojd[3] = {pv.o[3 * j], pv.o[3 * j + 1], pv.o[3 * j + 2]};
+    bp_pair(rd, oid, ojd, pv, F, T);
+  };
+  // the wall node at offsets (dx, oy, oz) from rint(X); queued packed in
+  // 3 x 10 bits (offsets within +-511, else evaluated where found)
+  auto wall_force = [&](int dx, int oy, int oz) {
+    const double rd[3] = {(double)dx - fd[0], (double)oy - fd[1], (double)oz - fd[2]};
+    bp_wall(rd, oid, pv, F, T);
+  };
   if (threadIdx.x < 27) {
     const int bin = cl.bin_of[i];
     const int bc[3] = {bin % cl.nb[0], (bin / cl.nb[0]) % cl.nb[1], bin / (cl.nb[0] * cl.nb[1])};
@@ -438,10 +470,9 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
         if (r2 >= rc2 || r2 > smax2) continue;
         const float oj[3] = {(float)pv.o[3 * j], (float)pv.o[3 * j + 1], (float)pv.o[3 * j + 2]};
         if (!near_contact(r, r2, oif, oj, pv)) continue;
-        double rd[3];
-        for (int m = 0; m < 3; ++m) rd[m] = min_image_exact(__dsub_rn(pv.X[3 * j + m], Xd[m]), dims[m], lv.per[m]);
-        const double ojd[3] = {pv.o[3 * j], pv.o[3 * j + 1], pv.o[3 * j + 2]};
-        bp_pair(rd, oid, ojd, pv, F, T);
+        const int q = atomicAdd(&s_np, 1);
+        if (q < FQ_PAIR) s_pair[q] = j;
+        else pair_force(j);
       }
     }
   }
@@ -449,7 +480,8 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
     const int R = (int)ceilf(pv.sigw_max) + 1;
     const int side = 2 * R + 1;
     const float rw2 = pv.sigw_max * pv.sigw_max;
-    for (int t = threadIdx.x; t < side * side; t += CB) {
+    const bool packable = R <= 511;
+    for (int t = threadIdx.x; t < side * side; t += FB) {
       const int oy = t % side - R, oz = t / side - R;  // node offsets from rint(X)
       int y = Xi[1] + oy, z = Xi[2] + oz;
       const float ry = (float)oy - fi[1], rz = (float)oz - fi[2];
@@ -458,7 +490,9 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
       else if (y < 0 || y >= lv.ny) continue;
       if (lv.per[2]) z = wrapi(z, lv.nz);
       else if (z < 0 || z >= lv.nz) continue;
-      const uint32_t *row = sb.bits + (size_t)(y + lv.ny * z) * sb.nxw;
+      const unsigned ri = (unsigned)y + (unsigned)lv.ny * (unsigned)z;
+      if (!((sb.rows[ri >> 5] >> (ri & 31)) & 1u)) continue;  // no surface wall node in the row
+      const uint32_t *row = sb.bits + (size_t)ri * sb.nxw;
       for (int dx = -R; dx <= R; ++dx) {
         int x = Xi[0] + dx;
         if (lv.per[0]) x = wrapi(x, lv.nx);
@@ -469,13 +503,22 @@ __global__ void __launch_bounds__(CB) k_forces(LatticeView lv, PartView pv, Cell
         const float r2 = rx * rx + ry * ry + rz * rz;
         const float af = rx * oif[0] + ry * oif[1] + rz * oif[2];
         if (!(r2 > 0.f) || (r2 - pv.chi_w * af * af) >= pv.sigbar_w * pv.sigbar_w * 1.0002f) continue;
-        const double rd[3] = {(double)dx - fd[0], (double)oy - fd[1], (double)oz - fd[2]};
-        bp_wall(rd, oid, pv, F, T);
+        const int q = packable ? atomicAdd(&s_nw, 1) : FQ_WALL;
+        if (q < FQ_WALL) s_wall[q] = (unsigned)(dx + 512) | ((unsigned)(oy + 512) << 10) | ((unsigned)(oz + 512) << 20);
+        else wall_force(dx, oy, oz);
       }
     }
   }
+  __syncthreads();
+  // the queued contacts, one per thread
+  const int np = min(s_np, FQ_PAIR), nw = min(s_nw, FQ_WALL);
+  for (int k = threadIdx.x; k < np; k += FB) pair_force(s_pair[k]);
+  for (int k = threadIdx.x; k < nw; k += FB) {
+    const unsigned w = s_wall[k];
+    wall_force((int)(w & 1023u) - 512, (int)((w >> 10) & 1023u) - 512, (int)(w >> 20) - 512);
+  }
   float v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
-  block_sum<6>(v, sh);
+  block_sum<6, FB>(v, sh);
   if (threadIdx.x == 0)
     for (int m = 0; m < 3; ++m) {
       pv.Fpot[3 * i + m] = (double)v[m];
@@ -1745,7 +1788,7 @@ void launch_cell_list(const LatticeView &lv, const PartView &pv, const CellListV
 void launch_forces(const LatticeView &lv, const PartView &pv, const CellListView &cl, const SurfBits &sb,
                    cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  k_forces<<<pv.n, CB, 0, st>>>(lv, pv, cl, sb);
+  k_forces<<<pv.n, FB, 0, st>>>(lv, pv, cl, sb);
   *nl += 1;
 }
 

@@ -126,7 +126,9 @@ constexpr uint32_t REC_DIRECT = 1u << 31;
 
 // neighbour word of a node: bit 0 the node is fluid; bit r (1..18) the
 // neighbour x + c_r is solid; NB_WALL some solid neighbour is a wall node;
-// NB_CELL some solid neighbour is a cell node.  Zero for solid nodes.
+// NB_CELL some solid neighbour is a cell node.  For a cell node (bit 0
+// clear) bit r marks a contact link: the neighbour x + c_r is a wall node or
+// a node of another cell.  Zero for wall nodes.
 constexpr uint32_t NB_FLUID = 1u;
 constexpr uint32_t NB_SOLID = 0x7FFFEu;
 constexpr uint32_t NB_WALL = 1u << 19;

@@ -65,8 +65,8 @@ __global__ void __launch_bounds__(128) k_geometry(LatticeView lv, PartView pv) {
       lv.nbm[n] = NB_FLUID | solid | (wall ? NB_WALL : 0u) | ((solid & ~wall) ? NB_CELL : 0u);
       lv.nbc[n] = (first >= 0 && !mixed) ? (uint32_t)first : NBC_MIXED;
     } else {
-      lv.nbm[n] = 0u;
       cmask = solid & ~same;  // other cells and walls
+      lv.nbm[n] = cmask;
     }
   } else if (valid) {
     lv.nbm[n] = 0u;

@@ -1501,10 +1501,21 @@ __device__ __forceinline__ uint32_t node_word(const LatticeView &lv, int x, int 
   using D = D3Q19;
   const unsigned nx = (unsigned)lv.nx, nxy = (unsigned)lv.nx * (unsigned)lv.ny;
   cellw = NBC_MIXED;
-  if (lv.owner[(unsigned)x + nx * (unsigned)y + nxy * (unsigned)z] != FLUID) return 0u;
+  const int own = lv.owner[(unsigned)x + nx * (unsigned)y + nxy * (unsigned)z];
+  if (own <= -2) return 0u;  // wall node
   const int xs[3] = {x == 0 ? lv.nx - 1 : x - 1, x, x == lv.nx - 1 ? 0 : x + 1};
   const int ys[3] = {y == 0 ? lv.ny - 1 : y - 1, y, y == lv.ny - 1 ? 0 : y + 1};
   const int zs[3] = {z == 0 ? lv.nz - 1 : z - 1, z, z == lv.nz - 1 ? 0 : z + 1};
+  if (own != FLUID) {
+    // cell node: its contact links (neighbours owned by a wall or another cell)
+    unsigned cmask = 0;
+    sfor<1, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      const int on = lv.owner[(unsigned)xs[1 + D::cx(r)] + nx * (unsigned)ys[1 + D::cy(r)] + nxy * (unsigned)zs[1 + D::cz(r)]];
+      cmask |= (on != FLUID && on != own ? 1u : 0u) << r;
+    });
+    return cmask;
+  }
   unsigned solid = 0, wall = 0;
   int first = -1;
   bool mixed = false;
@@ -1607,17 +1618,10 @@ __global__ void __launch_bounds__(LB) k_contacts(LatticeView lv, PartView pv) {
       int x = g.Xi[0] + s_x0[lo] + (k - s_off[lo]);
       if (lv.per[0]) x = wrapi(x, lv.nx);
       const int yy = s_y[lo], zz = s_z[lo];
-      if (lv.owner[(unsigned)x + nx * (unsigned)yy + nxy * (unsigned)zz] != p) continue;
-      const int xs[3] = {x == 0 ? lv.nx - 1 : x - 1, x, x == lv.nx - 1 ? 0 : x + 1};
-      const int ys[3] = {yy == 0 ? lv.ny - 1 : yy - 1, yy, yy == lv.ny - 1 ? 0 : yy + 1};
-      const int zs[3] = {zz == 0 ? lv.nz - 1 : zz - 1, zz, zz == lv.nz - 1 ? 0 : zz + 1};
-      unsigned cmask = 0;
-      sfor<1, Q>([&](auto R) {
-        constexpr int r = decltype(R)::value;
-        const int on =
-            lv.owner[(unsigned)xs[1 + D::cx(r)] + nx * (unsigned)ys[1 + D::cy(r)] + nxy * (unsigned)zs[1 + D::cz(r)]];
-        cmask |= (on != FLUID && on != p ? 1u : 0u) << r;  // another cell or a wall
-      });
+      const unsigned nn = (unsigned)x + nx * (unsigned)yy + nxy * (unsigned)zz;
+      if (lv.owner[nn] != p) continue;
+      // the node's contact links, kept in its neighbour word by the geometry passes
+      const unsigned cmask = lv.nbm[nn] & NB_SOLID;
       if (cmask) {
         const int di[3] = {imin_image(x - Xk[0], lv.nx, lv.per[0]), imin_image(yy - Xk[1], lv.ny, lv.per[1]),
                            imin_image(zz - Xk[2], lv.nz, lv.per[2])};

@@ -230,7 +230,7 @@ def make_workload(name):
 # workload at FP32 storage kept with the profiles, valid for the sweep source
 # it was taken on (lb_sweep.cuh, first 16 hex digits of its SHA-256) and that
 # workload only
-SWEEP_TRAFFIC = {"sha": "ad506e7e2729c60d", "config": "shear128", "store": 0, "bytes": 271938944}
+SWEEP_TRAFFIC = {"sha": "bef56a5f69834f1b", "config": "shear128", "store": 0, "bytes": 354465152}
 
 
 SWEEP_KERNELS = {
@@ -363,7 +363,8 @@ def run_gpu(args, ws, rank, local):
                      "step_frac": round(bytes_per / (ms_max / args.steps * 1e-3) / 1e9 / hbm, 4)},
         "kernel_time_share": group_share,
         "instrumented": {"steps": k_inst, "ms_per_step": round(ms_inst / k_inst, 5),
-                         "note": "per-kernel CUDA events, no graph replay; roofline and shares from this run"},
+                         "note": "per-kernel CUDA events, no graph replay, the sweep timed alone (the side "
+                                 "streams start when it ends); roofline and shares from this run"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": e2e,

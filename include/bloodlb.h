@@ -303,13 +303,16 @@ int bl_pair_features(bl_ctx *c, const int32_t *pairs, int n, float *out);
 
 /* Kernel timing with CUDA events.  While enabled, steps are enqueued one
    kernel group at a time (no graph), each group bracketed by an event pair
-   on the stream it runs on.  Groups: 0 fused collide/stream/bounce-back
-   (the lattice sweep), 1 cell list, 2 pair + wall potentials (1 and 2 on
-   the second stream, beside the sweep), 3 link sums + half-step solve +
-   leap-frog + moving-boundary correction, 4 claims + resolve with
-   fill/drain + geometry pass.  bl_timing_read waits, then writes per group
-   the summed milliseconds and the number of timed launches (arrays of
-   ngroups), and clears the sums. */
+   on the stream it runs on, and the lattice sweep runs alone: the side
+   streams start when it ends (in a replayed graph they run beside it), so
+   that its time is the kernel's own.  Groups: 0 fused
+   collide/stream/bounce-back with the cell-link records (the lattice
+   sweep), 1 cell list, 2 pair + wall potentials (1 and 2 on a side
+   stream), 3 link sums + half-step solve + leap-frog + claims + pending
+   moving-boundary term, 4 contact sums (second side stream) + resolve with
+   fill/drain + neighbour words.  bl_timing_read waits, then writes per
+   group the summed milliseconds and the number of timed launches (arrays
+   of ngroups), and clears the sums. */
 int bl_timing_enable(bl_ctx *c, int enable);
 int bl_timing_read(bl_ctx *c, double *ms, int64_t *count, int ngroups);
 

@@ -564,7 +564,7 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
   // re-placement only around the nodes resolve changed (every step starts by
   // building the link lists and contact sums of the current owner map)
   if (first) launch_geometry(c->lv, c->pv, c->stream, &c->launches);
-  else launch_nbm_update(c->lv, c->pv, c->chg, c->stream, &c->launches);
+  else launch_nbm_update(c->dtype, c->lv, c->pv, c->chg, c->parity, c->stream, &c->launches);
   std::swap(c->pv.kin, c->pv.kin_next);
   if (check_launch(c, "particles_set")) return c->sticky;
   // a first placement waits (device errors surface here); a re-placement
@@ -635,7 +635,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     cudaStreamWaitEvent(st, c->ev_join2, 0);
     group_begin(c, 4, &slot, st);
     launch_resolve_fill(c->dtype, c->lv, c->pv, c->cl, c->claim, c->chg, c->parity ^ 1, 1, st, &c->launches);
-    launch_nbm_update(c->lv, c->pv, c->chg, st, &c->launches);
+    launch_nbm_update(c->dtype, c->lv, c->pv, c->chg, c->parity ^ 1, st, &c->launches);
     group_end(c, slot, st);
     std::swap(c->pv.kin, c->pv.kin_next);
   }

@@ -493,7 +493,12 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, Wal
   cl.p2 = -1;
   if (nbw & NB_FLUID) {
     const int xyz[3] = {x, y, z};
-    node_update<S, PAR, FORCE, TAU1>(lv, wa, n, xyz, xo, yo, zo, nbw, lv.nbc[n], lv.pu[n],
+    // the neighbour-cell word and the pending velocity matter only next to a
+    // cell (a node that lost its last cell neighbour had its pending C
+    // flushed by the neighbour-word update)
+    const bool near = (nbw & NB_CELL) != 0;
+    node_update<S, PAR, FORCE, TAU1>(lv, wa, n, xyz, xo, yo, zo, nbw, near ? lv.nbc[n] : NBC_MIXED,
+                                     near ? lv.pu[n] : make_float4(0.f, 0.f, 0.f, 0.f),
                                      [&](int, unsigned slot) { return Store<S>::ld(pop + slot); }, wkey, wF, wK,
                                      cl);
   }
@@ -580,8 +585,10 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step_pipe(LatticeView lv
     zoff(z, zo);
     if (w[0] & NB_FLUID) {
       const int xyz[3] = {x, y, z};
-      node_update<float, PAR, FORCE, TAU1>(lv, wa, rowb + zo[1], xyz, xo, yo, zo, w[0], lv.nbc[rowb + zo[1]],
-                                           lv.pu[rowb + zo[1]],
+      const bool near = (w[0] & NB_CELL) != 0;
+      node_update<float, PAR, FORCE, TAU1>(lv, wa, rowb + zo[1], xyz, xo, yo, zo, w[0],
+                                           near ? lv.nbc[rowb + zo[1]] : NBC_MIXED,
+                                           near ? lv.pu[rowb + zo[1]] : make_float4(0.f, 0.f, 0.f, 0.f),
                                            [&](int r, unsigned) { return stage[b][r][tx]; }, wkey, wF, wK, cl);
     }
     emit_links<TAU1>(lv, cl, rowb + zo[1]);

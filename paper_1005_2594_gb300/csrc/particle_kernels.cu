@@ -1534,8 +1534,13 @@ __device__ __forceinline__ uint32_t node_word(const LatticeView &lv, int x, int 
 }
 
 // neighbour words of every changed node x and of the nodes x - c_r that see
-// it; the whole lattice if the change list overflowed (grid-stride)
-__global__ void k_nbm_update(LatticeView lv, ChangeList chg) {
+// it; the whole lattice if the change list overflowed (grid-stride).  A fluid
+// node left with no cell neighbour gets its pending C now (the sweep reads
+// the pending velocity only next to a cell); par_next is the layout of the
+// stored populations.  A node can be visited by several threads: the one
+// that takes the pending mask (atomic exchange) applies it.
+template <class S>
+__global__ void k_nbm_update(LatticeView lv, ChangeList chg, int par_next) {
   using D = D3Q19;
   const int cnt = *chg.count;
   const bool all = cnt > chg.cap;
@@ -1554,8 +1559,24 @@ __global__ void k_nbm_update(LatticeView lv, ChangeList chg) {
     }
     uint32_t cw;
     const unsigned nn = node_of(lv, xyz[0], xyz[1], xyz[2]);
-    lv.nbm[nn] = node_word(lv, xyz[0], xyz[1], xyz[2], cw);
+    const uint32_t w = node_word(lv, xyz[0], xyz[1], xyz[2], cw);
+    lv.nbm[nn] = w;
     lv.nbc[nn] = cw;
+    if ((w & NB_FLUID) && !(w & NB_CELL)) {
+      const uint32_t pm = atomicExch(reinterpret_cast<unsigned *>(lv.pu + nn) + 3, 0u);
+      if (pm) {
+        const float4 pu = lv.pu[nn];
+        S *pop = reinterpret_cast<S *>(lv.pop);
+        for (uint32_t m = pm; m; m &= m - 1u) {
+          const int r = __ffs(m) - 1;
+          const float C = -((float)rt_m(r) / 6.0f) *
+                          ((float)rt_c<0>(r) * pu.x + (float)rt_c<1>(r) * pu.y + (float)rt_c<2>(r) * pu.z);
+          // the slot from which node nn reads direction rbar in layout par_next
+          const unsigned slot = bounce_slot(lv, par_next ^ 1, nn, xyz, r);
+          Store<S>::st(pop + slot, Store<S>::ld(pop + slot) + C);
+        }
+      }
+    }
   }
 }
 
@@ -1851,10 +1872,12 @@ void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const 
   *nl += 1;
 }
 
-void launch_nbm_update(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
-                       int64_t *nl) {
+void launch_nbm_update(int dtype, const LatticeView &lv, const PartView &pv, const ChangeList &chg, int par_next,
+                       cudaStream_t st, int64_t *nl) {
   if (pv.n == 0) return;
-  k_nbm_update<<<4 * 152, 256, 0, st>>>(lv, chg);
+  if (dtype == 0) k_nbm_update<float><<<4 * 152, 256, 0, st>>>(lv, chg, par_next);
+  else if (dtype == 1) k_nbm_update<__nv_bfloat16><<<4 * 152, 256, 0, st>>>(lv, chg, par_next);
+  else k_nbm_update<__half><<<4 * 152, 256, 0, st>>>(lv, chg, par_next);
   *nl += 1;
 }
 

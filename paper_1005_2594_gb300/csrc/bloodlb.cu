@@ -512,8 +512,14 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
       if (c->lv.per[k] && !((double)dims[k] >= 2.0 * rmax + 4.0))
         return fail(c, BL_EINVAL, "periodic length %d < 2 max(R) + 4", dims[k]);
   }
-  if (flush_pending(c)) return c->sticky;
   const bool first = n != c->np || c->np == 0;
+  // a new set of cells clears the old cells and rebuilds the geometry, which
+  // drops pending terms: they go to the populations first.  A re-placement
+  // keeps them: fluid that stays fluid gets its term in the next sweep, the
+  // resolve counts that of fluid it covers in the impulses, and the
+  // neighbour-word update gives a node that loses its last cell neighbour
+  // its term
+  if (first && flush_pending(c)) return c->sticky;
   // the graphs hold the cell arrays' pointers and the cell constants by
   // value: they stay valid for a re-placement with the same arrays and
   // parameters (their keys, parity and kinematics buffer, are checked)

@@ -829,7 +829,7 @@ __global__ void __launch_bounds__(LT, BL_REDUCE_MINB) k_link_reduce(LatticeView 
 __global__ void k_solve(LatticeView lv, PartView pv) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pv.n) return;
-  const float4 k0 = pv.kin[3 * p], k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
+  const float4 k1 = pv.kin[3 * p + 1], k2 = pv.kin[3 * p + 2];
   double X[3], q[4], V[3], L[3], W[3], Xold[3], o_old[3];
   for (int k = 0; k < 3; ++k) {
     X[k] = pv.X[3 * p + k];
@@ -1405,16 +1405,14 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
       chg.items[3 * pos + 1] = old;
       chg.items[3 * pos + 2] = nw;
     }
-    unsigned slot[Q];
-    for (int r = 0; r < Q; ++r) {
-      if (par_next == 0 || r == 0) {
-        slot[r] = (unsigned)r * lv.N + idx;
-      } else {
-        slot[r] = (unsigned)D::opp(r) * lv.N +
-                  node_of(lv, wrapi(xyz[0] - D::cx(r), lv.nx), wrapi(xyz[1] - D::cy(r), lv.ny),
-                          wrapi(xyz[2] - D::cz(r), lv.nz));
-      }
-    }
+    // the slot from which the node reads direction r in layout par_next (the
+    // loops over r below stay rolled: this path is rare, and its code stays
+    // small enough for the instruction cache)
+    auto slot_of = [&](int r) -> unsigned {
+      if (par_next == 0 || r == 0) return (unsigned)r * lv.N + idx;
+      return (unsigned)rt_opp(r) * lv.N + node_of(lv, wrapi(xyz[0] - rt_c<0>(r), lv.nx),
+                                                  wrapi(xyz[1] - rt_c<1>(r), lv.ny), wrapi(xyz[2] - rt_c<2>(r), lv.nz));
+    };
     double arm_o[3] = {0, 0, 0}, arm_n[3] = {0, 0, 0};
     float u_o[3] = {0.f, 0.f, 0.f};
     if (old >= 0) {
@@ -1436,20 +1434,22 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
       const uint32_t pm = __float_as_uint(pu.w);
       if (impulses) {
         float mf[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
         for (int r = 0; r < Q; ++r) {
-          const float v = Store<S>::ld(pop + slot[r]);
-          mf[0] += v * D::cx(r);
-          mf[1] += v * D::cy(r);
-          mf[2] += v * D::cz(r);
+          const float v = Store<S>::ld(pop + slot_of(r));
+          mf[0] += v * (float)rt_c<0>(r);
+          mf[1] += v * (float)rt_c<1>(r);
+          mf[2] += v * (float)rt_c<2>(r);
         }
         // C_r owed to direction rbar: momentum -C_r c_r (the links to a second
         // or third cell got theirs in place)
         for (uint32_t m = pm; m; m &= m - 1u) {
           const int r = __ffs(m) - 1;
-          const float C = -(D::m(r) / 6.0f) * (D::cx(r) * pu.x + D::cy(r) * pu.y + D::cz(r) * pu.z);
-          mf[0] -= C * D::cx(r);
-          mf[1] -= C * D::cy(r);
-          mf[2] -= C * D::cz(r);
+          const float cx = (float)rt_c<0>(r), cy = (float)rt_c<1>(r), cz = (float)rt_c<2>(r);
+          const float C = -((float)rt_m(r) / 6.0f) * (cx * pu.x + cy * pu.y + cz * pu.z);
+          mf[0] -= C * cx;
+          mf[1] -= C * cy;
+          mf[2] -= C * cz;
         }
         const double mom[3] = {mf[0], mf[1], mf[2]};
         const double tq[3] = {arm_n[1] * mom[2] - arm_n[2] * mom[1], arm_n[2] * mom[0] - arm_n[0] * mom[2],
@@ -1469,10 +1469,11 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
         // uncovered: new fluid at n^eq(rho_bar, u_rigid), stored shifted
         const float rho0 = (float)pv.rho0;
         const float uu = u_o[0] * u_o[0] + u_o[1] * u_o[1] + u_o[2] * u_o[2];
+#pragma unroll 1
         for (int r = 0; r < Q; ++r) {
-          const float cu = D::cx(r) * u_o[0] + D::cy(r) * u_o[1] + D::cz(r) * u_o[2];
-          const float w = D::m(r) / 36.0f;
-          Store<S>::st(pop + slot[r], rho0 * w * (cu * (3.0f + cu * (4.5f + 4.5f * cu)) - uu * (1.5f + 4.5f * cu)));
+          const float cu = (float)rt_c<0>(r) * u_o[0] + (float)rt_c<1>(r) * u_o[1] + (float)rt_c<2>(r) * u_o[2];
+          const float w = (float)rt_m(r) / 36.0f;
+          Store<S>::st(pop + slot_of(r), rho0 * w * (cu * (3.0f + cu * (4.5f + 4.5f * cu)) - uu * (1.5f + 4.5f * cu)));
         }
       } else {
         // direct change of owner: uncover by the old, cover by the new (reading Q6)

@@ -19,9 +19,10 @@
  *   are borrowed for the duration of the call only.
  * Streams: every call of a context is ordered on the CUDA stream given to
  *   bl_lb_init (NULL = the legacy default stream).  Inside a step the cell
- *   list, the potentials and the link lists run on two more streams of the
- *   context beside the lattice sweep, and the claims beside the link
- *   correction; steps replay captured graphs on a fourth stream.  All are
+ *   list, the potentials and the contact sums run on two more streams of the
+ *   context (created at the highest priority) beside the lattice sweep, and
+ *   the claims beside the pending moving-boundary terms; steps replay
+ *   captured graphs on a fourth stream.  All are
  *   forked from and joined back to the caller's stream with events, so work
  *   the caller enqueues later still follows the step.  A context is not
  *   thread-safe; use one context per stream.
@@ -126,7 +127,12 @@ int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, const doubl
 /* Enqueues nsteps coupled time steps on the context stream (no host sync):
    collide + stream + bounce-back + momentum exchange + contact links, cell
    list, pair and wall potentials, leap-frog, re-discretisation with
-   fill/drain.  With timing off, pairs of steps are launched as one CUDA
+   fill/drain.  The moving-boundary term of the populations a step bounces
+   off cells is added when the next step reads them (Eqs. c, lbe-bb-corr
+   with the half-step cell velocity of the implicit coupling): between steps
+   it is held per fluid node, and every read-out of populations or fields
+   adds it first, so what the caller sees is the state after the whole step.
+   With timing off, pairs of steps are launched as one CUDA
    graph and a last single step as a one-step graph (captured on first use,
    and again when the cell arrays or parameters, the walls, the sweep variant
    or the attached network change).  Returns the sticky status known so far

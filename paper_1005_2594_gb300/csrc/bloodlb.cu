@@ -3,13 +3,14 @@
 // One context owns one lattice and its cells on one CUDA stream.  A time step
 // (arXiv:1005.2594, Sec. II and III) is enqueued as five kernel groups (the
 // groups of the timing read-out):
-//   0  fused collide / stream / bounce-back / wall momentum (the sweep)
+//   0  fused collide / stream / bounce-back / wall momentum / pending
+//      moving-boundary term / cell-link records (the sweep)
 //   1  cell list (count, scan, scatter, per-bin sort)
 //   2  pair and wall potentials (+ the learned correction)
-//   3  link sums, implicit solve + leap-frog, link correction, claims
-//   4  link lists and contact sums, resolve + fill/drain, neighbour words
-// Groups 1-2 and the link lists run on two side streams beside the sweep,
-// the claims beside the link correction.  The host never waits inside
+//   3  link sums, implicit solve + leap-frog, claims, pending terms
+//   4  contact sums, resolve + fill/drain, neighbour words
+// Groups 1-2 and the contact sums run on two side streams beside the sweep,
+// the claims beside the pending terms.  The host never waits inside
 // bl_step; device failures are raised into a status word that bl_sync reads.
 #include <math.h>
 #include <stdarg.h>
@@ -36,13 +37,13 @@ struct bl_ctx {
   bl_particle_params pp;
   cudaStream_t stream;  // the caller's stream: every call is ordered on it
   // the cell list and the potentials of a step run on a second stream, the
-  // link lists on a third, overlapped with the lattice sweep (they touch
-  // disjoint data); the claims run on the second beside the link correction
+  // contact sums on a third, overlapped with the lattice sweep (they touch
+  // disjoint data); the claims run on the second beside the pending terms
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;     // cell list and potentials beside the sweep
-  cudaEvent_t ev_fork2, ev_join2;   // claims beside the link correction
+  cudaEvent_t ev_fork2, ev_join2;   // claims beside the pending terms
   cudaStream_t side2;
-  cudaEvent_t ev_join3;             // link lists beside the sweep (second side stream)
+  cudaEvent_t ev_join3;             // contact sums beside the sweep (second side stream)
   // repeated steps replay a CUDA graph of two steps (even + odd parity), a
   // lone step a one-step graph, on an internal stream forked from and joined
   // to the caller's stream
@@ -568,7 +569,7 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
                       &c->launches);
   // neighbour words: the whole lattice after a first placement; after a
   // re-placement only around the nodes resolve changed (every step starts by
-  // building the link lists and contact sums of the current owner map)
+  // summing the contact links of the current owner map)
   if (first) launch_geometry(c->lv, c->pv, c->stream, &c->launches);
   else launch_nbm_update(c->dtype, c->lv, c->pv, c->chg, c->parity, c->stream, &c->launches);
   std::swap(c->pv.kin, c->pv.kin_next);
@@ -597,7 +598,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
   }
   if (c->np > 0) {
     // cell list and potentials from the state at t, beside the sweep; on a
-    // second side stream the link lists of the current owner map
+    // second side stream the contact sums of the current owner map
     cudaEventRecord(c->ev_fork, st);
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     cudaStreamWaitEvent(c->side2, c->ev_fork, 0);

@@ -1180,8 +1180,8 @@ constexpr int PB = 128;  // threads of the claims and resolve blocks (8 blocks f
 // mode 1: no old ellipsoid (first particles_set, all owners fluid).
 // In particles_set (modes 1, 2) also clears the cell's link count and
 // contact sums for the lattice-wide geometry pass, which adds to them; in a
-// step (mode 0) the link correction may still be reading them, and the
-// step's geometry rewrites them.
+// step (mode 0) the contact sums of this step are in use, and the next
+// step's contact kernel rewrites them.
 __global__ void __launch_bounds__(PB, BL_CLAIMS_MINB) k_claims(LatticeView lv, PartView pv, int *claim, ChangeList chg, int mode) {
   __shared__ int sh_len;
   const int p = blockIdx.x;
@@ -1489,15 +1489,16 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
 // ---------------------------------------------------------------------------
 // geometry of the step, incrementally.  After resolve, a node's neighbour
 // word can differ from the last one only if its own owner or a neighbour's
-// changed, and every change is in the change list; the link lists and
-// contact sums of a cell come from the nodes it owns, which lie inside its
-// ellipsoid at its current position (a cell owns only nodes it covers).
-// The link lists are built at the start of the next step, beside its sweep
-// (the sweep needs only the neighbour words), from the current kinematics.
+// changed, and every change is in the change list.  The contact sums of a
+// cell come from the nodes it owns, which lie inside its ellipsoid at its
+// current position (a cell owns only nodes it covers); they are summed at
+// the start of the next step, beside its sweep (the sweep needs only the
+// neighbour words).
 
-// neighbour word of node (x, y, z) from the owner map: bit 0 fluid, bit r
-// neighbour x + c_r solid, NB_WALL / NB_CELL some solid neighbour is a wall /
-// a cell; zero for solid nodes
+// neighbour word of node (x, y, z) from the owner map: for a fluid node bit 0,
+// bit r neighbour x + c_r solid, NB_WALL / NB_CELL some solid neighbour is a
+// wall / a cell; for a cell node its contact links (bit r: the neighbour is a
+// wall node or another cell's); zero for wall nodes
 __device__ __forceinline__ uint32_t node_word(const LatticeView &lv, int x, int y, int z, uint32_t &cellw) {
   using D = D3Q19;
   const unsigned nx = (unsigned)lv.nx, nxy = (unsigned)lv.nx * (unsigned)lv.ny;

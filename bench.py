@@ -230,7 +230,7 @@ def make_workload(name):
 # workload at FP32 storage kept with the profiles, valid for the sweep source
 # it was taken on (lb_sweep.cuh, first 16 hex digits of its SHA-256) and that
 # workload only
-SWEEP_TRAFFIC = {"sha": "bef56a5f69834f1b", "config": "shear128", "store": 0, "bytes": 354465152}
+SWEEP_TRAFFIC = {"sha": "e33ef13a0c31ee96", "config": "shear128", "store": 0, "bytes": 329916032}
 
 
 SWEEP_KERNELS = {

@@ -484,6 +484,21 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, Wal
                           (unsigned)(z == lv.nz - 1 ? 0 : z + 1) * nxy};
   const S *pop = reinterpret_cast<const S *>(lv.pop);
   const uint32_t nbw = valid ? lv.nbm[n] : 0u;
+  // the node's populations, neighbour-cell word and pending velocity are
+  // requested with its neighbour word, before it is known whether the node
+  // is fluid: one memory round trip per node instead of two (a solid node's
+  // values are discarded; every slot read lies in the population array)
+  float fin[Q];
+  uint32_t nbcv = NBC_MIXED;
+  float4 puv = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid) {
+    sfor<0, Q>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      fin[r] = Store<S>::ld(pop + src_slot<PAR>(r, lv.N, n, xo, yo, zo));
+    });
+    nbcv = lv.nbc[n];
+    puv = lv.pu[n];
+  }
   // wall momentum of this thread: wall id, variable part, constant-part integers
   int wkey = -1;
   float wF[3] = {0.f, 0.f, 0.f};
@@ -497,10 +512,9 @@ __global__ void __launch_bounds__(128, BL_LB_MINB) k_lb_step(LatticeView lv, Wal
     // cell (a node that lost its last cell neighbour had its pending C
     // flushed by the neighbour-word update)
     const bool near = (nbw & NB_CELL) != 0;
-    node_update<S, PAR, FORCE, TAU1>(lv, wa, n, xyz, xo, yo, zo, nbw, near ? lv.nbc[n] : NBC_MIXED,
-                                     near ? lv.pu[n] : make_float4(0.f, 0.f, 0.f, 0.f),
-                                     [&](int, unsigned slot) { return Store<S>::ld(pop + slot); }, wkey, wF, wK,
-                                     cl);
+    node_update<S, PAR, FORCE, TAU1>(lv, wa, n, xyz, xo, yo, zo, nbw, near ? nbcv : NBC_MIXED,
+                                     near ? puv : make_float4(0.f, 0.f, 0.f, 0.f),
+                                     [&](int r, unsigned) { return fin[r]; }, wkey, wF, wK, cl);
   }
   emit_links<TAU1>(lv, cl, n);
   flush_wall_momentum(wa, wkey, wF, wK);

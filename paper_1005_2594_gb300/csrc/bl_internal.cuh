@@ -243,8 +243,7 @@ void launch_geometry(const LatticeView &lv, const PartView &pv, cudaStream_t st,
 // the same result as launch_geometry): neighbour words around the changed
 // nodes (after resolve); contact sums cell by cell from the current owner
 // map and kinematics (at the start of the next step)
-void launch_nbm_update(int dtype, const LatticeView &lv, const PartView &pv, const ChangeList &chg, int par_next,
-                       cudaStream_t st,
+void launch_nbm_update(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
                        int64_t *nl);
 void launch_contacts(const LatticeView &lv, const PartView &pv, cudaStream_t st, int64_t *nl);
 // the pending C of the last step into the stored populations (layout par),

@@ -516,10 +516,9 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
   const bool first = n != c->np || c->np == 0;
   // a new set of cells clears the old cells and rebuilds the geometry, which
   // drops pending terms: they go to the populations first.  A re-placement
-  // keeps them: fluid that stays fluid gets its term in the next sweep, the
-  // resolve counts that of fluid it covers in the impulses, and the
-  // neighbour-word update gives a node that loses its last cell neighbour
-  // its term
+  // keeps them: fluid that stays fluid gets its term in the next sweep (which
+  // reads every fluid node's pending velocity), and the resolve counts that
+  // of fluid it covers in the impulses
   if (first && flush_pending(c)) return c->sticky;
   // the graphs hold the cell arrays' pointers and the cell constants by
   // value: they stay valid for a re-placement with the same arrays and
@@ -571,7 +570,7 @@ extern "C" int bl_particles_set(bl_ctx *c, int n, const bl_particle_params *pp, 
   // re-placement only around the nodes resolve changed (every step starts by
   // summing the contact links of the current owner map)
   if (first) launch_geometry(c->lv, c->pv, c->stream, &c->launches);
-  else launch_nbm_update(c->dtype, c->lv, c->pv, c->chg, c->parity, c->stream, &c->launches);
+  else launch_nbm_update(c->lv, c->pv, c->chg, c->stream, &c->launches);
   std::swap(c->pv.kin, c->pv.kin_next);
   if (check_launch(c, "particles_set")) return c->sticky;
   // a first placement waits (device errors surface here); a re-placement
@@ -642,7 +641,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     cudaStreamWaitEvent(st, c->ev_join2, 0);
     group_begin(c, 4, &slot, st);
     launch_resolve_fill(c->dtype, c->lv, c->pv, c->cl, c->claim, c->chg, c->parity ^ 1, 1, st, &c->launches);
-    launch_nbm_update(c->dtype, c->lv, c->pv, c->chg, c->parity ^ 1, st, &c->launches);
+    launch_nbm_update(c->lv, c->pv, c->chg, st, &c->launches);
     group_end(c, slot, st);
     std::swap(c->pv.kin, c->pv.kin_next);
   }

@@ -1405,14 +1405,16 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
       chg.items[3 * pos + 1] = old;
       chg.items[3 * pos + 2] = nw;
     }
-    // the slot from which the node reads direction r in layout par_next (the
-    // loops over r below stay rolled: this path is rare, and its code stays
-    // small enough for the instruction cache)
-    auto slot_of = [&](int r) -> unsigned {
-      if (par_next == 0 || r == 0) return (unsigned)r * lv.N + idx;
-      return (unsigned)rt_opp(r) * lv.N + node_of(lv, wrapi(xyz[0] - rt_c<0>(r), lv.nx),
-                                                  wrapi(xyz[1] - rt_c<1>(r), lv.ny), wrapi(xyz[2] - rt_c<2>(r), lv.nz));
-    };
+    unsigned slot[Q];
+    for (int r = 0; r < Q; ++r) {
+      if (par_next == 0 || r == 0) {
+        slot[r] = (unsigned)r * lv.N + idx;
+      } else {
+        slot[r] = (unsigned)D::opp(r) * lv.N +
+                  node_of(lv, wrapi(xyz[0] - D::cx(r), lv.nx), wrapi(xyz[1] - D::cy(r), lv.ny),
+                          wrapi(xyz[2] - D::cz(r), lv.nz));
+      }
+    }
     double arm_o[3] = {0, 0, 0}, arm_n[3] = {0, 0, 0};
     float u_o[3] = {0.f, 0.f, 0.f};
     if (old >= 0) {
@@ -1434,12 +1436,11 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
       const uint32_t pm = __float_as_uint(pu.w);
       if (impulses) {
         float mf[3] = {0.f, 0.f, 0.f};
-#pragma unroll 1
         for (int r = 0; r < Q; ++r) {
-          const float v = Store<S>::ld(pop + slot_of(r));
-          mf[0] += v * (float)rt_c<0>(r);
-          mf[1] += v * (float)rt_c<1>(r);
-          mf[2] += v * (float)rt_c<2>(r);
+          const float v = Store<S>::ld(pop + slot[r]);
+          mf[0] += v * D::cx(r);
+          mf[1] += v * D::cy(r);
+          mf[2] += v * D::cz(r);
         }
         // C_r owed to direction rbar: momentum -C_r c_r (the links to a second
         // or third cell got theirs in place)
@@ -1469,11 +1470,10 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
         // uncovered: new fluid at n^eq(rho_bar, u_rigid), stored shifted
         const float rho0 = (float)pv.rho0;
         const float uu = u_o[0] * u_o[0] + u_o[1] * u_o[1] + u_o[2] * u_o[2];
-#pragma unroll 1
         for (int r = 0; r < Q; ++r) {
-          const float cu = (float)rt_c<0>(r) * u_o[0] + (float)rt_c<1>(r) * u_o[1] + (float)rt_c<2>(r) * u_o[2];
-          const float w = (float)rt_m(r) / 36.0f;
-          Store<S>::st(pop + slot_of(r), rho0 * w * (cu * (3.0f + cu * (4.5f + 4.5f * cu)) - uu * (1.5f + 4.5f * cu)));
+          const float cu = D::cx(r) * u_o[0] + D::cy(r) * u_o[1] + D::cz(r) * u_o[2];
+          const float w = D::m(r) / 36.0f;
+          Store<S>::st(pop + slot[r], rho0 * w * (cu * (3.0f + cu * (4.5f + 4.5f * cu)) - uu * (1.5f + 4.5f * cu)));
         }
       } else {
         // direct change of owner: uncover by the old, cover by the new (reading Q6)
@@ -1536,13 +1536,8 @@ __device__ __forceinline__ uint32_t node_word(const LatticeView &lv, int x, int 
 }
 
 // neighbour words of every changed node x and of the nodes x - c_r that see
-// it; the whole lattice if the change list overflowed (grid-stride).  A fluid
-// node left with no cell neighbour gets its pending C now (the sweep reads
-// the pending velocity only next to a cell); par_next is the layout of the
-// stored populations.  A node can be visited by several threads: the one
-// that takes the pending mask (atomic exchange) applies it.
-template <class S>
-__global__ void k_nbm_update(LatticeView lv, ChangeList chg, int par_next) {
+// it; the whole lattice if the change list overflowed (grid-stride)
+__global__ void k_nbm_update(LatticeView lv, ChangeList chg) {
   using D = D3Q19;
   const int cnt = *chg.count;
   const bool all = cnt > chg.cap;
@@ -1561,24 +1556,8 @@ __global__ void k_nbm_update(LatticeView lv, ChangeList chg, int par_next) {
     }
     uint32_t cw;
     const unsigned nn = node_of(lv, xyz[0], xyz[1], xyz[2]);
-    const uint32_t w = node_word(lv, xyz[0], xyz[1], xyz[2], cw);
-    lv.nbm[nn] = w;
+    lv.nbm[nn] = node_word(lv, xyz[0], xyz[1], xyz[2], cw);
     lv.nbc[nn] = cw;
-    if ((w & NB_FLUID) && !(w & NB_CELL)) {
-      const uint32_t pm = atomicExch(reinterpret_cast<unsigned *>(lv.pu + nn) + 3, 0u);
-      if (pm) {
-        const float4 pu = lv.pu[nn];
-        S *pop = reinterpret_cast<S *>(lv.pop);
-        for (uint32_t m = pm; m; m &= m - 1u) {
-          const int r = __ffs(m) - 1;
-          const float C = -((float)rt_m(r) / 6.0f) *
-                          ((float)rt_c<0>(r) * pu.x + (float)rt_c<1>(r) * pu.y + (float)rt_c<2>(r) * pu.z);
-          // the slot from which node nn reads direction rbar in layout par_next
-          const unsigned slot = bounce_slot(lv, par_next ^ 1, nn, xyz, r);
-          Store<S>::st(pop + slot, Store<S>::ld(pop + slot) + C);
-        }
-      }
-    }
   }
 }
 
@@ -1874,12 +1853,10 @@ void launch_claims(const LatticeView &lv, const PartView &pv, int *claim, const 
   *nl += 1;
 }
 
-void launch_nbm_update(int dtype, const LatticeView &lv, const PartView &pv, const ChangeList &chg, int par_next,
-                       cudaStream_t st, int64_t *nl) {
+void launch_nbm_update(const LatticeView &lv, const PartView &pv, const ChangeList &chg, cudaStream_t st,
+                       int64_t *nl) {
   if (pv.n == 0) return;
-  if (dtype == 0) k_nbm_update<float><<<4 * 152, 256, 0, st>>>(lv, chg, par_next);
-  else if (dtype == 1) k_nbm_update<__nv_bfloat16><<<4 * 152, 256, 0, st>>>(lv, chg, par_next);
-  else k_nbm_update<__half><<<4 * 152, 256, 0, st>>>(lv, chg, par_next);
+  k_nbm_update<<<4 * 152, 256, 0, st>>>(lv, chg);
   *nl += 1;
 }
 

@@ -1345,8 +1345,12 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
                                                       ChangeList chg, int par_next, int impulses) {
   using D = D3Q19;
   const int p = blockIdx.x;
-  const int nt = pv.touched_count[p];
   const unsigned long long *touched = pv.touched + (size_t)p * pv.touched_cap;
+  // the first touched node of this thread is requested with the count (the
+  // list holds touched_cap entries)
+  unsigned long long tv0 = 0ull;
+  if ((int)threadIdx.x < pv.touched_cap) tv0 = touched[threadIdx.x];
+  const int nt = pv.touched_count[p];
   const int lane = threadIdx.x & 31;
   S *pop = reinterpret_cast<S *>(lv.pop);
   const int dims[3] = {lv.nx, lv.ny, lv.nz};
@@ -1361,12 +1365,13 @@ __global__ void __launch_bounds__(PB) k_resolve_fill(LatticeView lv, PartView pv
     __syncthreads();
     if (t < nt) {
       int r_unused;
-      unpack_xyzr(touched[t], xyz, r_unused);
+      unpack_xyzr(t0 == 0 ? tv0 : touched[t], xyz, r_unused);
       idx = node_of(lv, xyz[0], xyz[1], xyz[2]);
+      const int own = lv.owner[idx];  // requested beside the claim's exchange
       const int c = atomicExch(&claim[idx], CLAIM_FREE);
       if (c != CLAIM_FREE) {
         act = true;
-        old = lv.owner[idx];
+        old = own;
         // TOUCHED: the old owner left the node -> the lowest-index cell now
         // covering it (searched below by a warp), else fluid; a claim: a
         // fluid node entered by the claimants, the lowest of which takes it
@@ -1503,18 +1508,24 @@ __device__ __forceinline__ uint32_t node_word(const LatticeView &lv, int x, int 
   using D = D3Q19;
   const unsigned nx = (unsigned)lv.nx, nxy = (unsigned)lv.nx * (unsigned)lv.ny;
   cellw = NBC_MIXED;
-  const int own = lv.owner[(unsigned)x + nx * (unsigned)y + nxy * (unsigned)z];
-  if (own <= -2) return 0u;  // wall node
   const int xs[3] = {x == 0 ? lv.nx - 1 : x - 1, x, x == lv.nx - 1 ? 0 : x + 1};
   const int ys[3] = {y == 0 ? lv.ny - 1 : y - 1, y, y == lv.ny - 1 ? 0 : y + 1};
   const int zs[3] = {z == 0 ? lv.nz - 1 : z - 1, z, z == lv.nz - 1 ? 0 : z + 1};
+  // the node's owner and its 18 neighbours' are requested together (one
+  // memory round trip; a wall node's neighbour owners go unused)
+  int on[Q];
+  sfor<0, Q>([&](auto R) {
+    constexpr int r = decltype(R)::value;
+    on[r] = lv.owner[(unsigned)xs[1 + D::cx(r)] + nx * (unsigned)ys[1 + D::cy(r)] + nxy * (unsigned)zs[1 + D::cz(r)]];
+  });
+  const int own = on[0];
+  if (own <= -2) return 0u;  // wall node
   if (own != FLUID) {
     // cell node: its contact links (neighbours owned by a wall or another cell)
     unsigned cmask = 0;
     sfor<1, Q>([&](auto R) {
       constexpr int r = decltype(R)::value;
-      const int on = lv.owner[(unsigned)xs[1 + D::cx(r)] + nx * (unsigned)ys[1 + D::cy(r)] + nxy * (unsigned)zs[1 + D::cz(r)]];
-      cmask |= (on != FLUID && on != own ? 1u : 0u) << r;
+      cmask |= (on[r] != FLUID && on[r] != own ? 1u : 0u) << r;
     });
     return cmask;
   }
@@ -1523,12 +1534,11 @@ __device__ __forceinline__ uint32_t node_word(const LatticeView &lv, int x, int 
   bool mixed = false;
   sfor<1, Q>([&](auto R) {
     constexpr int r = decltype(R)::value;
-    const int on = lv.owner[(unsigned)xs[1 + D::cx(r)] + nx * (unsigned)ys[1 + D::cy(r)] + nxy * (unsigned)zs[1 + D::cz(r)]];
-    solid |= (on != FLUID ? 1u : 0u) << r;
-    wall |= (on <= -2 ? 1u : 0u) << r;
-    if (on != FLUID) {
-      if (first == -1) first = on;
-      else if (on != first) mixed = true;
+    solid |= (on[r] != FLUID ? 1u : 0u) << r;
+    wall |= (on[r] <= -2 ? 1u : 0u) << r;
+    if (on[r] != FLUID) {
+      if (first == -1) first = on[r];
+      else if (on[r] != first) mixed = true;
     }
   });
   if (first >= 0 && !mixed) cellw = (uint32_t)first;

@@ -608,20 +608,46 @@ def run_rheology(args, ws, rank, local):
     X, Y, _, runs = learned.approach_samples(64, seed=11)
     m, info = learned.fit(X, Y, runs, seed=0)
     rng = (info["gap_min"], 2.0, info["speed_min"], info["speed_max"])
-    res = {}
+    res, profiles = {}, {}
     for name, k, cells, net in (("plasma_1x", 1, False, False), ("plain_1x", 1, True, False),
                                 ("learned_1x", 1, True, True), ("plasma_2x", 2, False, False),
                                 ("plain_2x", 2, True, False)):
         p, Xc, qc, mask = rheology.tube_case(k, cells=cells)
         steps = args.steps * k * k
-        Q, samples, ms = rheology.run(p, Xc, qc, mask, steps, model=m if net else None, gap_range=rng)
+        Q, samples, ms, prof = rheology.run(p, Xc, qc, mask, steps, model=m if net else None, gap_range=rng,
+                                            profile_radius=30.0 * k)
         N = p["nx"] * p["ny"] * p["nz"]
         res[name] = {"flux": Q, "flux_rel_spread": float(np.std(samples) / abs(Q)), "steps": steps,
                      "cells": int(len(Xc)), "lattice": [p["nx"], p["ny"], p["nz"]],
                      "mlups": N * steps / (ms * 1e-3) / 1e6}
+        profiles[name] = prof
     mu = {"plain_1x": res["plasma_1x"]["flux"] / res["plain_1x"]["flux"],
           "learned_1x": res["plasma_1x"]["flux"] / res["learned_1x"]["flux"],
           "plain_2x": res["plasma_2x"]["flux"] / res["plain_2x"]["flux"]}
+    # Sec. IV: the plasma-only profile places the staircase wall (its
+    # effective radius); each suspension's profile is then fitted with the
+    # two-layer model, the boundary viscosity set to the plasma's
+    # (lengths in coarse lattice units; the 2x lattice's force density is
+    # g / 8 in its own units)
+    mu_b = p["rho0"] * (p["tau"] - 0.5) / 3.0
+    fits = {}
+    for k, plasma, susp in ((1, "plasma_1x", ("plain_1x", "learned_1x")), (2, "plasma_2x", ("plain_2x",))):
+        f = p["rho0"] * 2e-6 / k ** 3
+        r_c, u_p, _, n_p = profiles[plasma]
+        R_eff = rheology.fit_poiseuille_radius(r_c, u_p, f, mu_b, n_p)
+        fits["R_eff_%dx" % k] = round(R_eff / k, 4)
+        for name in susp:
+            r_s, u_s, H, n_s = profiles[name]
+            d, mr = rheology.fit_axial_train(r_s, u_s, R_eff, f, mu_b, n_s)
+            Rc = R_eff - d
+            fits[name] = {"delta": round(d / k, 4), "mu_c_over_mu_b": round(mr, 4),
+                          "mu_rel_of_fit": round(R_eff ** 4 / (R_eff ** 4 - Rc ** 4 + Rc ** 4 / mr), 4)}
+            if k == 1:
+                fits[name].update({"u_axial": [round(float(v), 9) for v in u_s],
+                                   "H": [round(float(v), 4) for v in H]})
+        if k == 1:
+            fits["r"] = [float(v) for v in r_c]
+            fits["u_axial_plasma"] = [round(float(v), 9) for v in u_p]
     r = res["learned_1x"]
     out = {
         "metric": METRIC, "value": round(r["mlups"], 2), "unit": UNIT, "n_gpus": ws, "steps": r["steps"],
@@ -635,7 +661,12 @@ def run_rheology(args, ws, rank, local):
                      "note": "apparent viscosity relative to the plasma = plasma flux / suspension flux under the "
                              "same driving, flux averaged over the second half of each run from rest",
                      "runs": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv) for kk, vv in v.items()}
-                              for k, v in res.items()}},
+                              for k, v in res.items()},
+                     "profiles": fits,
+                     "profiles_note": "radial bins of unit width about the tube axis, averaged over the flux samples: "
+                                      "mean axial velocity of the fluid nodes and cell fraction H; R_eff from the "
+                                      "plasma-only profile, delta and mu_c/mu_b from the two-layer fit of the "
+                                      "suspension's profile (boundary viscosity = plasma's, f = rho g)"},
         "roofline": None,
     }
     bl.bl_mlp_destroy(m)

@@ -69,7 +69,79 @@ def flux(sim, p):
     return q_fluid + float(V[:, 0].sum()) * vol / p["nx"]
 
 
-def run(p, X, q, mask, steps, samples=20, model=None, gap_range=None, stream=None):
+def radial_profiles(u, owner, p, radius, axis=0):
+    """Radial profiles about the tube axis (through the box centre): bins of
+    unit width from the axis to `radius`; per bin the mean axial velocity of
+    its fluid nodes and the cell fraction, cell nodes over cell and fluid
+    nodes (Sec. IV, the arteriole's velocity and concentration profiles).
+    u: N x 3 (or N axial values), owner: N, node n = x + nx (y + ny z).
+    Returns (bin centres, mean axial velocity, cell fraction, fluid nodes per
+    bin)."""
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    coords = [x.reshape(-1), y.reshape(-1), z.reshape(-1)]
+    c = [(nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0]
+    others = [k for k in range(3) if k != axis]
+    r = np.sqrt(sum((coords[k] - c[k]) ** 2 for k in others))
+    ua = np.asarray(u)
+    ua = ua[:, axis] if ua.ndim == 2 else ua
+    own = np.asarray(owner)
+    nb = int(math.ceil(radius))
+    b = np.minimum((r).astype(np.int64), nb)
+    inside = (r < radius) & (own > -2)
+    fl = inside & (own == -1)
+    cell = inside & (own >= 0)
+    n_fl = np.bincount(b[fl], minlength=nb + 1)[:nb]
+    n_cell = np.bincount(b[cell], minlength=nb + 1)[:nb]
+    u_sum = np.bincount(b[fl], weights=ua[fl], minlength=nb + 1)[:nb]
+    centres = np.arange(nb) + 0.5
+    with np.errstate(invalid="ignore", divide="ignore"):
+        u_mean = np.where(n_fl > 0, u_sum / np.maximum(n_fl, 1), np.nan)
+        H = np.where(n_fl + n_cell > 0, n_cell / np.maximum(n_fl + n_cell, 1), np.nan)
+    return centres, u_mean, H, n_fl
+
+
+def poiseuille(r, R, f, mu):
+    """Hagen-Poiseuille profile of a tube of radius R under force density f"""
+    return f / (4.0 * mu) * (R * R - np.asarray(r) ** 2)
+
+
+def axial_train(r, R, delta, mu_ratio, f, mu_b):
+    """The two-layer (modified axial-train) profile that Sec. IV fits to the
+    arteriole: a cell-depleted layer of width delta next to the wall with the
+    plasma viscosity mu_b, and a core of viscosity mu_c = mu_ratio mu_b; the
+    shear stress f r / 2 is continuous at the core radius R - delta."""
+    r = np.asarray(r, dtype=np.float64)
+    Rc = R - delta
+    outer = f / (4.0 * mu_b) * (R * R - r * r)
+    core = f / (4.0 * mu_b) * (R * R - Rc * Rc) + f / (4.0 * mu_b * mu_ratio) * (Rc * Rc - r * r)
+    return np.where(r >= Rc, outer, core)
+
+
+def fit_poiseuille_radius(r, u, f, mu, weights=None):
+    """effective wall radius of a plasma-only profile (the staircase wall's
+    position is uncertain by about half a node)"""
+    from scipy.optimize import curve_fit
+
+    ok = np.isfinite(u)
+    sig = None if weights is None else 1.0 / np.sqrt(np.maximum(weights[ok], 1))
+    (R,), _ = curve_fit(lambda rr, R: poiseuille(rr, R, f, mu), r[ok], u[ok], p0=[r[ok].max() + 0.5], sigma=sig)
+    return float(R)
+
+
+def fit_axial_train(r, u, R, f, mu_b, weights=None):
+    """(delta, mu_c / mu_b) of the two-layer profile closest to u(r), the wall
+    radius R and the boundary viscosity mu_b (the plasma's) given"""
+    from scipy.optimize import curve_fit
+
+    ok = np.isfinite(u)
+    sig = None if weights is None else 1.0 / np.sqrt(np.maximum(weights[ok], 1))
+    (delta, ratio), _ = curve_fit(lambda rr, d, m: axial_train(rr, R, d, m, f, mu_b), r[ok], u[ok], p0=[0.1 * R, 2.0],
+                                  bounds=([0.0, 1.0], [R, 100.0]), sigma=sig)
+    return float(delta), float(ratio)
+
+
+def run(p, X, q, mask, steps, samples=20, model=None, gap_range=None, stream=None, profile_radius=None):
     """steps of the tube from rest (with `model` attached over gap_range =
     (gap_lo, gap_hi[, speed_lo, speed_hi])); the flux sampled at `samples` even
     intervals over the second half.  Returns (mean flux, flux samples,
@@ -77,6 +149,7 @@ def run(p, X, q, mask, steps, samples=20, model=None, gap_range=None, stream=Non
     import torch
 
     st = torch.cuda.current_stream() if stream is None else stream
+    prof = []
     sim = bl.Simulation(p, stream=st.cuda_stream, wall_mask=mask)
     if len(X):
         sim.set_particles(X, q)
@@ -101,6 +174,15 @@ def run(p, X, q, mask, steps, samples=20, model=None, gap_range=None, stream=Non
         ms += advance(every)
         done += every
         out.append(flux(sim, p))
+        if profile_radius is not None:
+            _, u, own = sim.fields()
+            prof.append(radial_profiles(u, own, p, profile_radius))
     sim.sync()
     sim.close()
-    return float(np.mean(out)), out, ms
+    if profile_radius is None:
+        return float(np.mean(out)), out, ms
+    centres = prof[0][0]
+    u_mean = np.nanmean(np.array([pr[1] for pr in prof]), axis=0)
+    H = np.nanmean(np.array([pr[2] for pr in prof]), axis=0)
+    n_fl = np.sum(np.array([pr[3] for pr in prof]), axis=0)
+    return float(np.mean(out)), out, ms, (centres, u_mean, H, n_fl)

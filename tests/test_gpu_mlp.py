@@ -231,18 +231,26 @@ def test_attached_network_adds_rotated_correction_to_close_pairs(lo, speed):
 
 
 def test_tube_flux_of_plasma_is_poiseuille():
-    """The tube observable: plasma alone, driven by g in a tube of radius R,
+    """The tube observables: plasma alone, driven by g in a tube of radius R,
     carries the Poiseuille flux pi R_eff^4 g / (8 nu) once developed, with the
-    staircase's effective radius within half a node of R."""
+    staircase's effective radius within half a node of R; its radial profile
+    is the parabola g (R_eff^2 - r^2) / (4 nu) of a radius that agrees with
+    the flux's, and the cell fraction is zero in every bin."""
     import math
 
     from paper_1005_2594_gb300 import rheology
 
     R = 10.0
     p, X, q, mask = rheology.tube_case(1, radius=R, length=16, cells=False, g=1e-5)
-    Q, samples, _ = rheology.run(p, X, q, mask, 6000, samples=4)
+    Q, samples, _, (r, u, H, n) = rheology.run(p, X, q, mask, 6000, samples=4, profile_radius=R)
     nu = (p["tau"] - 0.5) / 3.0
-    R_eff = (8.0 * Q * nu / (math.pi * p["g"][0])) ** 0.25
-    print("tube radius %.1f: effective radius %.3f, flux spread %.1e" % (R, R_eff, np.std(samples) / Q))
+    g = p["g"][0]
+    R_eff = (8.0 * Q * nu / (math.pi * g)) ** 0.25
+    R_prof = rheology.fit_poiseuille_radius(r, u, g, nu, n)
+    dev = np.abs(u - rheology.poiseuille(r, R_prof, g, nu))[r < R - 2].max() / np.nanmax(u)
+    print("tube radius %.1f: effective radius %.3f (flux), %.3f (profile), profile deviation %.1e, "
+          "flux spread %.1e" % (R, R_eff, R_prof, dev, np.std(samples) / Q))
     assert abs(R_eff - R) < 0.5
     assert np.std(samples) / Q < 1e-3  # developed
+    assert abs(R_prof - R_eff) < 0.25 and dev < 2e-2
+    assert np.all(H[n > 0] == 0.0)

@@ -1,0 +1,70 @@
+"""Radial profiles of tube flow and the two-layer fit of Sec. IV (CPU).
+
+Sec. IV fits the arteriole's radial velocity profile with a modified
+axial-train model: a cell-depleted layer of width delta next to the wall,
+with the plasma viscosity, around a core of viscosity mu_c.  These tests pin
+the profile function, the fit and the binning of lattice fields.
+"""
+import math
+
+import numpy as np
+
+from paper_1005_2594_gb300 import rheology, workloads
+
+F, MU = 2e-6, 1.0 / 6.0
+
+
+def test_two_layer_profile_limits_and_continuity():
+    r = np.linspace(0.0, 30.0, 301)
+    R = 30.0
+    # no layer: the core's Poiseuille profile; equal viscosities: the plasma's
+    np.testing.assert_allclose(rheology.axial_train(r, R, 0.0, 2.5, F, MU), rheology.poiseuille(r, R, F, 2.5 * MU),
+                               rtol=1e-12, atol=0)
+    np.testing.assert_allclose(rheology.axial_train(r, R, 7.0, 1.0, F, MU), rheology.poiseuille(r, R, F, MU),
+                               rtol=1e-12, atol=0)
+    # continuous at the core radius, and the stress f r / 2 on both sides
+    Rc = R - 4.0
+    lo, hi = rheology.axial_train([Rc - 1e-7, Rc + 1e-7], R, 4.0, 3.0, F, MU)
+    assert abs(lo - hi) < 1e-6 * abs(lo)  # the slope alone moves it by ~5e-8 of its value
+    eps = 1e-4
+    d_in = (rheology.axial_train(Rc - eps, R, 4.0, 3.0, F, MU) - rheology.axial_train(Rc - 2 * eps, R, 4.0, 3.0, F, MU)) / eps
+    d_out = (rheology.axial_train(Rc + 2 * eps, R, 4.0, 3.0, F, MU) - rheology.axial_train(Rc + eps, R, 4.0, 3.0, F, MU)) / eps
+    assert abs(3.0 * MU * d_in + F * Rc / 2) < 1e-3 * F * Rc
+    assert abs(MU * d_out + F * Rc / 2) < 1e-3 * F * Rc
+
+
+def test_fit_recovers_layer_width_and_viscosity_ratio():
+    R = 30.0
+    r = np.arange(30) + 0.5
+    for delta, ratio in ((2.0, 2.43), (4.5, 1.8), (1.0, 3.5)):
+        u = rheology.axial_train(r, R, delta, ratio, F, MU)
+        d, m = rheology.fit_axial_train(r, u, R, F, MU)
+        assert abs(d - delta) < 1e-3 and abs(m - ratio) < 1e-3 * ratio, (d, m, delta, ratio)
+    # the effective radius of a plasma-only profile
+    u = rheology.poiseuille(r, 29.6, F, MU)
+    assert abs(rheology.fit_poiseuille_radius(r, u, F, MU) - 29.6) < 1e-6
+
+
+def test_radial_binning_of_lattice_fields():
+    """a synthetic tube: Poiseuille velocity on the fluid nodes, cell nodes
+    inside radius 8; the bins give the profile at their nodes' mean radius
+    and a cell fraction of 1 inside, 0 outside"""
+    p = workloads.base_params(16, 40, 40, periodic=(1, 1, 1))
+    radius = 18.0
+    mask = workloads.tube_mask(p, radius, axis=0)
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    c = (ny - 1) / 2.0
+    r = np.hypot(y - c, z - c).reshape(-1)
+    owner = np.where(mask > 0, -2 - 6, -1).astype(np.int32)
+    owner[(r < 8.0) & (mask == 0)] = 0
+    u = np.zeros((nx * ny * nz, 3))
+    u[:, 0] = np.where(owner == -1, rheology.poiseuille(r, radius, F, MU), 0.0)
+    centres, um, H, n = rheology.radial_profiles(u, owner, p, radius)
+    assert len(centres) == math.ceil(radius)
+    for k in range(len(centres)):
+        sel = (r >= k) & (r < k + 1) & (r < radius) & (owner == -1)
+        if sel.any():
+            assert abs(um[k] - u[sel, 0].mean()) < 1e-15
+            assert n[k] == sel.sum()
+    assert np.all(H[:8] == 1.0) and np.all(H[9:] == 0.0)

@@ -219,6 +219,11 @@ def make_workload(name):
 
         p, X, q, mask = rheology.tube_case(1)
         return p, X, q, mask, "tube radius 30, length 128, %d (7,7,3) cells at 35 %% of the lumen, g = 2e-6" % len(X)
+    if name == "arteriole":
+        from paper_1005_2594_gb300 import rheology
+
+        p, X, q, mask = rheology.arteriole_case()
+        return p, X, q, mask, "arteriole radius 46.5, length 64, %d (5.5,5.5,1.83) cells at 42 %% of the lumen, g = 8e-6" % len(X)
     if name == "duct256":
         p, X, q = workloads.duct(n=256, n_cells=8192, g=1e-6, seed=1003)
         return p, X, q, None, "duct 256^3, walls y z, g = 1e-6 along x, 8192 (7,7,3) cells"
@@ -673,6 +678,71 @@ def run_rheology(args, ws, rank, local):
     return out
 
 
+def run_arteriole(args, ws, rank, local):
+    """Sec. IV's arteriole (radius 31 um = 46.5 nodes, periodic length 64,
+    cells sigma = (6, 2), R = 11/12 sigma, 42 % of the lumen, cell-wall
+    stiffness 1.47e-16 J) driven from rest for --steps steps (60000 let the
+    fcc start dissolve): the radial velocity profile fitted with the two-layer
+    model (cell-depleted layer width delta, core-to-boundary viscosity ratio)
+    and the cell fraction H(r), with the wall radius taken from the plasma
+    alone under the same force.  Two fcc starts: centres kept R_perp + 1
+    from the wall (no cell reaches it) and R_par + 1 (edge-on cells reach
+    into it); the second also at ten times and a tenth of the cell-wall
+    stiffness, the paper's knob for the layer width."""
+    import torch
+
+    import __graft_entry__
+    from paper_1005_2594_gb300 import rheology
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    g = 8e-6
+    p, _, _, mask = rheology.arteriole_case(cells=False, g=g)
+    f, mu_b = p["rho0"] * g, p["rho0"] * (p["tau"] - 0.5) / 3.0
+    Qp, _, msp, (r_c, u_p, _, n_p) = rheology.run(p, np.zeros((0, 3)), np.zeros((0, 4)), mask, args.steps,
+                                                   profile_radius=31.0 / rheology.DX_UM)
+    R_eff = rheology.fit_poiseuille_radius(r_c, u_p, f, mu_b, n_p)
+    runs = {}
+    for name, ew, start in (("wide start, eps_w 1.47e-16 J", 1.47e-16, "wide"),
+                            ("close start, eps_w 1.47e-16 J", 1.47e-16, "close"),
+                            ("close start, eps_w 1.47e-15 J", 1.47e-15, "close"),
+                            ("close start, eps_w 1.47e-17 J", 1.47e-17, "close")):
+        p, X, q, mask = rheology.arteriole_case(g=g, eps_w_J=ew, start=start)
+        Q, samples, ms, (r_c, u_s, H, n_s) = rheology.run(p, X, q, mask, args.steps,
+                                                          profile_radius=31.0 / rheology.DX_UM)
+        d, mr = rheology.fit_axial_train(r_c, u_s, R_eff, f, mu_b, n_s)
+        Rc = R_eff - d
+        N = p["nx"] * p["ny"] * p["nz"]
+        runs[name] = {"eps_w": round(p["eps_w"], 6), "cells": int(len(X)), "flux": round(Q, 5),
+                      "flux_rel_spread": round(float(np.std(samples) / abs(Q)), 5),
+                      "pseudo_shear_rate_per_s": round(rheology.pseudo_shear_rate(Q, R_eff), 1),
+                      "mu_rel": round(Qp / Q, 4), "delta_nodes": round(d, 3),
+                      "delta_um": round(d * rheology.DX_UM, 3), "mu_c_over_mu_b": round(mr, 3),
+                      "mu_rel_of_fit": round(R_eff ** 4 / (R_eff ** 4 - Rc ** 4 + Rc ** 4 / mr), 4),
+                      "H_axis": round(float(np.nanmean(H[:5])), 4),
+                      "mlups": round(N * args.steps / (ms * 1e-3) / 1e6, 1),
+                      "u_axial": [round(float(v), 9) for v in u_s], "H": [round(float(v), 4) for v in H]}
+    main = runs["close start, eps_w 1.47e-16 J"]
+    return {
+        "metric": METRIC, "value": main["mlups"], "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (jittered fcc start, resting plasma)",
+        "config": {"workload": "arteriole radius 31 um (46.5 nodes), periodic length 64, %d cells sigma (6,2) "
+                               "R = 11/12 sigma at 42 %% of the lumen, g = %g on plasma and cells; value: MLUPS "
+                               "of the stepping at the paper's cell-wall stiffness" % (main["cells"], g), "g": g,
+                   "lattice": [p["nx"], p["ny"], p["nz"]]},
+        "arteriole": {"R_eff_nodes": round(R_eff, 4), "plasma_flux": round(Qp, 5),
+                      "paper": {"mu_c_over_mu_b": "2.43 +- 0.01", "delta_um": "1.47 +- 0.04",
+                                "pseudo_shear_rate_per_s": 1.3e3, "H_axis": "up to about 0.6"},
+                      "r_nodes": [float(v) for v in r_c], "u_axial_plasma": [round(float(v), 9) for v in u_p],
+                      "runs": runs,
+                      "note": "radial bins of unit width about the axis, averaged over 20 samples in the second "
+                              "half; two-layer fit with the boundary viscosity the plasma's and the wall radius "
+                              "fitted to the plasma alone; mu_rel = plasma flux / suspension flux"},
+        "roofline": None,
+    }
+
+
 def run_e2e(sim, n, N, steps, stream):
     import torch
 
@@ -798,11 +868,11 @@ def run_reference(args, ws, rank):
         return None
     p, X, q, _mask, desc = make_workload(args.config)
     steps, warmup = args.steps, args.warmup
-    if args.config == "tube_rheology":
-        # the coarse tube itself (about 0.7 s per oracle step): as many steps as fit
+    if args.config in ("tube_rheology", "arteriole"):
+        # the whole tube (under a second per oracle step): as many steps as fit
         sp, sX, sq, smask = p, X, q, _mask
         steps, warmup = max(1, min(steps, 100)), min(warmup, 3)
-        sample = "the whole coarse tube (128x68x68, %d cells), %d steps" % (len(sX), steps)
+        sample = "the whole tube (%dx%dx%d, %d cells), %d steps" % (p["nx"], p["ny"], p["nz"], len(sX), steps)
     elif args.config == "tube512":
         # the cross-section is fixed by the radius: a slab of 8 x-planes of the
         # same tube, and as many steps as fit the budget (~0.5 s each)
@@ -833,7 +903,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--config", default="shear128", choices=["shear128", "small32", "duct256", "ensemble64", "tube512", "tube_rheology"])
+    ap.add_argument("--config", default="shear128", choices=["shear128", "small32", "duct256", "ensemble64", "tube512", "tube_rheology",
+                                                          "arteriole"])
     ap.add_argument("--store", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--sweep", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
                     help="sweep variant (default: the library's choice for the row length and storage)")
@@ -849,8 +920,9 @@ def main():
         if rank == 0:
             print(json.dumps(out), flush=True)
         return
-    if args.config in ("ensemble64", "tube512", "tube_rheology"):
-        fn = {"ensemble64": run_ensemble, "tube512": run_learned, "tube_rheology": run_rheology}[args.config]
+    if args.config in ("ensemble64", "tube512", "tube_rheology", "arteriole"):
+        fn = {"ensemble64": run_ensemble, "tube512": run_learned, "tube_rheology": run_rheology,
+              "arteriole": run_arteriole}[args.config]
         out = fn(args, ws, rank, local)
         if rank == 0:
             print(json.dumps(out), flush=True)

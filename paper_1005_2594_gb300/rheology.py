@@ -52,6 +52,49 @@ def tube_case(k=1, radius=30.0, length=128, hct=0.35, g=2e-6, R=(7.0, 3.0), seed
     return p, Xk, q, mask
 
 
+# Sec. IV's units: dx = 2/3 um, dt = 6.80e-8 s (tau = 1 with the plasma's
+# kinematic viscosity), dm = 3.05e-16 kg, so that one lattice energy unit is
+# dm dx^2 / dt^2 = 2.93e-14 J
+DX_UM, DT_S = 2.0 / 3.0, 6.80e-8
+E_UNIT_J = 3.05e-16 * (DX_UM * 1e-6) ** 2 / DT_S ** 2
+
+
+def arteriole_case(cells=True, g=8e-6, hct=0.42, eps_w_J=1.47e-16, seed=1010, start="wide"):
+    """Sec. IV's arteriole in lattice units: radius 31 um (46.5 nodes), closed
+    periodically at 43 um (64 nodes); cells of the potential's half-axes
+    sigma_perp = 4 um, sigma_par = 4/3 um (6 and 2 nodes) with coupling
+    half-axes R = 11/12 sigma, cell stiffness 1.47e-15 J, cell-wall stiffness
+    eps_w_J (1.47e-16 J in the paper), cells at hct of the lumen (42 %) on a
+    jittered fcc start; the body force g drives plasma and cells.  The start
+    keeps each centre R_perp + 1 from the wall ("wide": no orientation
+    reaches it) or R_par + 1 ("close": cells lying edge-on to the wall reach
+    into it, and the wall potential pushes them out).  Returns params, X, q,
+    wall mask (X, q empty without cells)."""
+    radius, length = 31.0 / DX_UM, 64
+    n = int(2 * radius + 8)
+    sig = (4.0 / DX_UM, (4.0 / 3.0) / DX_UM)
+    R = (sig[0] * 11.0 / 12.0, sig[1] * 11.0 / 12.0)
+    p = workloads.base_params(length, n, n, periodic=(1, 1, 1), R=R, sigma=sig, eps=1.47e-15 / E_UNIT_J,
+                              eps_w=eps_w_J / E_UNIT_J, g=(g, 0.0, 0.0), body_force_on_cells=1)
+    mask = workloads.tube_mask(p, radius, axis=0)
+    if not cells:
+        return p, np.zeros((0, 3)), np.zeros((0, 4)), mask
+    n_cells = int(round(hct * math.pi * radius ** 2 * length / workloads.cell_volume(p)))
+    c = (n - 1) / 2.0
+    margin = {"wide": R[0], "close": R[1]}[start] + 1.0
+
+    def inside(x):
+        return np.hypot(x[:, 1] - c, x[:, 2] - c) + margin < radius
+
+    X, q = workloads.fcc_cells(p, n_cells, seed, inside)
+    return p, X, q, mask
+
+
+def pseudo_shear_rate(Q, radius):
+    """Sec. IV's pseudo-shear rate Q / (2 pi R^3), in 1/s"""
+    return Q / (2.0 * math.pi * radius ** 3) / DT_S
+
+
 def flux(sim, p):
     """volume flux along x (lattice units)"""
     import torch

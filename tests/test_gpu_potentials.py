@@ -93,3 +93,35 @@ def test_potentials_active_100_steps(geometry, mu):
     assert diverged == 0, "owner-map divergence: %d node-steps" % diverged
     for k, v in errs.items():
         assert v < 1e-5, (k, v)
+
+
+def test_arteriole_matches_oracle():
+    """Sec. IV's arteriole as the bench runs it (radius 46.5 nodes, 786 cells
+    sigma = (6, 2) at 42 % of the lumen overlapping one another and, edge-on,
+    the wall on their fcc start, cell stiffness 0.05 and cell-wall stiffness
+    0.005, body force on plasma and cells): 10 steps against the oracle, owner maps bit-exact every step,
+    then fields, forces and the cell state to 1e-5"""
+    import oracle
+    from paper_1005_2594_gb300 import bloodlb as bl
+    from paper_1005_2594_gb300 import rheology
+
+    p, X, q, mask = rheology.arteriole_case(start="close")
+    orc, sim = oracle.Oracle(p), bl.Simulation(p, wall_mask=mask)
+    orc.set_walls(mask)
+    orc.set_particles(X, q)
+    sim.set_particles(X, q)
+    np.testing.assert_array_equal(sim.owner(), orc.owner())
+    for _ in range(10):
+        orc.step(1)
+        sim.step(1)
+        np.testing.assert_array_equal(sim.owner(), orc.owner())
+    rho_o, u_o, own = orc.fields()
+    rho_g, u_g, _ = sim.fields()
+    fl = own == -1
+    po, pg = orc.particles(), sim.particles()
+    errs = {"u": rel(u_g[fl], u_o[fl]), "rho": rel(rho_g[fl], rho_o[fl])}
+    for k in ("F", "T", "X", "q", "V", "L"):
+        errs[k] = rel(pg[k], po[k])
+    print("arteriole, 10 steps: %s" % {k: "%.2e" % v for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v < 1e-5, (k, v)

@@ -68,3 +68,26 @@ def test_radial_binning_of_lattice_fields():
             assert abs(um[k] - u[sel, 0].mean()) < 1e-15
             assert n[k] == sel.sum()
     assert np.all(H[:8] == 1.0) and np.all(H[9:] == 0.0)
+
+
+def test_arteriole_case_in_lattice_units():
+    """Sec. IV's units and arteriole: dt from tau = 1 and the plasma's
+    kinematic viscosity 1.09e-6 m^2/s at dx = 2/3 um; the cell stiffness
+    1.47e-15 J is 0.05 lattice units; radius 31 um, sigma = (4, 4/3) um,
+    R = 11/12 sigma and 42 % of the lumen in cells, all inside the tube"""
+    dx = rheology.DX_UM * 1e-6
+    assert abs((2 * 1.0 - 1) / 6 * dx * dx / rheology.DT_S - 1.09e-6) < 1e-3 * 1.09e-6
+    p, X, q, mask = rheology.arteriole_case()
+    assert abs(p["eps"] - 0.05) < 5e-4 and abs(p["eps_w"] - 0.005) < 5e-5
+    assert (p["sig_perp"], p["sig_par"]) == (6.0, 2.0)
+    assert abs(p["R_perp"] - 5.5) < 1e-12 and abs(p["R_par"] - 11.0 / 6.0) < 1e-12
+    radius = 31.0 / rheology.DX_UM
+    lumen = math.pi * radius ** 2 * p["nx"]
+    assert abs(len(X) * workloads.cell_volume(p) / lumen - 0.42) < 2e-3
+    c = (p["ny"] - 1) / 2.0
+    assert np.all(np.hypot(X[:, 1] - c, X[:, 2] - c) + p["R_perp"] < radius)
+    assert mask.reshape(p["nz"], p["ny"], p["nx"])[int(c), int(c), :].max() == 0  # the axis is open
+    # the pseudo-shear rate Q / (2 pi R^3) of Poiseuille flow is u_max / (4 R)
+    u_max = rheology.poiseuille(0.0, radius, 1e-6, 1 / 6.0)
+    Q = math.pi * radius ** 2 * u_max / 2
+    assert abs(rheology.pseudo_shear_rate(Q, radius) * rheology.DT_S - u_max / (4 * radius)) < 1e-15

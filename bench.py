@@ -687,11 +687,13 @@ def run_arteriole(args, ws, rank, local):
     and the cell fraction H(r), with the wall radius taken from the plasma
     alone under the same force.  Two fcc starts: centres kept R_perp + 1
     from the wall (no cell reaches it) and R_par + 1 (edge-on cells reach
-    into it); the second also at ten times and a tenth of the cell-wall
-    stiffness, the paper's knob for the layer width."""
+    into it); the second also at 10 and 100 times and a tenth of the
+    cell-wall stiffness, the paper's knob for the layer width.  A run that the
+    library stops as unstable is reported as such."""
     import torch
 
     import __graft_entry__
+    from paper_1005_2594_gb300 import bloodlb as bl
     from paper_1005_2594_gb300 import rheology
 
     __graft_entry__.build()
@@ -706,10 +708,15 @@ def run_arteriole(args, ws, rank, local):
     for name, ew, start in (("wide start, eps_w 1.47e-16 J", 1.47e-16, "wide"),
                             ("close start, eps_w 1.47e-16 J", 1.47e-16, "close"),
                             ("close start, eps_w 1.47e-15 J", 1.47e-15, "close"),
+                            ("close start, eps_w 1.47e-14 J", 1.47e-14, "close"),
                             ("close start, eps_w 1.47e-17 J", 1.47e-17, "close")):
         p, X, q, mask = rheology.arteriole_case(g=g, eps_w_J=ew, start=start)
-        Q, samples, ms, (r_c, u_s, H, n_s) = rheology.run(p, X, q, mask, args.steps,
-                                                          profile_radius=31.0 / rheology.DX_UM)
+        try:
+            Q, samples, ms, (r_c, u_s, H, n_s) = rheology.run(p, X, q, mask, args.steps,
+                                                              profile_radius=31.0 / rheology.DX_UM)
+        except bl.BloodLBError as e:  # the library's stability check (a host-read status)
+            runs[name] = {"eps_w": round(p["eps_w"], 6), "cells": int(len(X)), "failed": str(e)}
+            continue
         d, mr = rheology.fit_axial_train(r_c, u_s, R_eff, f, mu_b, n_s)
         Rc = R_eff - d
         N = p["nx"] * p["ny"] * p["nz"]

@@ -210,18 +210,20 @@ def run(p, X, q, mask, steps, samples=20, model=None, gap_range=None, stream=Non
         e1.synchronize()
         return e0.elapsed_time(e1)
 
-    ms += advance(half)
     out = []
-    done = half
-    while done + every <= steps:
-        ms += advance(every)
-        done += every
-        out.append(flux(sim, p))
-        if profile_radius is not None:
-            _, u, own = sim.fields()
-            prof.append(radial_profiles(u, own, p, profile_radius))
-    sim.sync()
-    sim.close()
+    try:
+        ms += advance(half)
+        done = half
+        while done + every <= steps:
+            ms += advance(every)
+            done += every
+            out.append(flux(sim, p))
+            if profile_radius is not None:
+                _, u, own = sim.fields()
+                prof.append(radial_profiles(u, own, p, profile_radius))
+        sim.sync()
+    finally:
+        sim.close()
     if profile_radius is None:
         return float(np.mean(out)), out, ms
     centres = prof[0][0]

@@ -92,6 +92,9 @@ def lib():
         L.orc_wall.restype = ctypes.c_double
         L.orc_wall.argtypes = [P, D, D, D, D]
         L.orc_integrate_one.argtypes = [P, D, D, D, D, D, D, D]
+        L.orc_set_lees_edwards.restype = ctypes.c_int
+        L.orc_set_lees_edwards.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+        L.orc_get_lees_edwards.argtypes = [vp, D]
         _lib = L
     return _lib
 
@@ -249,6 +252,26 @@ class Oracle:
         lib().orc_get_counters(self._h, _dp(c), _dp(wm))
         return {"sumC": c[0], "mass_created": c[1], "mass_deleted": c[2], "n_covered": int(c[3]),
                 "n_uncovered": int(c[4]), "n_switched": int(c[5]), "t": int(c[6]), "wallmom": wm}
+
+    def set_lees_edwards(self, U, d_reflect=None):
+        """Sec. IV's sheared plane between x = nx-1 and x = 0 (reading Q25):
+        the image above slides along z with velocity offset U; cells reflect
+        within d_reflect of the plane, by default max(sigma_perp, max(R) + 1),
+        so that they never cover a node next to it.  Every axis periodic, no
+        wall node."""
+        p = self.params
+        if d_reflect is None:
+            d_reflect = max(p["sig_perp"], max(p["R_perp"], p["R_par"]) + 1.0)
+        if lib().orc_set_lees_edwards(self._h, float(U), float(d_reflect)) != 0:
+            raise ValueError("Lees-Edwards needs every axis periodic and no wall node")
+
+    def lees_edwards(self):
+        """z-momentum moved along +x across the sheared plane in the last step
+        and summed since it was set, the steps summed, the cell reflections,
+        and the crossings whose source was not fluid"""
+        o = np.zeros(5)
+        lib().orc_get_lees_edwards(self._h, _dp(o))
+        return {"P": o[0], "P_sum": o[1], "steps": int(o[2]), "reflections": int(o[3]), "bad": int(o[4])}
 
     def boundary_links(self):
         n = lib().orc_boundary_links(self._h, None, 0)

@@ -28,6 +28,8 @@
  *   Sec. III, Eq. (phi),(epsilon),(sigma),(sigmaw)
  *                              Berne-Pechukas-scaled Hookean potentials
  *   Sec. II (leap-frog on unit quaternions)
+ *   Sec. IV (Lees-Edwards shear across the x plane, reflective cell
+ *                              boundary, momentum transfer Delta p_LE of Eq. mu)
  *
  * Where the paper is silent the readings are (numbered as in the design notes):
  *   Q1 body force: Guo forcing, u = (j + rho g / 2) / rho
@@ -41,6 +43,10 @@
  *   Q8 neutrally buoyant solid ellipsoid, analytic mass and inertia
  *   Q9 epsilon may carry the Gay-Berne factor eps2^mu (paper: mu = 0, nu = 1)
  *   Q10 a walled axis has solid layers at index 0 and N-1
+ *   Q25 Lees-Edwards: offset D = U t, linear interpolation along z, the
+ *       equilibrium part of a crossing population moved by -+U with its
+ *       source's rho and u; Delta p_LE the mean flux of the two frames; cells
+ *       reflected after the step's coupling, before they move
  *
  * Direction numbering (the interface order, also used by the link lists):
  *   0 (0,0,0); 1..6 (+x,-x,+y,-y,+z,-z); 7..18 the twelve (+-1,+-1,0)-type
@@ -115,6 +121,17 @@ typedef struct {
   double sumC, mass_created, mass_deleted;
   long n_covered, n_uncovered, n_switched;
   long t;
+  double *u; /* N x 3: velocity of the current step's collision */
+  /* Lees-Edwards shear across the plane between x = nx-1 and x = 0 (Sec. IV,
+     reading Q25): the image above (x + nx) is displaced by D = U le_t along z
+     and moves with velocity offset U along z; cells reflect within le_dr of
+     the plane */
+  int le_on;
+  double le_U, le_dr;
+  long le_t;
+  double le_P, le_Psum;   /* z-momentum moved across the plane along +x: last step, summed */
+  long le_n, le_reflect;  /* steps summed, cell reflections so far */
+  long le_bad;            /* crossings whose source was not fluid (the planes must stay fluid) */
 } orc_state;
 
 /* ------------------------------------------------------------------ */
@@ -447,7 +464,7 @@ static void free_particles(orc_state *s) {
 
 void orc_destroy(orc_state *s) {
   if (!s) return;
-  free(s->n); free(s->nstar); free(s->nnew); free(s->rho); free(s->owner);
+  free(s->n); free(s->nstar); free(s->nnew); free(s->rho); free(s->owner); free(s->u);
   free_particles(s);
   free(s);
 }
@@ -474,6 +491,7 @@ orc_state *orc_create(const orc_params *p) {
   s->nstar = (double *)xcalloc(s->N * NQ, sizeof(double));
   s->nnew = (double *)xcalloc(s->N * NQ, sizeof(double));
   s->rho = (double *)xcalloc(s->N, sizeof(double));
+  s->u = (double *)xcalloc(3 * s->N, sizeof(double));
   s->owner = (int32_t *)xcalloc(s->N, sizeof(int32_t));
   double zero[3] = {0, 0, 0}, feq[NQ];
   orc_equilibrium(p->rho0, zero, feq); /* resting fluid at rho_bar */
@@ -615,6 +633,66 @@ int orc_set_particles(orc_state *s, int np, const double *X, const double *q, co
 /* ------------------------------------------------------------------ */
 /* one coupled time step                                               */
 
+/* ------------------------------------------------------------------ */
+/* Lees-Edwards shear (Sec. IV, reading Q25)                           */
+
+/* post-collision population r of fluid node src carried into a frame moving
+   with du_z along z relative to the node: its equilibrium part is moved,
+   n*_r + n^eq_r(rho, u + du_z e_z) - n^eq_r(rho, u) */
+static double le_shifted(const orc_state *s, long src, int r, double du_z) {
+  double u2[3] = {s->u[3 * src], s->u[3 * src + 1], s->u[3 * src + 2] + du_z};
+  double fa[NQ], fb[NQ];
+  orc_equilibrium(s->rho[src], &s->u[3 * src], fa);
+  orc_equilibrium(s->rho[src], u2, fb);
+  return s->nstar[src * NQ + r] + (fb[r] - fa[r]);
+}
+
+/* population r arriving at fluid node y across the plane.  Into x = 0 (c_r,x
+   = +1) it comes from the image below, displaced by -D and moving with -U: its
+   source is the node (nx-1, y - c_y, z - c_z + D) of this box, shifted by -U;
+   into x = nx-1 (c_r,x = -1) from the image above: (0, y - c_y, z - c_z - D),
+   shifted by +U.  D = U t (mod nz) falls between two nodes along z, whose
+   values are interpolated linearly. */
+static double le_crossing(orc_state *s, long y, int r) {
+  const orc_params *p = &s->p;
+  int yi = (int)((y / p->nx) % p->ny), zi = (int)(y / ((long)p->nx * p->ny));
+  int up = CX[r] == 1;
+  double D = fmod(s->le_U * (double)s->le_t, (double)p->nz);
+  double zs = (double)(zi - CZ[r]) + (up ? D : -D);
+  double z0 = floor(zs), w = zs - z0;
+  int xs = up ? p->nx - 1 : 0, ys = wrap(yi - CY[r], p->ny);
+  int za = (((int)z0 % p->nz) + p->nz) % p->nz, zb = (za + 1) % p->nz;
+  long s0 = node_index(p, xs, ys, za), s1 = node_index(p, xs, ys, zb);
+  if (s->owner[s0] != FLUID || s->owner[s1] != FLUID) s->le_bad++;
+  double du = up ? -s->le_U : s->le_U;
+  return (1.0 - w) * le_shifted(s, s0, r, du) + w * le_shifted(s, s1, r, du);
+}
+
+/* switch the shear on: offset U, reflection distance dr; every axis
+   periodic and no wall node (the planes must hold fluid).  0 or -1. */
+int orc_set_lees_edwards(orc_state *s, double U, double dr) {
+  const orc_params *p = &s->p;
+  if (!p->periodic[0] || !p->periodic[1] || !p->periodic[2]) return -1;
+  for (long i = 0; i < s->N; ++i)
+    if (IS_WALL(s->owner[i])) return -1;
+  s->le_on = 1;
+  s->le_U = U;
+  s->le_dr = dr;
+  s->le_t = 0;
+  s->le_P = s->le_Psum = 0.0;
+  s->le_n = s->le_reflect = s->le_bad = 0;
+  return 0;
+}
+
+/* {P of the last step, P summed, steps summed, reflections, bad crossings} */
+void orc_get_lees_edwards(const orc_state *s, double out[5]) {
+  out[0] = s->le_P;
+  out[1] = s->le_Psum;
+  out[2] = (double)s->le_n;
+  out[3] = (double)s->le_reflect;
+  out[4] = (double)s->le_bad;
+}
+
 static void step_once(orc_state *s) {
   orc_params *p = &s->p;
   const long N = s->N;
@@ -641,6 +719,27 @@ static void step_once(orc_state *s) {
     for (int r = 0; r < NQ; ++r)
       ns[r] = ni[r] - (ni[r] - feq[r]) / p->tau + (1.0 - 1.0 / (2.0 * p->tau)) * S[r];
     s->rho[i] = rho;
+    for (int k = 0; k < 3; ++k) s->u[3 * i + k] = u[k];
+  }
+
+  /* 2b. Lees-Edwards momentum transfer of this step (reading Q25): the
+     z-momentum flux along +x through the plane, as the mean of its value in
+     the frame below the plane and in the frame above it */
+  if (s->le_on) {
+    double P = 0.0;
+    for (int z = 0; z < p->nz; ++z)
+      for (int y = 0; y < p->ny; ++y) {
+        long top = node_index(p, p->nx - 1, y, z), bot = node_index(p, 0, y, z);
+        for (int r = 1; r < NQ; ++r) {
+          if (CX[r] == 1 && s->owner[top] == FLUID)
+            P += 0.5 * CZ[r] * (s->nstar[top * NQ + r] + le_shifted(s, top, r, -s->le_U));
+          if (CX[r] == -1 && s->owner[bot] == FLUID)
+            P -= 0.5 * CZ[r] * (s->nstar[bot * NQ + r] + le_shifted(s, bot, r, s->le_U));
+        }
+      }
+    s->le_P = P;
+    s->le_Psum += P;
+    s->le_n++;
   }
 
   /* 3. contact links, Eq. (deltapppp),(deltapppm): each solid node of p with a
@@ -774,7 +873,11 @@ static void step_once(orc_state *s) {
       long x = neighbour(p, y, r, -1); /* source node x = y - c_r */
       int32_t ox = s->owner[x];
       if (ox == FLUID) {
-        s->nnew[y * NQ + r] = s->nstar[x * NQ + r];
+        int xi = (int)(y % p->nx);
+        if (s->le_on && ((CX[r] == 1 && xi == 0) || (CX[r] == -1 && xi == p->nx - 1)))
+          s->nnew[y * NQ + r] = le_crossing(s, y, r);
+        else
+          s->nnew[y * NQ + r] = s->nstar[x * NQ + r];
         continue;
       }
       int rb = opposite(r);
@@ -818,12 +921,24 @@ static void step_once(orc_state *s) {
       s->Ttot[3 * i + k] = s->Th[3 * i + k] + s->Tp[3 * i + k] + s->PT[3 * i + k];
       s->PF[3 * i + k] = s->PT[3 * i + k] = 0.0;
     }
+    /* Sec. IV: a cell whose centre is closer than le_dr to the sheared plane
+       (x = -1/2, i.e. nx - 1/2) has its normal velocity negated if it moves
+       toward the plane; the step's coupling used the velocity of the solve,
+       the cell moves with the reflected one (reading Q25) */
+    if (s->le_on && p->move_particles == 1) {
+      double lo = s->X[3 * i] + 0.5, hi = (double)p->nx - 0.5 - s->X[3 * i];
+      if ((lo < s->le_dr && s->V[3 * i] < 0.0) || (hi < s->le_dr && s->V[3 * i] > 0.0)) {
+        s->V[3 * i] = -s->V[3 * i];
+        s->le_reflect++;
+      }
+    }
     if (p->move_particles) rigid_advance(p, &s->X[3 * i], &s->q[4 * i], &s->V[3 * i], &s->Om[3 * i]);
   }
 
   /* 7. re-discretise with the first-arrival rule, fill/drain */
   if (s->np > 0 && p->move_particles) rediscretise(s, 0);
   s->t++;
+  if (s->le_on) s->le_t++;
 }
 
 void orc_step(orc_state *s, int nsteps) {

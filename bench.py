@@ -219,6 +219,13 @@ def make_workload(name):
 
         p, X, q, mask = rheology.tube_case(1)
         return p, X, q, mask, "tube radius 30, length 128, %d (7,7,3) cells at 35 %% of the lumen, g = 2e-6" % len(X)
+    if name == "le_shear":
+        from paper_1005_2594_gb300 import rheology
+
+        p, X, q = rheology.le_shear_case()
+        p["le_U"] = LE_U
+        return p, X, q, None, "Lees-Edwards shear cell 128x40x40, offset %g, %d (5.5,5.5,1.83) cells at 56 %%" % (
+            LE_U, len(X))
     if name == "arteriole":
         from paper_1005_2594_gb300 import rheology
 
@@ -750,6 +757,50 @@ def run_arteriole(args, ws, rank, local):
     }
 
 
+# Lees-Edwards offset of the shear cell: Sec. IV's shear rate 2.21e3 / s is
+# 1.50e-4 per step (dt = 6.80e-8 s), times l_x = 128
+LE_U = 0.0192
+
+
+def run_le_shear(args, ws, rank, local):
+    """Sec. IV's apparent viscosity in plane Couette flow (Eq. mu): the shear
+    cell 128 x 40 x 40 under the Lees-Edwards offset LE_U, from rest for
+    --steps steps (60000: a strain of about 9), plasma alone (mu_rel must be
+    1) and the suspension of 388 cells at the paper's 56 %; Delta p_LE and the
+    shear rate (linear fit over the central half) averaged over the second
+    half.  value: MLUPS of the suspension's stepping."""
+    import torch
+
+    import __graft_entry__
+    from paper_1005_2594_gb300 import rheology
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    runs = {}
+    for name, cells in (("plasma", False), ("suspension", True)):
+        p, X, q = rheology.le_shear_case(cells=cells)
+        r = rheology.run_le(p, X, q, LE_U, args.steps)
+        N = p["nx"] * p["ny"] * p["nz"]
+        runs[name] = {"cells": int(len(X)), "mu_rel": round(r["mu_rel"], 4),
+                      "gamma_dot_per_step": r["gamma_dot"], "gamma_dot_per_s": round(r["gamma_dot_per_s"], 1),
+                      "P_per_step": r["P_per_step"], "mlups": round(N * args.steps / (r["ms"] * 1e-3) / 1e6, 1),
+                      "profile": [round(float(v), 7) for v in r["profile"]]}
+    s = runs["suspension"]
+    return {
+        "metric": METRIC, "value": s["mlups"], "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (jittered fcc start, resting plasma)",
+        "config": {"workload": "Lees-Edwards shear cell 128x40x40, offset %g, %d cells sigma (6,2) R = 11/12 sigma "
+                               "at the paper's 6.4e15 / m^3 (56 %%); value: MLUPS of the suspension's stepping"
+                               % (LE_U, s["cells"]), "U": LE_U},
+        "lees_edwards": {"runs": runs,
+                         "paper": {"gamma_dot_per_s": "2.21e3 +- 0.08e3"},
+                         "note": "mu_rel = -<Delta p_LE> / (l_y l_z gamma_dot mu), Eq. (mu), over the second half; "
+                                 "gamma_dot from a linear fit of v_z(x) over the central half"},
+        "roofline": None,
+    }
+
+
 def run_e2e(sim, n, N, steps, stream):
     import torch
 
@@ -791,6 +842,8 @@ def _oracle_worker(p, X, q, mask, warmup, steps, barrier, out):
     o = oracle.Oracle(p)
     if mask is not None:
         o.set_walls(mask)
+    if "le_U" in p:  # the Lees-Edwards shear cell
+        o.set_lees_edwards(p["le_U"])
     o.set_particles(X, q)
     o.step(warmup)
     barrier.wait()
@@ -875,7 +928,7 @@ def run_reference(args, ws, rank):
         return None
     p, X, q, _mask, desc = make_workload(args.config)
     steps, warmup = args.steps, args.warmup
-    if args.config in ("tube_rheology", "arteriole"):
+    if args.config in ("tube_rheology", "arteriole", "le_shear"):
         # the whole tube (under a second per oracle step): as many steps as fit
         sp, sX, sq, smask = p, X, q, _mask
         steps, warmup = max(1, min(steps, 100)), min(warmup, 3)
@@ -911,7 +964,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--config", default="shear128", choices=["shear128", "small32", "duct256", "ensemble64", "tube512", "tube_rheology",
-                                                          "arteriole"])
+                                                          "arteriole", "le_shear"])
     ap.add_argument("--store", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--sweep", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
                     help="sweep variant (default: the library's choice for the row length and storage)")
@@ -927,9 +980,9 @@ def main():
         if rank == 0:
             print(json.dumps(out), flush=True)
         return
-    if args.config in ("ensemble64", "tube512", "tube_rheology", "arteriole"):
+    if args.config in ("ensemble64", "tube512", "tube_rheology", "arteriole", "le_shear"):
         fn = {"ensemble64": run_ensemble, "tube512": run_learned, "tube_rheology": run_rheology,
-              "arteriole": run_arteriole}[args.config]
+              "arteriole": run_arteriole, "le_shear": run_le_shear}[args.config]
         out = fn(args, ws, rank, local)
         if rank == 0:
             print(json.dumps(out), flush=True)

@@ -165,6 +165,33 @@ int bl_force_parts_get(bl_ctx *c, double *Fh, double *Th, double *Fp, double *Tp
    doubles, host); the momentum-transfer observable of Eq. (mu). */
 int bl_wall_momentum_get(bl_ctx *c, double *wallmom);
 
+/* Lees-Edwards shear (Sec. IV, the plane Couette cells of its rheology):
+   the periodic images of the box along x slide past each other in z, the
+   image above moving with velocity offset U (lattice units, |U| < 0.3) and
+   displaced by U t after t steps.  A population crossing the plane between
+   x = nx-1 and x = 0 comes from the neighbouring image, from a point U t
+   along z from its periodic source (linear interpolation between the two
+   nearest nodes), its equilibrium part carried into this image's frame,
+   n + n^eq(rho, u -+ U e_z) - n^eq(rho, u) with its source node's moments
+   (reading Q25).  A free cell whose centre comes closer than d_reflect to
+   the plane (x = -1/2) while moving toward it has its x velocity negated
+   before it moves (Sec. IV; the step's coupling used the solved velocity);
+   d_reflect <= 0 takes max(sigma_perp, max(R_perp, R_par) + 1), so that no
+   cell covers a node beside the plane.  Every axis must be periodic and no
+   wall mask set (BL_EINVAL / BL_ESTATE); a node beside the plane that is not
+   fluid during a step is reported by bl_sync as BL_ESTATE.  A later call
+   sets a new U and restarts t and the momentum sums.  The sweep keeps its
+   variant; two small passes over the two planes follow each sweep. */
+int bl_lees_edwards_set(bl_ctx *c, double U, double d_reflect);
+
+/* The z-momentum moved along +x across the sheared plane, summed over the
+   steps since bl_lees_edwards_set, and the number of steps (host scalars).
+   Per step it is the flux of the crossing post-collision populations, the
+   mean of its value in the frame below the plane and in the frame above it;
+   in steady shear it is -mu gamma_dot l_y l_z, so that Eq. (mu) reads
+   mu_app = -Delta p_LE / (l_y l_z gamma_dot).  Waits on the stream. */
+int bl_lees_edwards_get(bl_ctx *c, double *P_sum, int64_t *steps);
+
 /* Checkpoint of the fluid: node-major host array N x 19 doubles, the
    unshifted populations n_r(x, t) in the direction order above; non-fluid
    nodes read as 0 and are ignored on set. */

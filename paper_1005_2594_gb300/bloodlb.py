@@ -32,7 +32,8 @@ TIMING_GROUPS = ("lattice_sweep", "cell_list", "potentials", "leapfrog_claims", 
 
 ABI_FUNCTIONS = (
     "bl_lb_init", "bl_walls_set", "bl_particles_set", "bl_step", "bl_fields_get", "bl_forces_get",
-    "bl_force_parts_get", "bl_wall_momentum_get", "bl_populations_get", "bl_populations_set",
+    "bl_force_parts_get", "bl_wall_momentum_get", "bl_lees_edwards_set", "bl_lees_edwards_get",
+    "bl_populations_get", "bl_populations_set",
     "bl_boundary_links_get", "bl_contact_links_get", "bl_cell_links_get", "bl_cell_list_get", "bl_cell_list_build_static",
     "bl_sweep_variant", "bl_autotune", "bl_ensemble_create", "bl_ensemble_step", "bl_ensemble_sync",
     "bl_ensemble_destroy", "bl_mlp_create", "bl_mlp_params_set", "bl_mlp_params_get", "bl_mlp_forward",
@@ -94,6 +95,8 @@ def lib():
         "bl_forces_get": (ctypes.c_int, [vp, D, D, D, D, D, D]),
         "bl_force_parts_get": (ctypes.c_int, [vp, D, D, D, D, D, D, D]),
         "bl_wall_momentum_get": (ctypes.c_int, [vp, D]),
+        "bl_lees_edwards_set": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double]),
+        "bl_lees_edwards_get": (ctypes.c_int, [vp, D, ctypes.POINTER(i64)]),
         "bl_populations_get": (ctypes.c_int, [vp, D]),
         "bl_populations_set": (ctypes.c_int, [vp, D]),
         "bl_boundary_links_get": (ctypes.c_int, [vp, I, i64, ctypes.POINTER(i64)]),
@@ -362,6 +365,17 @@ def bl_wall_momentum_get(ctx):
     return out
 
 
+def bl_lees_edwards_set(ctx, U, d_reflect=0.0):
+    _check(ctx, lib().bl_lees_edwards_set(ctx, float(U), float(d_reflect)))
+
+
+def bl_lees_edwards_get(ctx):
+    P = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(ctx, lib().bl_lees_edwards_get(ctx, ctypes.byref(P), ctypes.byref(n)))
+    return P.value, int(n.value)
+
+
 def bl_populations_get(ctx, N):
     pop = np.zeros((N, 19))
     _check(ctx, lib().bl_populations_get(ctx, _dp(pop)))
@@ -509,6 +523,16 @@ class Simulation:
 
     def wall_momentum(self):
         return bl_wall_momentum_get(self.ctx)
+
+    def lees_edwards(self, U, d_reflect=0.0):
+        """shear the box across the plane between x = nx-1 and x = 0 with
+        velocity offset U along z (Sec. IV); d_reflect <= 0: the default
+        reflection distance"""
+        bl_lees_edwards_set(self.ctx, U, d_reflect)
+
+    def lees_edwards_momentum(self):
+        """(z-momentum moved along +x across the plane, summed; steps summed)"""
+        return bl_lees_edwards_get(self.ctx)
 
     def autotune(self, trial_steps=20):
         return bl_autotune(self.ctx, trial_steps)

@@ -112,6 +112,21 @@ struct LatticeView {
   int *rec_count;          // ncells
   int rec_cap;
   int *status;
+  // Lees-Edwards shear (null when off): the sweep leaves (drho, u) of the
+  // nodes at x = 0 (first ny nz) and x = nx - 1 (next ny nz), y + ny z
+  float4 *le_mom;
+};
+
+// Lees-Edwards shear across the plane between x = nx - 1 and x = 0 (Sec. IV,
+// reading Q25): the image above moves with velocity offset U along z and is
+// displaced by U t
+struct LeView {
+  double U;
+  double *D;     // offset of the pass in flight: written by the gather, read by the scatter
+  long long *t;  // steps since the shear was set
+  double *P;     // z-momentum moved along +x across the plane, summed over the steps
+  long long *n;  // steps summed
+  float *T;      // 2 x 5 x ny nz crossing populations of the two planes, shifted to the other frame
 };
 
 // A link record (two float4): node n (bits of .x), direction mask (bits of
@@ -174,6 +189,7 @@ struct PartView {
   double m, Iperp, Ipar, rho0;
   double g[3];
   int bfc, move;
+  double le_dr;  // Lees-Edwards: reflect a cell within le_dr of the sheared plane (0: no shear)
   double inv_rpar2, inv_rperp2, R_par, R_perp;
   float sig_par, sig_perp, eps, eps_w, mu, nu, chi_prime, r_cut;
   float chi, sigbar, sigbar_w, chi_w, sigw_max;
@@ -260,11 +276,14 @@ void launch_mlp_correction(const LatticeView &lv, const PartView &pv, const Cell
                            cudaStream_t st, int64_t *nl);
 // forward pass of a bl_mlp over *count rows of x (at most cap), raw units
 void launch_mlp_forward_dev(const void *mlp, const float *x, const int *count, int cap, float *y, cudaStream_t st);
+// the Lees-Edwards passes after a sweep of parity par
+void launch_lees_edwards(int dtype, const LatticeView &lv, const LeView &le, int par, cudaStream_t st, int64_t *nl);
 
 // bit flags of the device status word
 constexpr int ST_UNSTABLE = 1;
 constexpr int ST_OVERFLOW = 2;
 constexpr int ST_BARRIER = 4;  // a bounded wait on an mbarrier gave up
+constexpr int ST_LEPLANE = 8;  // a node beside the Lees-Edwards plane is not fluid
 
 // ---------------------------------------------------------------------------
 // exact FP64 geometry (no contraction), matching the operation order of the

@@ -82,6 +82,12 @@ struct bl_ctx {
   double *scratch;
   size_t scratch_bytes;
   // timing
+  // Lees-Edwards shear (bl_lees_edwards_set): its passes run after every
+  // sweep; masked: a wall mask was set (the shear needs fluid planes)
+  LeView le;
+  int le_on;
+  double le_dr_req;  // reflection distance asked for (<= 0: the default)
+  int masked;
   int timing;
   int sweep_fixed;  // the sweep variant was set (bl_sweep_variant, bl_autotune), not chosen here
   std::vector<cudaEvent_t> ev;  // pairs
@@ -92,6 +98,8 @@ struct bl_ctx {
 };
 
 static void drop_graph(bl_ctx *c);
+static int read_status(bl_ctx *c);
+static void fill_particle_constants(bl_ctx *c);
 
 static int fail(bl_ctx *c, int code, const char *fmt, ...) {
   if (c && c->sticky == BL_OK) {
@@ -327,6 +335,10 @@ extern "C" int bl_walls_set(bl_ctx *c, const uint8_t *mask) {
   if (c->np > 0) return fail(c, BL_ESTATE, "bl_walls_set after bl_particles_set");
   for (size_t i = 0; i < c->lv.N; ++i)
     if (mask[i] > bl::NWALL) return fail(c, BL_EINVAL, "wall mask value %d > 8 at node %zu", (int)mask[i], i);
+  bool any = false;
+  for (size_t i = 0; i < c->lv.N && !any; ++i) any = mask[i] != 0;
+  if (any && c->le_on) return fail(c, BL_ESTATE, "bl_walls_set with a Lees-Edwards shear (its planes must hold fluid)");
+  if (any) c->masked = 1;
   uint8_t *d = nullptr;
   CU(cudaMalloc(&d, c->lv.N));
   CU(cudaMemcpyAsync(d, mask, c->lv.N, cudaMemcpyHostToDevice, c->stream));
@@ -467,6 +479,11 @@ static void fill_particle_constants(bl_ctx *c) {
   pv.status = c->status;
   pv.bfc = c->lp.body_force_on_cells ? 1 : 0;
   pv.move = pp.move_particles;
+  // Sec. IV's reflection distance sigma_perp, raised to max(R) + 1 so that no
+  // cell covers a node beside the sheared plane (reading Q25)
+  pv.le_dr = !c->le_on ? 0.0
+                       : (c->le_dr_req > 0.0 ? c->le_dr_req
+                                             : fmax(pp.sig_perp, fmax(pp.R_perp, pp.R_par) + 1.0));
   pv.inv_rpar2 = 1.0 / (pp.R_par * pp.R_par);
   pv.inv_rperp2 = 1.0 / (pp.R_perp * pp.R_perp);
   pv.R_par = pp.R_par;
@@ -594,6 +611,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     launch_lb_step(c->dtype, c->lv, c->parity, c->wacc, c->status, st);
     group_end(c, slot, st);
     c->launches++;
+    if (c->le_on) launch_lees_edwards(c->dtype, c->lv, c->le, c->parity, st, &c->launches);
   }
   if (c->np > 0) {
     // cell list and potentials from the state at t, beside the sweep; on a
@@ -621,6 +639,7 @@ static int enqueue_step(bl_ctx *c, cudaStream_t st) {
     launch_lb_step(c->dtype, c->lv, c->parity, c->wacc, c->status, st);
     group_end(c, slot, st);
     c->launches++;
+    if (c->le_on) launch_lees_edwards(c->dtype, c->lv, c->le, c->parity, st, &c->launches);
   }
   if (c->np > 0) {
     cudaStreamWaitEvent(st, c->ev_join, 0);
@@ -754,6 +773,43 @@ extern "C" int bl_step(bl_ctx *c, int nsteps) {
   return BL_OK;
 }
 
+extern "C" int bl_lees_edwards_set(bl_ctx *c, double U, double d_reflect) {
+  if (!c || !(fabs(U) < 0.3) || !(d_reflect == d_reflect)) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (!c->lv.per[0] || !c->lv.per[1] || !c->lv.per[2])
+    return fail(c, BL_EINVAL, "Lees-Edwards shear needs every axis periodic");
+  if (c->masked) return fail(c, BL_ESTATE, "Lees-Edwards shear with a wall mask (its planes must hold fluid)");
+  const size_t M = (size_t)c->lv.ny * c->lv.nz;
+  if (!c->le_on) {
+    if (cudaMalloc(&c->lv.le_mom, sizeof(float4) * 2 * M) != cudaSuccess ||
+        cudaMalloc(&c->le.T, sizeof(float) * 10 * M) != cudaSuccess ||
+        cudaMalloc(&c->le.D, sizeof(double)) != cudaSuccess || cudaMalloc(&c->le.t, sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&c->le.P, sizeof(double)) != cudaSuccess || cudaMalloc(&c->le.n, sizeof(long long)) != cudaSuccess)
+      return fail(c, BL_ENOMEM, "Lees-Edwards buffers");
+  }
+  CU(cudaMemsetAsync(c->le.t, 0, sizeof(long long), c->stream));
+  CU(cudaMemsetAsync(c->le.P, 0, sizeof(double), c->stream));
+  CU(cudaMemsetAsync(c->le.n, 0, sizeof(long long), c->stream));
+  c->le.U = U;
+  c->le_on = 1;
+  c->le_dr_req = d_reflect;
+  if (c->np > 0) fill_particle_constants(c);
+  drop_graph(c);  // the graphs hold the views by value
+  return BL_OK;
+}
+
+extern "C" int bl_lees_edwards_get(bl_ctx *c, double *P_sum, int64_t *steps) {
+  if (!c || !P_sum || !steps) return BL_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (!c->le_on) return fail(c, BL_ESTATE, "no Lees-Edwards shear set");
+  long long n = 0;
+  CU(cudaMemcpyAsync(P_sum, c->le.P, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(&n, c->le.n, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  *steps = (int64_t)n;
+  return read_status(c);
+}
+
 static int read_status(bl_ctx *c) {
   int st = 0;
   CU(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -761,6 +817,7 @@ static int read_status(bl_ctx *c) {
   if (st & ST_UNSTABLE) return fail(c, BL_EUNSTABLE, "unstable: rho <= 0, NaN or |u| >= 0.3 at some node, or a cell speed >= 0.5");
   if (st & ST_OVERFLOW) return fail(c, BL_EOVERFLOW, "internal list overflow");
   if (st & ST_BARRIER) return fail(c, BL_EBARRIER, "a bounded wait for asynchronous copies timed out");
+  if (st & ST_LEPLANE) return fail(c, BL_ESTATE, "a node beside the Lees-Edwards plane is not fluid (a cell reached it)");
   return BL_OK;
 }
 
@@ -1260,7 +1317,8 @@ extern "C" void bl_destroy(bl_ctx *c) {
   if (c->side2) cudaStreamDestroy(c->side2);
   free_particles(c);
   void *ptrs[] = {c->lv.pop, c->lv.owner, c->lv.nbm, c->lv.nbc, c->lv.pu, c->claim, c->status,
-                  c->wacc.F, c->wacc.K, c->sbits.bits, c->sbits.rows, c->scratch};
+                  c->wacc.F, c->wacc.K, c->sbits.bits, c->sbits.rows, c->scratch,
+                  c->lv.le_mom, c->le.T, c->le.D, c->le.t, c->le.P, c->le.n};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);

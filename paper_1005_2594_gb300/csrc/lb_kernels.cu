@@ -382,4 +382,153 @@ void launch_links(const LatticeView &lv, int contact, int pass, int *block_count
   k_links<<<nblk(lv.N, 256), 256, 0, st>>>(lv, contact, pass, block_count, block_off, out, cap);
 }
 
+
+// ---------------------------------------------------------------------------
+// Lees-Edwards shear (Sec. IV, reading Q25).  The images of the box along x
+// slide past each other in z: the image above moves with velocity offset U
+// and is displaced by D = U t (mod nz).  A population crossing the plane
+// between x = nx - 1 and x = 0 therefore comes from the neighbouring image,
+// from a point D along z from its periodic source -- between two nodes,
+// interpolated linearly -- with its equilibrium part carried into this
+// image's frame: n + n^eq(rho, u -+ U e_z) - n^eq(rho, u), with the moments of
+// its source node.  Into x = 0 (c_x = +1) the source is
+// (nx - 1, y - c_y, z - c_z + D) and the shift -U; into x = nx - 1 (c_x = -1)
+// it is (0, y - c_y, z - c_z - D) and the shift +U.
+//
+// The sweep streams the crossing populations periodically; after each sweep
+// two passes put the sheared values where the next read takes them.  After
+// an even sweep (in place) population r of node s waits in slot rbar of s,
+// and the odd sweep's node s + c_r reads it there; after an odd sweep it was
+// written to slot r of s + c_r, where the even sweep reads it.  The gather
+// forms each crossing population's shifted value from the moments the sweep
+// left for its node (and the plane's momentum transfer); the scatter
+// interpolates along z and writes the slots.  Both planes must hold fluid
+// (ST_LEPLANE otherwise): the host allows no wall node, and cells are
+// reflected before they reach them.
+
+// the five directions with c_x = +1, and their opposites (c_x = -1)
+__device__ constexpr int kLeUp[5] = {1, 7, 9, 11, 13};
+__device__ constexpr int kLeDn[5] = {2, 8, 10, 12, 14};
+static_assert(D3Q19::cx(1) == 1 && D3Q19::cx(7) == 1 && D3Q19::cx(9) == 1 && D3Q19::cx(11) == 1 &&
+                  D3Q19::cx(13) == 1,
+              "c_x = +1 directions");
+static_assert(D3Q19::opp(1) == 2 && D3Q19::opp(7) == 8 && D3Q19::opp(9) == 10 && D3Q19::opp(11) == 12 &&
+                  D3Q19::opp(13) == 14,
+              "their opposites");
+
+// t_r(u) of the third-order equilibrium n^eq_r = w_r rho (1 + t_r(u))
+__device__ __forceinline__ float eq_t(float cu, float uu) {
+  return cu * (3.0f + 4.5f * cu * cu - 4.5f * uu) + 4.5f * cu * cu - 1.5f * uu;
+}
+
+template <int PAR>
+__device__ __forceinline__ unsigned le_node_plus(const LatticeView &lv, int x, int y, int z, int r) {
+  // node x + c_r (periodic) for the odd sweep's write target
+  using D = D3Q19;
+  const int xx = x + D::cx(r), yy = y + D::cy(r), zz = z + D::cz(r);
+  const int xw = xx < 0 ? xx + lv.nx : (xx >= lv.nx ? xx - lv.nx : xx);
+  const int yw = yy < 0 ? yy + lv.ny : (yy >= lv.ny ? yy - lv.ny : yy);
+  const int zw = zz < 0 ? zz + lv.nz : (zz >= lv.nz ? zz - lv.nz : zz);
+  return (unsigned)xw + (unsigned)lv.nx * ((unsigned)yw + (unsigned)lv.ny * (unsigned)zw);
+}
+
+// one thread per node of the two planes: x = 0 (pl 0, its c_x = -1
+// populations cross) and x = nx - 1 (pl 1, c_x = +1)
+template <class S, int PAR>
+__global__ void __launch_bounds__(128) k_le_gather(LatticeView lv, LeView le) {
+  using D = D3Q19;
+  const int ny = lv.ny, M = lv.ny * lv.nz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const S *pop = reinterpret_cast<const S *>(lv.pop);
+  float Pc = 0.f;
+  if (i < 2 * M) {
+    const int pl = i >= M ? 1 : 0;
+    const int yz = i - pl * M, y = yz % ny, z = yz / ny;
+    const int x = pl ? lv.nx - 1 : 0;
+    const unsigned n = (unsigned)x + (unsigned)lv.nx * (unsigned)yz;
+    if (!(lv.nbm[n] & NB_FLUID)) atomicOr(lv.status, ST_LEPLANE);
+    const float4 m = lv.le_mom[i];
+    const float rho = lv.rho0 + m.x;
+    const float uz2 = m.w + (pl ? -(float)le.U : (float)le.U);
+    const float uu = m.y * m.y + m.z * m.z + m.w * m.w, uu2 = m.y * m.y + m.z * m.z + uz2 * uz2;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int r = pl ? kLeUp[k] : kLeDn[k];
+      const float cx = (float)D::cx(r), cy = (float)D::cy(r), cz = (float)D::cz(r);
+      const unsigned slot = PAR == 0 ? (unsigned)D::opp(r) * lv.N + n : (unsigned)r * lv.N + le_node_plus<PAR>(lv, x, y, z, r);
+      const float f = Store<S>::ld(pop + slot);
+      const float cu = cx * m.y + cy * m.z + cz * m.w, cu2 = cx * m.y + cy * m.z + cz * uz2;
+      const float dT = ((float)D::m(r) / 36.0f) * rho * (eq_t(cu2, uu2) - eq_t(cu, uu));
+      le.T[(size_t)(pl * 5 + k) * M + yz] = f + dT;
+      // z-momentum flux along +x through the plane, mean of the frame below
+      // (c_x = +1 after the shift, c_x = -1 before) and above (the reverse)
+      Pc += (pl ? 0.5f : -0.5f) * cz * (2.0f * f + dT);
+    }
+  }
+  const float ws = warp_sum(Pc);
+  if ((threadIdx.x & 31) == 0 && ws != 0.f) atomicAdd(le.P, (double)ws);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *le.D = fmod(le.U * (double)*le.t, (double)lv.nz);
+    *le.t += 1;
+    *le.n += 1;
+  }
+}
+
+// one thread per node of the two planes: x = 0 (pl 0) receives the c_x = +1
+// populations of x = nx - 1, x = nx - 1 (pl 1) the c_x = -1 ones of x = 0
+template <class S, int PAR>
+__global__ void __launch_bounds__(128) k_le_scatter(LatticeView lv, LeView le) {
+  using D = D3Q19;
+  const int ny = lv.ny, nz = lv.nz, M = lv.ny * lv.nz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * M) return;
+  S *pop = reinterpret_cast<S *>(lv.pop);
+  const int pl = i >= M ? 1 : 0;
+  const int yz = i - pl * M, y = yz % ny, z = yz / ny;
+  const int x = pl ? lv.nx - 1 : 0;
+  const unsigned n = (unsigned)x + (unsigned)lv.nx * (unsigned)yz;
+  const double Dz = pl ? -*le.D : *le.D;
+  const float *T = le.T + (size_t)(pl ? 0 : 5) * M;  // sources: x = 0 for pl 1, x = nx - 1 for pl 0
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int r = pl ? kLeDn[k] : kLeUp[k];
+    const double zs = (double)(z - D::cz(r)) + Dz;
+    const double z0 = floor(zs);
+    const float w = (float)(zs - z0);
+    int za = (int)z0 % nz;
+    za = za < 0 ? za + nz : za;
+    const int zb = za + 1 == nz ? 0 : za + 1;
+    int ys = y - D::cy(r);
+    ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+    const float a = T[(size_t)k * M + ys + ny * za], b = T[(size_t)k * M + ys + ny * zb];
+    const float v = fmaf(w, b - a, a);
+    // where the next sweep reads population r of node n
+    const unsigned slot = PAR == 0 ? (unsigned)D::opp(r) * lv.N + le_node_plus<PAR>(lv, x, y, z, D::opp(r))
+                                   : (unsigned)r * lv.N + n;
+    Store<S>::st(pop + slot, v);
+  }
+}
+
+void launch_lees_edwards(int dtype, const LatticeView &lv, const LeView &le, int par, cudaStream_t st,
+                         int64_t *nl) {
+  const unsigned b = 128, g = nblk(2u * (unsigned)lv.ny * (unsigned)lv.nz, b);
+#define BL_LE(S_)                                                   \
+  if (par == 0) {                                                   \
+    k_le_gather<S_, 0><<<g, b, 0, st>>>(lv, le);                    \
+    k_le_scatter<S_, 0><<<g, b, 0, st>>>(lv, le);                   \
+  } else {                                                          \
+    k_le_gather<S_, 1><<<g, b, 0, st>>>(lv, le);                    \
+    k_le_scatter<S_, 1><<<g, b, 0, st>>>(lv, le);                   \
+  }
+  if (dtype == 0) {
+    BL_LE(float)
+  } else if (dtype == 1) {
+    BL_LE(__nv_bfloat16)
+  } else {
+    BL_LE(__half)
+  }
+#undef BL_LE
+  if (nl) *nl += 2;
+}
+
 }  // namespace bl

@@ -315,6 +315,10 @@ __device__ __forceinline__ void node_update(const LatticeView &lv, const WallAcc
     const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv, uz = (jz + 0.5f * Fz) * inv;
     const float uu = ux * ux + uy * uy + uz * uz;
     if (!(rho > 0.f) || !(uu < 0.09f)) atomicOr(lv.status, ST_UNSTABLE);
+    // the moments of the nodes beside a sheared plane, for its passes
+    if (lv.le_mom != nullptr && (xyz[0] == 0 || xyz[0] == lv.nx - 1))
+      lv.le_mom[(xyz[0] == 0 ? 0u : (unsigned)lv.ny * (unsigned)lv.nz) + (unsigned)xyz[1] +
+                (unsigned)lv.ny * (unsigned)xyz[2]] = make_float4(drho, ux, uy, uz);
     const float om = lv.omega;
     const float src_w = 1.0f - 0.5f * om;
     const float uF = ux * Fx + uy * Fy + uz * Fz;

@@ -921,6 +921,14 @@ __global__ void k_solve(LatticeView lv, PartView pv) {
   }
   int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
   if (move) {
+    // Sec. IV: a free cell closer than le_dr to the sheared plane (x = -1/2)
+    // and moving toward it has its normal velocity negated; the step's
+    // coupling above used the solve's velocity, the cell moves with the
+    // reflected one (reading Q25)
+    if (pv.le_dr > 0.0 && pv.move == 1) {
+      const double dlo = X[0] + 0.5, dhi = (double)lv.nx - 0.5 - X[0];
+      if ((dlo < pv.le_dr && V[0] < 0.0) || (dhi < pv.le_dr && V[0] > 0.0)) V[0] = -V[0];
+    }
     rigid_advance(lv, X, q, V, W);
     for (int k = 0; k < 3; ++k) {
       pv.X[3 * p + k] = X[k];

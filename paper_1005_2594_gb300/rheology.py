@@ -231,3 +231,100 @@ def run(p, X, q, mask, steps, samples=20, model=None, gap_range=None, stream=Non
     H = np.nanmean(np.array([pr[2] for pr in prof]), axis=0)
     n_fl = np.sum(np.array([pr[3] for pr in prof]), axis=0)
     return float(np.mean(out)), out, ms, (centres, u_mean, H, n_fl)
+
+
+# ---------------------------------------------------------------------------
+# Lees-Edwards shear cell (Sec. IV): plane Couette flow of a homogeneous
+# suspension, the velocity gradient along x, the flow along z
+
+
+def le_reflect_distance(p):
+    """Sec. IV's reflection distance sigma_perp, raised to max(R) + 1 so that
+    no cell covers a node beside the sheared plane (the library's default)"""
+    return max(p["sig_perp"], max(p["R_perp"], p["R_par"]) + 1.0)
+
+
+def le_shear_case(cells=True, nx=128, ny=40, nz=40, number_density_m3=6.4e15, seed=1011):
+    """Sec. IV's shear cell in lattice units: 128 x 40 x 40 (85 x 27 x 27
+    um^3), periodic, sheared across the x plane; cells with sigma = (4, 4/3)
+    um = (6, 2) nodes and R = 11/12 sigma at the paper's number density
+    6.4e15 / m^3 (its hematocrit of 56 %), stiffness 1.47e-15 J, on a jittered
+    fcc start with centres kept half a node beyond the reflection distance.
+    Returns params, X, q (empty without cells)."""
+    sig = (4.0 / DX_UM, (4.0 / 3.0) / DX_UM)
+    R = (sig[0] * 11.0 / 12.0, sig[1] * 11.0 / 12.0)
+    p = workloads.base_params(nx, ny, nz, periodic=(1, 1, 1), R=R, sigma=sig, eps=1.47e-15 / E_UNIT_J)
+    if not cells:
+        return p, np.zeros((0, 3)), np.zeros((0, 4))
+    n_cells = int(round(number_density_m3 * nx * ny * nz * (DX_UM * 1e-6) ** 3))
+    dr = le_reflect_distance(p)
+
+    def inside(x):
+        return (x[:, 0] + 0.5 > dr + 0.5) & (nx - 0.5 - x[:, 0] > dr + 0.5)
+
+    X, q = workloads.fcc_cells(p, n_cells, seed, inside)
+    return p, X, q
+
+
+def x_profile(u, owner, p, axis_flow=2):
+    """mean flow velocity of the fluid nodes in each plane x = const"""
+    nx = p["nx"]
+    x = np.arange(len(owner)) % nx
+    fl = np.asarray(owner) == -1
+    s = np.bincount(x[fl], weights=np.asarray(u)[fl, axis_flow], minlength=nx)
+    c = np.bincount(x[fl], minlength=nx)
+    return s / np.maximum(c, 1)
+
+
+def central_shear_rate(prof, nx):
+    """Sec. IV: the shear rate from a linear fit of v_z(x) over the central
+    half of the box, away from the sheared plane"""
+    x = np.arange(nx)
+    sel = (x >= nx // 4) & (x < nx - nx // 4)
+    return float(np.polyfit(x[sel], prof[sel], 1)[0])
+
+
+def run_le(p, X, q, U, steps, samples=20, stream=None):
+    """steps of the shear cell from rest under the offset U; over the second
+    half, Delta p_LE and the v_z(x) profile sampled `samples` times.
+    Returns dict(mu_rel = mu_app / mu of Eq. (mu), gamma_dot per step and in
+    1/s, the mean profile, the momentum transfer per step, ms of stepping)."""
+    import torch
+
+    st = torch.cuda.current_stream() if stream is None else stream
+    sim = bl.Simulation(p, stream=st.cuda_stream)
+    sim.lees_edwards(U)
+    if len(X):
+        sim.set_particles(X, q)
+    half = steps // 2
+    every = max(2, (steps - half) // samples) // 2 * 2
+    ms = 0.0
+
+    def advance(k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sim.step(k)
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    prof = []
+    try:
+        ms += advance(half)
+        P0, n0 = sim.lees_edwards_momentum()
+        done = half
+        while done + every <= steps:
+            ms += advance(every)
+            done += every
+            _, u, own = sim.fields()
+            prof.append(x_profile(u, own, p))
+        P1, n1 = sim.lees_edwards_momentum()
+        sim.sync()
+    finally:
+        sim.close()
+    v = np.mean(prof, axis=0)
+    gd = central_shear_rate(v, p["nx"])
+    P = (P1 - P0) / (n1 - n0)
+    mu = p["rho0"] * (p["tau"] - 0.5) / 3.0
+    return {"mu_rel": -P / (p["ny"] * p["nz"] * gd) / mu, "gamma_dot": gd, "gamma_dot_per_s": gd / DT_S,
+            "profile": v, "P_per_step": P, "ms": ms, "steps": done}

@@ -277,6 +277,52 @@ int bl_autotune(bl_ctx *c, int trial_steps, int *choice);
    member are reported by bl_ensemble_step / bl_ensemble_sync (the first
    one).  The paper has no counterpart (a batching interface of this
    library). */
+/* ---------------------------------------------------------------------
+   Indexed lattice of vessel networks (closing discussion of the paper: the
+   method joined to an indexed LB scheme for digitised vessel networks).
+   Only the fluid nodes of a lattice with walls are stored and swept, so
+   memory and time scale with the lumen, not the bounding box.  The update is
+   the dense lattice's plasma update of Sec. II (moments, Guo forcing, BGK
+   toward the third-order equilibrium, mid-link bounce-back with the
+   moving-wall term C, the walls' momentum); cells are not coupled to it.
+   Fluid nodes are numbered in dense node order (x fastest); a table gives
+   each one's 18 neighbours.  Walls: the face layers of non-periodic axes
+   (ids 0..5, first walled axis in x, y, z order) and a mask of N bytes as
+   for bl_walls_set (value k in 1..8: wall id k - 1, overriding). */
+typedef struct bl_sparse bl_sparse;
+
+/* Host only (no device work): the index of a lattice.  With dense_of and nbr
+   NULL, *n_fluid receives the number of fluid nodes.  Otherwise *n_fluid
+   must hold their capacity (>= that number; BL_EINVAL if smaller) and
+   receives the number; dense_of[i] is the dense index x + nx (y + ny z) of
+   fluid node i, nbr[(r - 1) n_fluid + i] (r = 1..18, the direction
+   numbering above) the fluid index of node i + c_r, or -1 - w for a wall of
+   id w.  Either array may be NULL.  mask may be NULL. */
+int bl_sparse_index_build(const bl_lb_params *p, const uint8_t *mask, int64_t *n_fluid, int32_t *dense_of,
+                          int32_t *nbr);
+
+/* Creates an indexed lattice: builds the index on the host, uploads it and
+   sets resting fluid n^eq(rho_bar, 0).  Storage 19 x n_fluid elements of
+   p->store_dtype plus 18 x n_fluid int32.  cuda_stream as in bl_lb_init. */
+int bl_sparse_init(bl_sparse **out, const bl_lb_params *p, const uint8_t *mask, void *cuda_stream);
+/* nsteps steps (pairs of steps replay one CUDA graph). */
+int bl_sparse_step(bl_sparse *s, int nsteps);
+/* rho (N) and u = (j + rho g / 2) / rho (N x 3) on the dense grid, zero at
+   walls; host (on_device 0) or device pointers.  Waits on the stream. */
+int bl_sparse_fields_get(bl_sparse *s, double *rho, double *u, int on_device);
+/* populations n_r (N x 19 host doubles on the dense grid, zero at walls) as
+   the next step reads them; set writes those of the fluid nodes. */
+int bl_sparse_populations_get(bl_sparse *s, double *pop);
+int bl_sparse_populations_set(bl_sparse *s, const double *pop);
+/* momentum given to each wall id since the previous call, then reset (8 x 3). */
+int bl_sparse_wall_momentum_get(bl_sparse *s, double *wallmom);
+/* waits for the stream; BL_EUNSTABLE if a node went unstable */
+int bl_sparse_sync(bl_sparse *s);
+int64_t bl_sparse_nodes(const bl_sparse *s);
+int64_t bl_sparse_launch_count(const bl_sparse *s);
+const char *bl_sparse_last_error(const bl_sparse *s);
+void bl_sparse_destroy(bl_sparse *s);
+
 typedef struct bl_ens bl_ens;
 int bl_ensemble_create(bl_ens **out, bl_ctx *const *ctxs, int n, void *cuda_stream);
 int bl_ensemble_step(bl_ens *e, int nsteps);

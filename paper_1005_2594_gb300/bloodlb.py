@@ -40,6 +40,9 @@ ABI_FUNCTIONS = (
     "bl_mlp_grad", "bl_mlp_adam", "bl_mlp_sync", "bl_mlp_destroy", "bl_mlp_attach", "bl_mlp_attach_range", "bl_pair_features",
     "bl_timing_enable",
     "bl_timing_read", "bl_launch_count", "bl_sync", "bl_last_error", "bl_destroy",
+    "bl_sparse_index_build", "bl_sparse_init", "bl_sparse_step", "bl_sparse_fields_get", "bl_sparse_populations_get",
+    "bl_sparse_populations_set", "bl_sparse_wall_momentum_get", "bl_sparse_sync", "bl_sparse_nodes",
+    "bl_sparse_launch_count", "bl_sparse_last_error", "bl_sparse_destroy",
 )
 
 
@@ -128,6 +131,20 @@ def lib():
         "bl_sync": (ctypes.c_int, [vp]),
         "bl_last_error": (ctypes.c_char_p, [vp]),
         "bl_destroy": (None, [vp]),
+        "bl_sparse_index_build": (ctypes.c_int, [ctypes.POINTER(bl_lb_params), ctypes.POINTER(ctypes.c_uint8),
+                                                 ctypes.POINTER(i64), I, I]),
+        "bl_sparse_init": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(bl_lb_params),
+                                          ctypes.POINTER(ctypes.c_uint8), vp]),
+        "bl_sparse_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "bl_sparse_fields_get": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "bl_sparse_populations_get": (ctypes.c_int, [vp, D]),
+        "bl_sparse_populations_set": (ctypes.c_int, [vp, D]),
+        "bl_sparse_wall_momentum_get": (ctypes.c_int, [vp, D]),
+        "bl_sparse_sync": (ctypes.c_int, [vp]),
+        "bl_sparse_nodes": (i64, [vp]),
+        "bl_sparse_launch_count": (i64, [vp]),
+        "bl_sparse_last_error": (ctypes.c_char_p, [vp]),
+        "bl_sparse_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -565,3 +582,143 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+# --- the indexed lattice of vessel networks ---------------------------------
+
+
+def _sparse_check(h, rc):
+    if rc != BL_OK:
+        msg = lib().bl_sparse_last_error(h) if h else b""
+        raise BloodLBError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _mask_ptr(mask, N):
+    if mask is None:
+        return None, None
+    m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    if m.size != N:
+        raise ValueError("mask has %d entries, the lattice %d nodes" % (m.size, N))
+    return m, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def bl_sparse_index_build(params: dict, mask=None):
+    """host-only index of a lattice: (dense index of each fluid node, the
+    18 x n_fluid neighbour table, fluid index or -1 - wall id)"""
+    p = lb_params(params)
+    N = int(params["nx"]) * int(params["ny"]) * int(params["nz"])
+    m, mp = _mask_ptr(mask, N)
+    n = ctypes.c_int64(0)
+    _sparse_check(None, lib().bl_sparse_index_build(ctypes.byref(p), mp, ctypes.byref(n), None, None))
+    dense = np.zeros(max(n.value, 1), dtype=np.int32)
+    nbr = np.zeros((18, max(n.value, 1)), dtype=np.int32)
+    _sparse_check(None, lib().bl_sparse_index_build(ctypes.byref(p), mp, ctypes.byref(n), _ip(dense), _ip(nbr)))
+    return dense[: n.value], nbr[:, : n.value]
+
+
+def bl_sparse_init(params: dict, wall_mask=None, store_dtype=BL_STORE_F32, stream=None):
+    N = int(params["nx"]) * int(params["ny"]) * int(params["nz"])
+    p = lb_params(params, store_dtype=store_dtype)
+    m, mp = _mask_ptr(wall_mask, N)
+    h = ctypes.c_void_p(None)
+    _sparse_check(None, lib().bl_sparse_init(ctypes.byref(h), ctypes.byref(p), mp, ctypes.c_void_p(stream or 0)))
+    return h.value
+
+
+def bl_sparse_step(h, n):
+    _sparse_check(h, lib().bl_sparse_step(h, int(n)))
+
+
+def bl_sparse_sync(h):
+    _sparse_check(h, lib().bl_sparse_sync(h))
+
+
+def bl_sparse_fields_get(h, N, rho=None, u=None, on_device=False):
+    """host: returns (rho, u) on the dense grid; on_device: fills the given
+    float64 tensors (N, N x 3)"""
+    if on_device:
+        _sparse_check(h, lib().bl_sparse_fields_get(h, rho.data_ptr() if rho is not None else None,
+                                                     u.data_ptr() if u is not None else None, 1))
+        return rho, u
+    rho = np.zeros(N)
+    u = np.zeros((N, 3))
+    _sparse_check(h, lib().bl_sparse_fields_get(h, rho.ctypes.data, u.ctypes.data, 0))
+    return rho, u
+
+
+def bl_sparse_populations_get(h, N):
+    pop = np.zeros((N, 19))
+    _sparse_check(h, lib().bl_sparse_populations_get(h, _dp(pop)))
+    return pop
+
+
+def bl_sparse_populations_set(h, N, pop):
+    pop = np.ascontiguousarray(pop, dtype=np.float64).reshape(N, 19)
+    _sparse_check(h, lib().bl_sparse_populations_set(h, _dp(pop)))
+
+
+def bl_sparse_wall_momentum_get(h):
+    out = np.zeros((8, 3))
+    _sparse_check(h, lib().bl_sparse_wall_momentum_get(h, _dp(out)))
+    return out
+
+
+def bl_sparse_nodes(h):
+    return int(lib().bl_sparse_nodes(h))
+
+
+def bl_sparse_launch_count(h):
+    return int(lib().bl_sparse_launch_count(h))
+
+
+def bl_sparse_last_error(h):
+    msg = lib().bl_sparse_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def bl_sparse_destroy(h):
+    lib().bl_sparse_destroy(h)
+
+
+class SparseLattice:
+    """The indexed lattice (only fluid nodes stored) of a geometry given by
+    face walls and a wall mask; plasma only."""
+
+    def __init__(self, params: dict, wall_mask=None, store_dtype=BL_STORE_F32, stream=None):
+        self.params = dict(params)
+        self.N = int(params["nx"]) * int(params["ny"]) * int(params["nz"])
+        self.h = bl_sparse_init(params, wall_mask, store_dtype, stream)
+        self.n_fluid = bl_sparse_nodes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            bl_sparse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        bl_sparse_step(self.h, n)
+
+    def sync(self):
+        bl_sparse_sync(self.h)
+
+    def fields(self):
+        return bl_sparse_fields_get(self.h, self.N)
+
+    def populations(self):
+        return bl_sparse_populations_get(self.h, self.N)
+
+    def set_populations(self, pop):
+        bl_sparse_populations_set(self.h, self.N, pop)
+
+    def wall_momentum(self):
+        return bl_sparse_wall_momentum_get(self.h)
+
+    def launch_count(self):
+        return bl_sparse_launch_count(self.h)

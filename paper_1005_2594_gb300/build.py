@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libbloodlb.so")
 SOURCES = ["bloodlb.cu", "lb_kernels.cu", "lb_sweep_f32.cu", "lb_sweep_bf16.cu", "lb_sweep_f16.cu",
-           "particle_kernels.cu", "cell_list_static.cu", "mlp_kernels.cu"]
+           "particle_kernels.cu", "cell_list_static.cu", "mlp_kernels.cu", "lb_indexed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-Xptxas", "-O3"]

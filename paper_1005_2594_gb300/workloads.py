@@ -457,3 +457,37 @@ def tube_contacts(mu=0.0, seed=1013, radius=11.0):
             X.append([x + 0.3, X[-1][1] - (2 * sig[1] - 0.1) * nvec[1], X[-1][2] - (2 * sig[1] - 0.1) * nvec[2]])
             q.append(qa)
     return p, np.array(X), np.array(q), mask
+
+
+def vessel_loop(nx=1024, ny=256, nz=64, r0=16.0, h=64.0, wall_id=6):
+    """uint8 wall mask of a synthetic vessel network for the indexed lattice:
+    a parent vessel of radius r0 along x through the box centre (periodic in
+    x) that splits into two daughters of radius r0 2^(-1/3) (Murray's law,
+    the parent's cube equal to the sum of the daughters'), offset by -+h in
+    y, which run parallel and rejoin -- the bifurcation and confluence of a
+    microvascular loop.  Each vessel is the union of capsules (segments with
+    round ends) along its centre line; nodes outside every capsule are wall
+    (mask value wall_id + 1).  Returns the mask (N bytes) and the lumen's
+    centre-line segments ((x0, y0), (x1, y1), radius) in the z = (nz-1)/2
+    plane."""
+    rd = r0 * 2.0 ** (-1.0 / 3.0)
+    yc, zc = (ny - 1) / 2.0, (nz - 1) / 2.0
+    xa, xb, xc, xd = 0.125 * nx, 0.375 * nx, 0.625 * nx, 0.875 * nx
+    segs = [((-r0, yc), (xa, yc), r0), ((xd, yc), (nx + r0, yc), r0)]
+    for s in (-1.0, 1.0):
+        segs += [((xa, yc), (xb, yc + s * h), rd), ((xb, yc + s * h), (xc, yc + s * h), rd),
+                 ((xc, yc + s * h), (xd, yc), rd)]
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    # squared in-plane distance to each centre line, then one z slice at a time
+    d2xy = []
+    for (x0, y0), (x1, y1), r in segs:
+        dx, dy = x1 - x0, y1 - y0
+        t = np.clip(((x - x0) * dx + (y - y0) * dy) / (dx * dx + dy * dy), 0.0, 1.0)
+        d2xy.append(((x - (x0 + t * dx)) ** 2 + (y - (y0 + t * dy)) ** 2, r))
+    mask = np.empty((nz, ny, nx), dtype=np.uint8)
+    for k in range(nz):
+        inside = np.zeros((ny, nx), dtype=bool)
+        for d2, r in d2xy:
+            inside |= d2 + (k - zc) ** 2 < r * r
+        mask[k] = np.where(inside, 0, wall_id + 1)
+    return mask.reshape(-1), segs

@@ -11,7 +11,8 @@ moved by -+U.  The pins:
 * U = 0 is the plain periodic box, bit for bit;
 * start-up Couette flow settles to the exact linear profile of slope U / nx,
   continuous across the plane, and the momentum moved across the plane per
-  step, Delta p_LE of Eq. (mu), gives the plasma's viscosity rho nu = 1/6;
+  step, Delta p_LE of Eq. (mu), gives the plasma's viscosity rho nu, at
+  tau = 1 (1/6) and tau = 0.8 (1/10);
 * a transverse shear wave (Kelvin mode) on that flow, whose phase fronts tilt
   and cross the plane at the image's offset, follows its exact solution --
   with the offset's sign flipped the error is ~45 times larger;
@@ -48,9 +49,11 @@ def test_zero_offset_is_the_periodic_box():
     assert b.lees_edwards()["steps"] == 20
 
 
-def test_couette_startup_is_exact_and_gives_the_plasma_viscosity():
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_couette_startup_is_exact_and_gives_the_plasma_viscosity(tau):
     nx, ny, nz, U = 16, 2, 4, 0.01
     p = workloads.base_params(nx, ny, nz, periodic=(1, 1, 1))
+    p["tau"] = tau
     o = oracle.Oracle(p)
     o.set_lees_edwards(U)
     m0, _ = o.totals()
@@ -63,9 +66,9 @@ def test_couette_startup_is_exact_and_gives_the_plasma_viscosity():
     assert np.abs(uz - (slope * x + icpt)).max() < 1e-12
     # continuous across the plane: x = nx continues as x = 0 of the image above
     assert abs(uz[-1] + slope - (uz[0] + U)) < 1e-12
-    # Eq. (mu): mu_app = -Delta p_LE / (l_y l_z gamma_dot) = rho nu
+    # Eq. (mu): mu_app = -Delta p_LE / (l_y l_z gamma_dot) = rho nu, nu = (tau - 1/2) / 3
     le = o.lees_edwards()
-    assert abs(-le["P"] / (ny * nz * slope) - 1.0 / 6.0) < 1e-9
+    assert abs(-le["P"] / (ny * nz * slope) - (tau - 0.5) / 3.0) < 1e-9
     m1, _ = o.totals()
     assert abs(m1 - m0) < 1e-12 * m0
 

@@ -91,3 +91,32 @@ def test_arteriole_case_in_lattice_units():
     u_max = rheology.poiseuille(0.0, radius, 1e-6, 1 / 6.0)
     Q = math.pi * radius ** 2 * u_max / 2
     assert abs(rheology.pseudo_shear_rate(Q, radius) * rheology.DT_S - u_max / (4 * radius)) < 1e-15
+
+
+def test_shear_cell_analysis_and_case():
+    """Sec. IV's shear cell: the profile v_z(x) averages the fluid nodes of
+    each plane, the shear rate comes from its central half only (a profile
+    with steeper layers beside the sheared plane keeps the central slope), and
+    the case has the paper's number density with every cell beyond the
+    reflection distance"""
+    p = workloads.base_params(16, 3, 4, periodic=(1, 1, 1))
+    N = 16 * 3 * 4
+    x = np.arange(N) % 16
+    u = np.zeros((N, 3))
+    u[:, 2] = 2e-4 * (x - 7.5)
+    owner = np.full(N, -1)
+    owner[::7] = 0  # cell nodes carry no fluid velocity
+    u[owner == 0, 2] = 99.0
+    prof = rheology.x_profile(u, owner, p)
+    np.testing.assert_allclose(prof, 2e-4 * (np.arange(16) - 7.5), rtol=0, atol=1e-15)
+    bent = prof + np.where(np.arange(16) < 4, -3e-4 * (4 - np.arange(16)), 0.0)
+    bent = bent + np.where(np.arange(16) >= 12, 3e-4 * (np.arange(16) - 11), 0.0)
+    assert abs(rheology.central_shear_rate(bent, 16) - 2e-4) < 1e-15
+    p, X, q = rheology.le_shear_case()
+    vol_m3 = p["nx"] * p["ny"] * p["nz"] * (rheology.DX_UM * 1e-6) ** 3
+    assert len(X) == round(6.4e15 * vol_m3)
+    dr = rheology.le_reflect_distance(p)
+    assert dr == max(p["sig_perp"], p["R_perp"] + 1.0) == 6.5
+    assert (X[:, 0] + 0.5 > dr).all() and (p["nx"] - 0.5 - X[:, 0] > dr).all()
+    sig_vol = len(X) * 4.0 / 3.0 * math.pi * p["sig_perp"] ** 2 * p["sig_par"] / (p["nx"] * p["ny"] * p["nz"])
+    assert abs(sig_vol - 0.56) < 0.02  # the paper's hematocrit of 56 %

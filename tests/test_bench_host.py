@@ -1,7 +1,9 @@
 """Host-side logic of bench.py (no GPU): the DRAM-traffic entry is reported
 only for the sweep source, workload and storage it was captured on; whole-job
 values sum the replicas over the slowest rank's time; the bounded oracle
-sample of the reference arm stays within its budget."""
+sample of the reference arm stays within its budget; the reference line of
+the indexed lattice counts fluid nodes; the indexed lattice's host index
+refuses bad input."""
 import os
 import sys
 
@@ -73,3 +75,36 @@ def test_clock_sampler_reports_without_a_gpu():
     c.start()
     out = c.stop()
     assert "samples" in out and "reasons" in out
+
+
+def test_reference_arm_line_for_the_vessel_loop_counts_fluid_nodes():
+    """--impl reference on the indexed-lattice config: the oracle's rate in
+    fluid-node updates, the unit saying so, as the GPU line does"""
+    import argparse
+
+    args = argparse.Namespace(config="vessel_loop", steps=1, warmup=0)
+    out = bench.run_reference(args, 1, 0)
+    assert out["impl"] == "reference" and out["unit"].endswith("(fluid nodes)")
+    assert out["cpu_baseline"]["unit"] == out["unit"] == out["e2e"]["unit"]
+    assert out["value"] > 0 and out["cpu_baseline"]["cores"] >= 1
+    assert "256x128x32" in out["config"]["sample"]
+
+
+def test_sparse_index_rejects_bad_input():
+    import ctypes
+
+    import numpy as np
+    import pytest
+
+    from paper_1005_2594_gb300 import bloodlb as bl
+    from paper_1005_2594_gb300 import workloads
+
+    p = workloads.base_params(6, 5, 4, periodic=(1, 0, 1))
+    with pytest.raises(ValueError):
+        bl.bl_sparse_index_build(p, np.zeros(7, dtype=np.uint8))  # wrong size
+    with pytest.raises(bl.BloodLBError):
+        bl.bl_sparse_index_build(p, np.full(6 * 5 * 4, 9, dtype=np.uint8))  # no wall id 8
+    q = workloads.base_params(6, 2, 4, periodic=(1, 0, 1))  # a walled axis needs fluid between its walls
+    n = ctypes.c_int64(0)
+    assert bl.lib().bl_sparse_index_build(ctypes.byref(bl.lb_params(q)), None, ctypes.byref(n), None, None) \
+        == bl.BL_EINVAL

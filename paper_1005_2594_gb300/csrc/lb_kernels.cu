@@ -421,9 +421,8 @@ __device__ __forceinline__ float eq_t(float cu, float uu) {
   return cu * (3.0f + 4.5f * cu * cu - 4.5f * uu) + 4.5f * cu * cu - 1.5f * uu;
 }
 
-template <int PAR>
+// node (x, y, z) + c_r, periodic
 __device__ __forceinline__ unsigned le_node_plus(const LatticeView &lv, int x, int y, int z, int r) {
-  // node x + c_r (periodic) for the odd sweep's write target
   using D = D3Q19;
   const int xx = x + D::cx(r), yy = y + D::cy(r), zz = z + D::cz(r);
   const int xw = xx < 0 ? xx + lv.nx : (xx >= lv.nx ? xx - lv.nx : xx);
@@ -455,7 +454,7 @@ __global__ void __launch_bounds__(128) k_le_gather(LatticeView lv, LeView le) {
     for (int k = 0; k < 5; ++k) {
       const int r = pl ? kLeUp[k] : kLeDn[k];
       const float cx = (float)D::cx(r), cy = (float)D::cy(r), cz = (float)D::cz(r);
-      const unsigned slot = PAR == 0 ? (unsigned)D::opp(r) * lv.N + n : (unsigned)r * lv.N + le_node_plus<PAR>(lv, x, y, z, r);
+      const unsigned slot = PAR == 0 ? (unsigned)D::opp(r) * lv.N + n : (unsigned)r * lv.N + le_node_plus(lv, x, y, z, r);
       const float f = Store<S>::ld(pop + slot);
       const float cu = cx * m.y + cy * m.z + cz * m.w, cu2 = cx * m.y + cy * m.z + cz * uz2;
       const float dT = ((float)D::m(r) / 36.0f) * rho * (eq_t(cu2, uu2) - eq_t(cu, uu));
@@ -503,7 +502,7 @@ __global__ void __launch_bounds__(128) k_le_scatter(LatticeView lv, LeView le) {
     const float a = T[(size_t)k * M + ys + ny * za], b = T[(size_t)k * M + ys + ny * zb];
     const float v = fmaf(w, b - a, a);
     // where the next sweep reads population r of node n
-    const unsigned slot = PAR == 0 ? (unsigned)D::opp(r) * lv.N + le_node_plus<PAR>(lv, x, y, z, D::opp(r))
+    const unsigned slot = PAR == 0 ? (unsigned)D::opp(r) * lv.N + le_node_plus(lv, x, y, z, D::opp(r))
                                    : (unsigned)r * lv.N + n;
     Store<S>::st(pop + slot, v);
   }
